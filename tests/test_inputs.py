@@ -1,0 +1,125 @@
+"""Pins for the seeded input generator (CPU only).
+
+The generator is shared by the CUDA decoder's tests and the oracle's, so it
+is pinned against things outside itself: CRC catalogue check values and
+zlib, the Kronecker-product definition of G_N, the (8,4) example of Fig. 1,
+scipy quadrature and the large-mean asymptote of phi, and the AWGN moments.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+from paper_1505_01466_gb300 import inputs as I
+
+CHECK = np.unpackbits(np.frombuffer(b"123456789", dtype=np.uint8))  # MSB-first per byte
+
+
+def test_crc_catalogue_values():
+    # CRC-8/SMBUS (poly 0x07, init 0, no reflection, no xor-out): check 0xF4.
+    assert int("".join(map(str, I.crc_bits(CHECK, 8, 0x07))), 2) == 0xF4
+    # CRC-32/MPEG-2 (poly 0x04C11DB7, init 0xFFFFFFFF, no reflection): 0x0376E6E7.
+    v = int("".join(map(str, I.crc_bits(CHECK, 32, I.CRC32_POLY, init=0xFFFFFFFF))), 2)
+    assert v == 0x0376E6E7
+    # CRC-32/POSIX has init 0 and xor-out 0xFFFFFFFF with check 0x765E7680, so
+    # the variant used here (init 0, no xor-out) must give 0x765E7680 ^ ~0.
+    v = int("".join(map(str, I.crc_bits(CHECK, 32, I.CRC32_POLY))), 2)
+    assert v == 0x765E7680 ^ 0xFFFFFFFF
+
+
+def _reflect(v, w):
+    return int(format(v, f"0{w}b")[::-1], 2)
+
+
+def test_crc32_matches_zlib_after_reflection():
+    rng = np.random.default_rng(5)
+    for n in (1, 7, 64, 300):
+        data = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        bits_lsb_first = np.unpackbits(np.frombuffer(data, np.uint8), bitorder="little")
+        reg = int("".join(map(str, I.crc_bits(bits_lsb_first, 32, I.CRC32_POLY, 0xFFFFFFFF))), 2)
+        assert _reflect(reg, 32) ^ 0xFFFFFFFF == zlib.crc32(data)
+
+
+def test_crc_appended_word_has_zero_remainder_and_is_linear():
+    rng = np.random.default_rng(1)
+    d = rng.integers(0, 2, (20, 100), dtype=np.uint8)
+    r = I.crc_bits(d, 32, I.CRC32_POLY)
+    full = np.concatenate([d, r], axis=1)
+    assert not I.crc_bits(full, 32, I.CRC32_POLY).any()
+    a, b = d[:10], d[10:]
+    assert np.array_equal(I.crc_bits(a ^ b, 32, I.CRC32_POLY),
+                          I.crc_bits(a, 32, I.CRC32_POLY) ^ I.crc_bits(b, 32, I.CRC32_POLY))
+
+
+@pytest.mark.parametrize("N", [2, 8, 32, 256])
+def test_polar_transform_is_kronecker_power(N):
+    F = np.array([[1, 0], [1, 1]], dtype=np.int64)
+    G = np.array([[1]], dtype=np.int64)
+    while G.shape[0] < N:
+        G = np.kron(G, F)
+    rng = np.random.default_rng(N)
+    u = rng.integers(0, 2, (16, N), dtype=np.uint8)
+    assert np.array_equal(I.polar_transform(u), (u.astype(np.int64) @ G) % 2)
+    assert np.array_equal(I.polar_transform(I.polar_transform(u)), u)   # G_N G_N = I
+
+
+def test_ga_information_set_of_fig1():
+    mask = I.ga_frozen_mask(8, 4, 2.0)
+    assert list(I.info_positions(mask)) == [3, 5, 6, 7]
+
+
+def test_phi_against_scipy_quadrature_and_asymptote():
+    integrate = pytest.importorskip("scipy.integrate")
+    for m in (0.05, 0.5, 2.0, 10.0, 40.0):
+        s = math.sqrt(2 * m)
+        f = lambda u: (1.0 - math.tanh(u / 2)) * math.exp(-(u - m) ** 2 / (4 * m)) / math.sqrt(4 * math.pi * m)
+        ref, _ = integrate.quad(f, m - 30 * s, m + 30 * s, points=[0.0], limit=400, epsabs=0, epsrel=1e-12)
+        lp, psi = I._log_phi_and_psi(m)
+        assert math.exp(lp) == pytest.approx(ref, rel=1e-6)
+        assert psi == pytest.approx(1.0 - ref, rel=1e-6, abs=1e-12)
+    # large-mean asymptote phi(m) ~ sqrt(pi/m) exp(-m/4) (1 - 10/(7m)) + O(m^-2)
+    for m in (200.0, 1000.0, 20000.0):
+        lp, _ = I._log_phi_and_psi(m)
+        asym = 0.5 * math.log(math.pi / m) - m / 4 + math.log(1 - 10 / (7 * m))
+        assert abs(lp - asym) < 5.0 / m
+
+
+def test_ga_means_monotone_and_doubling():
+    means = I.ga_leaf_means(64, 3.0, 0.5)
+    # a right (G) child doubles its parent's mean, a left (F) child is below it
+    assert (means[1::2] >= means[0::2]).all()
+    sig = I.sigma_for(3.0, 0.5)
+    assert means[-1] == pytest.approx(64 * 2 / sig ** 2)
+
+
+def test_awgn_llr_moments_and_quantisation():
+    fr = I.ga_frozen_mask(256, 128, 2.0)
+    f = I.make_frames(fr, 0, 0, 2.0, 400, seed=3)
+    sig = f.sigma
+    s = 1.0 - 2.0 * f.codeword.astype(np.float64)
+    z = f.llr_f32.astype(np.float64) * s          # sign-corrected LLR ~ N(2/s^2, 4/s^2)
+    assert z.mean() == pytest.approx(2 / sig ** 2, rel=0.02)
+    assert z.var() == pytest.approx(4 / sig ** 2, rel=0.03)
+    q = I.quantize_i8(np.array([0.125, 0.375, -0.125, -0.375, 100.0, -100.0, 1.0]))
+    assert list(q) == [0, 2, 0, -2, 127, -127, 4]   # rint: half to even
+
+
+def test_noiseless_frames_and_payload_placement():
+    fr = I.ga_frozen_mask(64, 40, 3.0)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 3.0, 10, seed=9, noiseless=True)
+    u = I.polar_transform(f.codeword)
+    info = I.info_positions(fr)
+    assert not u[:, fr == 1].any()
+    assert np.array_equal(u[:, info[:32]], f.payload)
+    assert not I.crc_bits(u[:, info], 8, I.CRC8_POLY).any()
+    assert np.array_equal(f.llr_f32 < 0, f.codeword == 1)
+
+
+def test_pack_roundtrip():
+    rng = np.random.default_rng(0)
+    b = rng.integers(0, 2, (3, 13), dtype=np.uint8)
+    p = I.pack_bits_lsb(b)
+    assert p.shape == (3, 2)
+    assert p[0, 0] == sum(int(b[0, i]) << i for i in range(8))
+    assert np.array_equal(I.unpack_bits_lsb(p, 13), b)

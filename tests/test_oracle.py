@@ -1,0 +1,298 @@
+"""Pins for the CPU oracle (CPU only).
+
+The oracle is checked against things that do not come from it:
+
+* brute-force maximum likelihood: with L >= 2^K nothing is pruned, so the
+  final list of the SC-list decoder holds every codeword, and with min-sum
+  (max-log) updates each path's penalty telescopes to the correlation
+  discrepancy sum_{i: x_i != h(y_i)} |y_i| (Eq. (6) summed down the tree);
+  the fast decoder must give the same list when its nodes are exhaustive
+  (Rate-1 of length <= 2, SPC of length 4, repetition, Rate-0);
+* noiseless frames decode to the sent payload with penalty 0;
+* the (8,4) example of Fig. 1 / Fig. 2 / Listing 2;
+* codes whose forking leaves each carry a single information bit make the
+  fast decoder and bit-by-bit SC-list take identical decisions at any L;
+* the fast decoder's frame-error rate matches SC-list (Sec. VI) within
+  Monte-Carlo confidence;
+* plausible single mistakes planted in a copy of the oracle source fail at
+  least one of these checks.
+"""
+import itertools
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1505_01466_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _brute_force(frozen, y):
+    """All codewords with their correlation discrepancy penalties."""
+    N = frozen.size
+    info = np.flatnonzero(frozen == 0)
+    hy = (y < 0).astype(np.uint8)
+    out = []
+    for bits in itertools.product((0, 1), repeat=info.size):
+        u = np.zeros(N, np.uint8)
+        u[info] = bits
+        x = I.polar_transform(u)
+        out.append((float(np.abs(y[x != hy]).sum()), tuple(int(v) for v in x)))
+    return sorted(out)
+
+
+def _final_list(oracle_mod, frozen, L, y, mode):
+    words, pens = oracle_mod.decode_list(frozen, L, y, mode)
+    return sorted((float(p), tuple(int(v) for v in w)) for w, p in zip(words, pens))
+
+
+def _random_code(rng, N, K):
+    fr = np.ones(N, np.uint8)
+    fr[rng.choice(N, K, replace=False)] = 0
+    return fr
+
+
+def _fast_leaves_exhaustive(oracle_mod, frozen, mode):
+    for kind, nv, _ in oracle_mod.schedule(frozen, mode):
+        if kind == oracle_mod.LEAF_RATE1 and nv > 2:
+            return False
+        if kind == oracle_mod.LEAF_SPC and nv != 4:
+            return False
+    return True
+
+
+def test_golden_fig1_schedule(oracle_mod):
+    names = {"F": 0, "G": 1, "COMBINE": 2, "RATE0": 11, "RATE1": 12, "REP": 13, "SPC": 14}
+    frozen, info, ops = None, None, []
+    with open(os.path.join(HERE, "golden", "fig1_code_8_4.txt")) as fh:
+        for line in fh:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "frozen":
+                frozen = np.array([int(v) for v in t[1:]], np.uint8)
+            elif t[0] == "info":
+                info = [int(v) for v in t[1:]]
+            elif t[0] == "op":
+                ops.append((names[t[1]], int(t[2]), int(t[3])))
+    assert list(np.flatnonzero(frozen == 0)) == info
+    assert oracle_mod.schedule(frozen, oracle_mod.SPC4) == ops
+    # the information set also comes out of the GA construction (Fig. 1)
+    assert np.array_equal(I.ga_frozen_mask(8, 4, 2.0), frozen)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_scl_list_equals_brute_force_ml(oracle_mod, dtype):
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        N = int(rng.choice([4, 8, 16]))
+        K = int(rng.integers(1, min(N, 6) + 1))
+        fr = _random_code(rng, N, K)
+        L = 1 << K
+        y = rng.integers(-6, 7, N).astype(np.float32)
+        yy = y.astype(np.int8) if dtype == "i8" else y
+        bf = _brute_force(fr, y)
+        assert _final_list(oracle_mod, fr, L, yy, oracle_mod.BITWISE) == bf
+        # the winner (no CRC) is a maximum-likelihood codeword
+        _, pm, ok, _ = oracle_mod.decode(fr, L, yy[None], 0, 0, oracle_mod.BITWISE)
+        assert pm[0] == bf[0][0] and ok[0] == 1
+
+
+@pytest.mark.parametrize("mode", ["SPC4", "SPC_ANY"])
+def test_fast_list_equals_brute_force_when_nodes_exhaustive(oracle_mod, mode):
+    m = getattr(oracle_mod, mode)
+    rng = np.random.default_rng(12)
+    checked = 0
+    while checked < 40:
+        N = int(rng.choice([4, 8, 16, 32]))
+        K = int(rng.integers(1, min(N, 7) + 1))
+        fr = _random_code(rng, N, K)
+        if not _fast_leaves_exhaustive(oracle_mod, fr, m):
+            continue
+        y = rng.integers(-7, 8, N).astype(np.float32)
+        assert _final_list(oracle_mod, fr, 1 << K, y, m) == _brute_force(fr, y)
+        checked += 1
+
+
+def test_fast_nonexhaustive_rate1_keeps_the_ml_word(oracle_mod):
+    # A Rate-1 node of length 8 (two least-reliable-bit Chase search) still
+    # puts the hard decision, i.e. the ML word of the node, on the list.
+    fr = np.zeros(8, np.uint8)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        y = rng.integers(-9, 10, 8).astype(np.float32)
+        words, pens = oracle_mod.decode_list(fr, 4, y, oracle_mod.SPC4)
+        assert len(words) == 4
+        assert np.array_equal(words[np.argmin(pens)], (y < 0).astype(np.uint8))
+        assert pens.min() == 0.0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("mode", ["BITWISE", "SPC4", "SPC_ANY"])
+def test_noiseless_decodes_sent_payload(oracle_mod, dtype, mode):
+    fr = I.ga_frozen_mask(256, 128, 2.0, 120 / 256)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 2.0, 12, seed=7, noiseless=True)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    for L in (1, 2, 4, 8):
+        bits, pm, ok, slot = oracle_mod.decode(fr, L, llr, 8, I.CRC8_POLY, getattr(oracle_mod, mode))
+        assert np.array_equal(I.unpack_bits_lsb(bits, 120), f.payload)
+        assert (pm == 0).all() and (ok == 1).all()
+
+
+def _sc_decode(frozen, y):
+    """Textbook recursive successive-cancellation decoder (min-sum)."""
+    def rec(a, fr):
+        if a.size == 1:
+            return np.array([0 if fr[0] else int(a[0] < 0)], np.uint8)
+        h = a.size // 2
+        l, r = a[:h], a[h:]
+        fa = np.sign(l) * np.sign(r) * np.minimum(np.abs(l), np.abs(r))
+        bl = rec(fa.astype(np.float32), fr[:h])
+        ga = (r + (1 - 2 * bl.astype(np.float32)) * l).astype(np.float32)
+        br = rec(ga, fr[h:])
+        return np.concatenate([bl ^ br, br])
+    return rec(np.asarray(y, np.float32), frozen)
+
+
+def test_scl_with_one_path_is_sc(oracle_mod):
+    fr = I.ga_frozen_mask(64, 32, 1.0)
+    f = I.make_frames(fr, 0, 0, 1.0, 60, seed=21)
+    bits, _, _, _ = oracle_mod.decode(fr, 1, f.llr_f32, 0, 0, oracle_mod.BITWISE)
+    info = I.info_positions(fr)
+    for i in range(60):
+        x = _sc_decode(fr, f.llr_f32[i])
+        u = I.polar_transform(x)
+        assert np.array_equal(I.unpack_bits_lsb(bits[i], 32), u[info])
+
+
+def _single_info_leaf_code(rng, N):
+    """Random frozen set whose Fast-SSC leaves are Rate-0, repetition or one-bit Rate-1."""
+    def rec(n):
+        r = rng.random()
+        if n == 1:
+            return [int(rng.random() < 0.45)]  # 1 = frozen
+        if r < 0.2:
+            return [1] * n
+        if r < 0.45:
+            return [1] * (n - 1) + [0]
+        return rec(n // 2) + rec(n // 2)
+    return np.array(rec(N), np.uint8)
+
+
+def test_fast_equals_scl_when_each_fork_has_one_info_bit(oracle_mod):
+    rng = np.random.default_rng(4)
+    checked = 0
+    while checked < 25:
+        N = int(rng.choice([16, 32, 64]))
+        fr = _single_info_leaf_code(rng, N)
+        sch = oracle_mod.schedule(fr, oracle_mod.SPC4)
+        if any(k == oracle_mod.LEAF_RATE1 and nv > 1 for k, nv, _ in sch) or \
+           any(k == oracle_mod.LEAF_SPC for k, _, _ in sch) or (fr == 0).sum() == 0:
+            continue
+        y = rng.integers(-8, 9, (6, N)).astype(np.float32)
+        for L in (1, 2, 4, 8):
+            a = oracle_mod.decode(fr, L, y, 0, 0, oracle_mod.BITWISE)
+            b = oracle_mod.decode(fr, L, y, 0, 0, oracle_mod.SPC4)
+            for u, v in zip(a, b):
+                assert np.array_equal(u, v)
+            for i in range(6):
+                wa, pa = oracle_mod.decode_list(fr, L, y[i], oracle_mod.BITWISE)
+                wb, pb = oracle_mod.decode_list(fr, L, y[i], oracle_mod.SPC4)
+                assert np.array_equal(wa, wb) and np.array_equal(pa, pb)
+        checked += 1
+
+
+def _two_proportion_ok(e1, e2, n, z=2.576):
+    p = (e1 + e2) / (2 * n)
+    if p == 0:
+        return True
+    se = math.sqrt(2 * p * (1 - p) / n)
+    return abs(e1 - e2) / n <= z * se + 1.0 / n
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_fast_fer_matches_scl(oracle_mod, dtype):
+    # Sec. VI: Dec-SPC-4 matches the SC-list error-correction performance.
+    fr = I.ga_frozen_mask(256, 128, 2.0, 120 / 256)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 1.75, 2000, seed=2024)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    errs = {}
+    for mode in (oracle_mod.BITWISE, oracle_mod.SPC4):
+        bits, _, _, _ = oracle_mod.decode(fr, 4, llr, 8, I.CRC8_POLY, mode, n_threads=8)
+        errs[mode] = int((I.unpack_bits_lsb(bits, 120) != f.payload).any(1).sum())
+    assert errs[oracle_mod.BITWISE] >= 20          # enough errors to be meaningful
+    assert _two_proportion_ok(errs[oracle_mod.BITWISE], errs[oracle_mod.SPC4], 2000), errs
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each textual mutation of the oracle must fail a pin.
+# ---------------------------------------------------------------------------
+MUTATIONS = [
+    ("G sign", "float r = beta ? b - a : b + a;", "float r = beta ? b + a : b - a;"),
+    ("F uses max", "float m = ma < mb ? ma : mb;", "float m = ma > mb ? ma : mb;"),
+    ("F drops sign", "return ((a < 0.0f) != (b < 0.0f)) ? -m : m;", "return m;"),
+    ("Rate-0 uses max", "for (int i = 0; i < nv; ++i) t[i] = a[i] < 0.0f ? -a[i] : 0.0f;",
+     "for (int i = 0; i < nv; ++i) t[i] = a[i] > 0.0f ? a[i] : 0.0f;"),
+    ("combine direction", "for (int i = 0; i < h; ++i) b[i] ^= b[i + h];",
+     "for (int i = 0; i < h; ++i) b[i + h] ^= b[i];"),
+    ("SPC parity inverted", "int q = parity == 0;", "int q = parity != 0;"),
+    ("Rate-1 flips wrong bit", "ocand_t c1 = {s, 1, pen_s + a1, 0, 1, {m[0], 0, 0, 0}};",
+     "ocand_t c1 = {s, 1, pen_s + a1, 0, 1, {m[1], 0, 0, 0}};"),
+    ("REP penalties swapped", "float p0 = tree_sum(t0, nv), p1 = tree_sum(t1, nv);",
+     "float p1 = tree_sum(t0, nv), p0 = tree_sum(t1, nv);"),
+    ("selection keeps worst", "if (x->pen < y->pen) return -1;", "if (x->pen < y->pen) return 1;"),
+    ("h of zero", "static int h_of(float a) { return a < 0.0f ? 1 : 0; }",
+     "static int h_of(float a) { return a <= 0.0f ? 1 : 0; }"),
+]
+
+
+def _pins_pass(mod):
+    """A compact run of the pins above against an oracle module."""
+    rng = np.random.default_rng(99)
+    for _ in range(30):
+        N = int(rng.choice([4, 8, 16]))
+        K = int(rng.integers(1, min(N, 5) + 1))
+        fr = _random_code(rng, N, K)
+        y = rng.integers(-6, 7, N).astype(np.float32)
+        if _final_list(mod, fr, 1 << K, y, mod.BITWISE) != _brute_force(fr, y):
+            return False
+        if _fast_leaves_exhaustive(mod, fr, mod.SPC4):
+            if _final_list(mod, fr, 1 << K, y, mod.SPC4) != _brute_force(fr, y):
+                return False
+    # zero LLRs: h(0) = 0, so the all-zero word has penalty 0
+    fr = I.ga_frozen_mask(16, 8, 2.0)
+    w, p = mod.decode_list(fr, 1, np.zeros(16, np.float32), mod.SPC4)
+    if p[0] != 0 or w[0].any():
+        return False
+    fr = I.ga_frozen_mask(64, 40, 3.0)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 3.0, 4, seed=5, noiseless=True)
+    for mode in (mod.BITWISE, mod.SPC4):
+        bits, pm, ok, _ = mod.decode(fr, 4, f.llr_f32, 8, I.CRC8_POLY, mode)
+        if not np.array_equal(I.unpack_bits_lsb(bits, 32), f.payload) or pm.any():
+            return False
+    return True
+
+
+def test_pins_pass_on_the_oracle(oracle_mod):
+    assert _pins_pass(oracle_mod)
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    import importlib.util
+    src_dir = os.path.join(os.path.dirname(HERE), "oracle")
+    dst = tmp_path / "oracle_mut"
+    shutil.copytree(src_dir, dst, ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    c_file = dst / "polar_oracle.c"
+    text = c_file.read_text()
+    assert text.count(old) == 1, name
+    c_file.write_text(text.replace(old, new))
+    spec = importlib.util.spec_from_file_location("oracle_mut", dst / "__init__.py")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build(force=True)
+    assert not _pins_pass(mod), f"mutation '{name}' was not detected"
