@@ -1,0 +1,170 @@
+/*
+ * polar.h -- C ABI of the GB300 (sm_103a) list-CRC polar decoder.
+ *
+ * Method: "Fast List Decoders for Polar Codes" (Sarkis, Giard, Vardy,
+ * Thibeault, Gross). A polar code of length N = 2^n with K information
+ * positions (CRC included) is decoded by successive-cancellation list
+ * decoding with list size L over the Fast-SSC decoding tree: inner nodes
+ * apply F (Eq. (1), min-sum), G (Eq. (2)) and Combine (Eq. (3)) to every path;
+ * Rate-0, Rate-1, repetition and single-parity-check nodes are decoded
+ * directly and fork paths with the metric of Eq. (9) (Sec. III); the L best
+ * candidates survive each forking node (Algorithm 1); the output is the best
+ * path that passes the CRC (Sec. II-B).
+ *
+ * Conventions shared by every entry point:
+ *  - Bit order is natural: codeword x = u * G_N, G_N = F^{(x)n},
+ *    F = [[1,0],[1,1]] (Fig. 1). No bit-reversal permutation.
+ *  - BPSK maps bit 0 to a positive LLR: an LLR a decides 0 iff a >= 0 (Eq. (4)).
+ *  - The path metric returned is the penalty P = -PM >= 0 of Sec. III-A
+ *    (smaller is better); winners are chosen by argmin.
+ *  - K counts the CRC bits. The payload is the first k = K - crc_len
+ *    information positions in ascending index; the CRC fills the last
+ *    crc_len. CRC: MSB-first division by crc_poly (normal form, e.g.
+ *    0x04C11DB7 for CRC-32, 0x07 for CRC-8), register starts at 0, no
+ *    reflection, no final xor (the paper does not fix these, Sec. II-B).
+ *  - Payload bits are returned packed LSB-first: payload bit b is bit (b % 8)
+ *    of byte b / 8 of the frame's ceil(k/8)-byte row.
+ *  - float32 LLRs are used as given. int8 LLRs are saturated values in
+ *    [-127, 127] (-128 is read as -127); G saturates to [-127, 127] and all
+ *    penalties are exact integers.
+ *  - Device pointers are CUDA device (or managed) memory of the calling
+ *    process's current device; the caller owns every I/O buffer. Work is
+ *    enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *    runs asynchronously; an entry point returns after launching.
+ *  - Every entry point returns POLAR_OK (0) or a negative status; nothing is
+ *    thrown across the ABI. polar_strerror names a status.
+ */
+#ifndef POLAR_GB300_H
+#define POLAR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(POLAR_BUILD)
+#define POLAR_API __attribute__((visibility("default")))
+#else
+#define POLAR_API
+#endif
+
+/* A cudaStream_t, declared without the CUDA headers. */
+typedef struct CUstream_st *polar_stream_t;
+
+/* Opaque code object: the decoding schedule and device tables of one code. */
+typedef struct polar_code polar_code_t;
+
+enum polar_status {
+    POLAR_OK = 0,
+    POLAR_EINVAL = -1,        /* an argument is out of range or NULL */
+    POLAR_ENOMEM = -2,        /* host or device allocation failed */
+    POLAR_ECUDA = -3,         /* a CUDA call failed (no device, launch error, ...) */
+    POLAR_EUNSUPPORTED = -4,  /* valid request this build does not support */
+    POLAR_ETIMEDOUT = -5,     /* a bounded device or host wait ran out */
+    POLAR_EBUSY = -6          /* no room right now (serving admission) */
+};
+
+enum polar_llr_dtype { POLAR_LLR_F32 = 0, POLAR_LLR_I8 = 1 };
+
+/* polar_code_create flags. The low byte selects the node set. */
+enum polar_flags {
+    POLAR_SPC_MAX_4 = 0,            /* Rate-0, Rate-1, repetition, SPC of length <= 4
+                                       ("Dec-SPC-4", Sec. VI) -- the default */
+    POLAR_SPC_ANY = 1,              /* SPC nodes of any length, four least reliable
+                                       bits ("Dec-SPC-4+", Sec. III-D, VI) */
+    POLAR_NO_SPECIAL_NODES = 2,     /* length-one leaves only: unrolled SC-list
+                                       (Table I, "Unrolled SC-list") */
+    POLAR_HOST_ONLY = 0x100         /* build the schedule and tables on the host
+                                       only: no CUDA call, cannot decode (for
+                                       inspecting schedules without a GPU) */
+};
+
+/* Create a code object.
+ *   N            code length, a power of two, 8 <= N <= 4096.
+ *   K            information positions including the CRC, crc_len < K <= N.
+ *   frozen_mask  host array of N bytes, nonzero = frozen; exactly N-K nonzero.
+ *                Read during the call only.
+ *   crc_len      0 (no CRC: the best path wins) or 1..32.
+ *   crc_poly     generator polynomial without the x^crc_len term.
+ *   L            list size, a power of two, 1 <= L <= 32 (L = 1 is Fast-SSC
+ *                decoding, Sec. V).
+ *   flags        one node-set value, optionally | POLAR_HOST_ONLY.
+ * Builds the decoding tree (Sec. II-D: the largest Rate-0 / Rate-1 /
+ * repetition / SPC sub-tree from the root down), the unrolled operation list
+ * (Listing 2) and the CRC tables, and copies them to the current device.
+ * Errors: POLAR_EINVAL (bad N, K, mask, crc_len, flags, NULL out),
+ * POLAR_EUNSUPPORTED (L not a power of two in 1..32), POLAR_ENOMEM,
+ * POLAR_ECUDA. On error *out is set to NULL. */
+POLAR_API int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t *frozen_mask,
+                      uint32_t crc_len, uint64_t crc_poly, uint32_t L, uint32_t flags);
+
+/* Free a code object and its device tables. The caller must make sure no
+ * decode that uses it is still running (synchronise its streams first).
+ * NULL is accepted. */
+POLAR_API int polar_code_destroy(polar_code_t *code);
+
+/* List-decode n_frames frames of one code (the plain, one-code-per-launch form).
+ *   llr_dev          device, [n_frames][N] float32 (POLAR_LLR_F32) or int8
+ *                    (POLAR_LLR_I8), row-major, read only.
+ *   info_bits_dev    device, [n_frames][ceil(k/8)] bytes, written (payload of
+ *                    the winning path, LSB-first).
+ *   path_metric_dev  device, [n_frames] float, written (winning penalty).
+ *   crc_ok_dev       device, [n_frames] bytes, 1 if the winner passed the CRC
+ *                    (always 1 when crc_len = 0); may be NULL.
+ *   winner_slot_dev  device, [n_frames] int32, list slot of the winner (slots
+ *                    are numbered in (source slot, candidate) order after each
+ *                    selection); may be NULL.
+ * Re-entrant: concurrent calls on distinct streams are safe (each call takes
+ * its own scratch from the stream-ordered allocator when the code needs any).
+ * Errors: POLAR_EINVAL (NULL code/required pointer, bad dtype, host-only
+ * code), POLAR_ENOMEM (scratch), POLAR_ECUDA (launch failure). n_frames = 0
+ * is a no-op. */
+POLAR_API int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dtype,
+                      uint32_t n_frames, uint8_t *info_bits_dev, float *path_metric_dev,
+                      uint8_t *crc_ok_dev, int32_t *winner_slot_dev, polar_stream_t stream);
+
+/* A short English name for a status code (never NULL). */
+POLAR_API const char *polar_strerror(int status);
+
+/* Facts about a code object (sizes, tree statistics, launch shape). */
+typedef struct {
+    uint32_t N, K, k, L, crc_len;
+    uint32_t n_ops;          /* entries of the unrolled operation list */
+    uint32_t n_leaves;       /* leaves of the decoding tree */
+    uint32_t n_rate0, n_rate1, n_rep, n_spc;
+    uint32_t warps_per_frame[2];     /* per dtype (index = polar_llr_dtype) */
+    uint32_t frames_per_cta[2];
+    uint32_t smem_per_frame[2];      /* bytes of shared memory per frame in flight */
+    uint64_t scratch_per_frame[2];   /* bytes of global scratch per frame in flight */
+    uint32_t spill_mask[2];          /* alpha stages kept in global scratch */
+} polar_code_info_t;
+
+POLAR_API int polar_code_get_info(const polar_code_t *code, polar_code_info_t *info);
+
+/* The unrolled operation list (Listing 2) as triples (kind, N_v, first u
+ * index): kind 0 = F, 1 = G, 2 = Combine, 11 = Rate-0 leaf, 12 = Rate-1 leaf,
+ * 13 = repetition leaf, 14 = SPC leaf. ops_out holds 3*cap int32. *n_ops gets
+ * the full count; POLAR_EINVAL if cap is too small. */
+POLAR_API int polar_code_schedule(const polar_code_t *code, int32_t *ops_out, uint32_t cap, uint32_t *n_ops);
+
+/* Algorithmic operation count of one frame (the roofline numerator): one
+ * operation is one element-wise min / add / compare / select / xor on one
+ * LLR, bit word or key, counted along the schedule with the number of live
+ * paths a noiseless frame has at each node (the list fills up to L at the
+ * first forks and stays full). Pure host arithmetic. */
+POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_frame);
+
+/* Override the launch shape chosen at create time for one dtype (for the
+ * autotuner and tests). warps_per_frame in {1,2,4}; smem_budget caps the
+ * shared memory of one frame (0 = default), larger alpha stages move to
+ * global scratch to meet it. POLAR_EINVAL if the shape cannot hold the code. */
+POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
+                          uint32_t smem_budget);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLAR_GB300_H */

@@ -55,7 +55,8 @@
  *      (Rate-0, repetition) is the pairwise tree s[i] = x[i] + x[i + n/2]
  *      applied until one value is left. The new penalty is old + increment.
  *  R9  int8 LLRs: F exact, G saturated to [-127, 127], penalties are exact
- *      integers (carried here in float, exact below 2^24).
+ *      integers (carried here in float, exact below 2^24). An input of -128
+ *      is read as -127 so that every value has a representable negation.
  *  R10 CRC: MSB-first division, register starts at 0, no reflection, no
  *      final xor, over the payload bits in ascending information index; the
  *      CRC occupies the last crc_len information positions.
@@ -392,7 +393,7 @@ static void run_list(olist_t *ls, const ocode_t *c, const void *llr) {
     float *ch = A(p0, c->n);
     if (c->dtype == OR_I8) {
         const int8_t *q = (const int8_t *)llr;
-        for (int i = 0; i < c->N; ++i) ch[i] = (float)q[i];
+        for (int i = 0; i < c->N; ++i) ch[i] = q[i] < -127 ? -127.0f : (float)q[i];  /* R9 */
     } else {
         memcpy(ch, llr, sizeof(float) * c->N);
     }

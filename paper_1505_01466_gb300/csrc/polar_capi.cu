@@ -1,0 +1,440 @@
+// polar_capi.cu -- host side of the C ABI declared in include/polar.h.
+//
+// polar_code_create turns a code description into what the decode kernel
+// runs: the Fast-SSC decoding tree flattened into an unrolled operation list
+// (Sec. II-D, Listing 2), the information positions, the CRC syndrome tables
+// and a launch shape (warps per frame, frames per CTA, which alpha stages
+// sit in shared memory and which spill to global scratch).
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/polar.h"
+#include "polar_internal.h"
+
+using namespace polar;
+
+struct polar_code {
+    uint32_t N, n, K, k, L, crc_len, flags;
+    uint64_t crc_poly;
+    std::vector<uint8_t> frozen;
+    std::vector<uint32_t> ops;          // unrolled schedule (device encoding)
+    std::vector<int32_t> sched;         // (kind, N_v, start) triples
+    std::vector<uint16_t> info;         // information positions
+    std::vector<uint32_t> syn;          // [N/8][256]
+    uint32_t n_leaves = 0, n_r0 = 0, n_r1 = 0, n_rep = 0, n_spc = 0;
+    bool host_only = false;
+    int device = -1;
+    int sm_count = 0;
+    uint32_t *d_ops = nullptr;
+    uint32_t *d_syn = nullptr;
+    uint16_t *d_info = nullptr;
+    LaunchShape shape[2];
+};
+
+namespace {
+
+uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
+uint64_t al256(uint64_t x) { return (x + 255u) & ~uint64_t(255); }
+
+// ---- decoding tree (Sec. II-D) ----------------------------------------------
+// Top down, first match wins: all frozen -> Rate-0; none frozen -> Rate-1;
+// only the last bit information (N_v >= 2) -> repetition; only the first bit
+// frozen (N_v >= 4; N_v <= 4 unless SPC_ANY) -> SPC; otherwise split.
+struct TreeBuilder {
+    const polar_code *c;
+    std::vector<uint32_t> prefix;   // prefix[i] = frozen count in [0, i)
+    std::vector<uint32_t> ops;
+    std::vector<int32_t> sched;
+    uint32_t leaves = 0, r0 = 0, r1 = 0, rep = 0, spc = 0;
+
+    uint32_t nfrozen(uint32_t a, uint32_t len) const { return prefix[a + len] - prefix[a]; }
+
+    uint32_t classify(int j, uint32_t start) const {
+        const uint32_t nv = 1u << j;
+        const uint32_t mode = c->flags & 0xFFu;
+        if (mode == POLAR_NO_SPECIAL_NODES && nv > 1) return 0;
+        const uint32_t nf = nfrozen(start, nv);
+        if (nf == nv) return OP_R0;
+        if (nf == 0) return OP_R1;
+        if (nv >= 2 && nf == nv - 1 && !c->frozen[start + nv - 1]) return OP_REP;
+        if (nv >= 4 && nf == 1 && c->frozen[start] && (mode == POLAR_SPC_ANY || nv <= 4)) return OP_SPC;
+        return 0;
+    }
+
+    void emit(uint32_t kind, int j, uint32_t dest, uint32_t start) {
+        ops.push_back(op_make(kind, (uint32_t)j, dest));
+        static const int32_t ext[7] = {0, 1, 2, 11, 12, 13, 14};
+        sched.push_back(ext[kind]);
+        sched.push_back(1 << j);
+        sched.push_back((int32_t)start);
+    }
+
+    void build(int j, uint32_t start, uint32_t dest) {
+        const uint32_t t = classify(j, start);
+        if (t) {
+            emit(t, j, dest, start);
+            ++leaves;
+            r0 += t == OP_R0; r1 += t == OP_R1; rep += t == OP_REP; spc += t == OP_SPC;
+            return;
+        }
+        const uint32_t h = 1u << (j - 1);
+        emit(OP_F, j, 0, start);
+        build(j - 1, start, 0);
+        emit(OP_G, j, 0, start);
+        build(j - 1, start + h, 1);
+        emit(OP_COMB, j, dest, start);
+    }
+};
+
+// ---- CRC syndrome of every codeword bit ------------------------------------
+// The register left after feeding the K information bits of u = x G_N
+// (payload then CRC, MSB first, start 0) is zero iff the CRC matches, and it is
+// linear in x. Column t is the register for the unit vector at information
+// index t; codeword bit i contributes the columns of every information
+// position p of row i of G_N, i.e. every p with (p & ~i) == 0.
+void build_syndrome(polar_code *c) {
+    const uint32_t K = c->K, N = c->N, cl = c->crc_len;
+    const uint32_t mask = cl >= 32 ? 0xffffffffu : ((1u << cl) - 1u);
+    const uint32_t poly = (uint32_t)c->crc_poly & mask;
+    std::vector<uint32_t> col(K, 0u);
+    uint32_t reg = poly;                              // unit vector at index K-1
+    for (int t = (int)K - 1; t >= 0; --t) {
+        col[t] = reg;
+        const uint32_t top = (reg >> (cl - 1)) & 1u;  // one more zero bit fed after it
+        reg = ((reg << 1) & mask) ^ (top ? poly : 0u);
+    }
+    std::vector<uint32_t> T(N, 0u);
+    for (uint32_t i = 0; i < N; ++i) {
+        uint32_t s = 0;
+        for (uint32_t t = 0; t < K; ++t)
+            if ((c->info[t] & ~i) == 0) s ^= col[t];
+        T[i] = s;
+    }
+    c->syn.assign((size_t)(N / 8) * 256, 0u);
+    for (uint32_t b = 0; b < N / 8; ++b)
+        for (uint32_t v = 0; v < 256; ++v) {
+            uint32_t s = 0;
+            for (int e = 0; e < 8; ++e)
+                if ((v >> e) & 1u) s ^= T[8 * b + e];
+            c->syn[(size_t)b * 256 + v] = s;
+        }
+}
+
+// ---- memory layout of one frame --------------------------------------------
+bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &lay) {
+    std::memset(&lay, 0, sizeof(lay));
+    const uint32_t N = 1u << n;
+    uint32_t fixed = 0;
+    fixed += al16(N * es);                                             // chan
+    for (uint32_t j = 0; j < n; ++j) fixed += al16(L * 4u * (uint32_t)beta_words((int)j));  // BL
+    fixed += al16(L * 4u * (uint32_t)beta_words((int)n));              // BR
+    fixed += 4 * al16(L * (n + 1));                                    // idx, bidx x2
+    fixed += 2 * al16(L * 4u);                                         // pen x2
+    fixed += al16(std::max(8u * L, 8u) * 8u);                          // keys
+    fixed += al16(L * 8u);                                             // surv
+    fixed += al16(L * 16u);                                            // cinfo
+    fixed += al16(4u * (uint32_t)beta_words((int)n));                  // ubuf
+    std::vector<uint32_t> abytes(n);
+    uint32_t total = fixed;
+    for (uint32_t j = 0; j < n; ++j) {
+        abytes[j] = al16(L * (1u << j) * es);
+        total += abytes[j];
+    }
+    uint32_t spill = 0;
+    for (int j = (int)n - 1; j >= 0 && total > budget; --j) {
+        spill |= 1u << j;
+        total -= abytes[j];
+    }
+    if (total > budget) return false;
+    uint32_t off = 0;
+    lay.chan = off; off += al16(N * es);
+    uint64_t goff = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        if ((spill >> j) & 1u) {
+            lay.galpha[j] = goff;
+            goff = al256(goff + abytes[j]);
+        } else {
+            lay.alpha[j] = off;
+            off += abytes[j];
+        }
+    }
+    for (uint32_t j = 0; j < n; ++j) { lay.bl[j] = off; off += al16(L * 4u * (uint32_t)beta_words((int)j)); }
+    lay.br = off; off += al16(L * 4u * (uint32_t)beta_words((int)n));
+    for (int b = 0; b < 2; ++b) { lay.idx[b] = off; off += al16(L * (n + 1)); }
+    for (int b = 0; b < 2; ++b) { lay.bidx[b] = off; off += al16(L * (n + 1)); }
+    for (int b = 0; b < 2; ++b) { lay.pen[b] = off; off += al16(L * 4u); }
+    lay.key = off; off += al16(std::max(8u * L, 8u) * 8u);
+    lay.surv = off; off += al16(L * 8u);
+    lay.cinfo = off; off += al16(L * 16u);
+    lay.ubuf = off; off += al16(4u * (uint32_t)beta_words((int)n));
+    lay.bytes = off;
+    lay.spill_mask = spill;
+    lay.gbytes = goff;
+    return true;
+}
+
+constexpr uint32_t kMaxSmemPerCta = 232448;   // 227 KB opt-in per CTA on sm_100-class parts
+
+bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget, LaunchShape &sh) {
+    if (warps != 1 && warps != 2 && warps != 4) return false;
+    const uint32_t es = dtype == POLAR_LLR_I8 ? 1u : 4u;
+    const uint32_t gpc = 4u / warps;
+    if (budget == 0) {
+        // Default: aim for 8 warps per SM from shared memory alone.
+        const uint32_t groups_per_sm = std::max(2u, 8u / warps);
+        budget = (kMaxSmemPerCta / groups_per_sm) & ~15u;
+    }
+    budget = std::min(budget, kMaxSmemPerCta / gpc);
+    Layout lay;
+    if (!build_layout(c->n, c->L, es, budget, lay)) return false;
+    sh.warps = (int)warps;
+    sh.groups_per_cta = (int)gpc;
+    sh.threads = 128;
+    sh.smem = lay.bytes * gpc;
+    sh.lay = lay;
+    return sh.smem <= kMaxSmemPerCta;
+}
+
+uint32_t default_warps(const polar_code *c) {
+    const uint64_t ln = (uint64_t)c->L * c->N;
+    if (ln >= 16384) return 4;
+    if (ln >= 2048) return 2;
+    return 1;
+}
+
+void free_device(polar_code *c) {
+    if (c->d_ops) cudaFree(c->d_ops);
+    if (c->d_syn) cudaFree(c->d_syn);
+    if (c->d_info) cudaFree(c->d_info);
+    c->d_ops = nullptr;
+    c->d_syn = nullptr;
+    c->d_info = nullptr;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &v) {
+    cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *polar_strerror(int status) {
+    switch (status) {
+        case POLAR_OK: return "ok";
+        case POLAR_EINVAL: return "invalid argument";
+        case POLAR_ENOMEM: return "out of memory";
+        case POLAR_ECUDA: return "CUDA error";
+        case POLAR_EUNSUPPORTED: return "unsupported";
+        case POLAR_ETIMEDOUT: return "timed out";
+        case POLAR_EBUSY: return "busy";
+        default: return "unknown status";
+    }
+}
+
+int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t *frozen_mask, uint32_t crc_len,
+                      uint64_t crc_poly, uint32_t L, uint32_t flags) {
+    if (!out) return POLAR_EINVAL;
+    *out = nullptr;
+    if (!frozen_mask) return POLAR_EINVAL;
+    if (N < 8 || N > 4096 || (N & (N - 1))) return POLAR_EINVAL;
+    if (K > N || crc_len > 32 || (crc_len > 0 && crc_len >= K) || (crc_len == 0 && K == 0)) return POLAR_EINVAL;
+    if ((flags & ~0x1FFu) != 0 || (flags & 0xFFu) > POLAR_NO_SPECIAL_NODES) return POLAR_EINVAL;
+    if (L < 1 || L > (uint32_t)kMaxL || (L & (L - 1))) return POLAR_EUNSUPPORTED;
+    uint32_t nf = 0;
+    for (uint32_t i = 0; i < N; ++i) nf += frozen_mask[i] ? 1u : 0u;
+    if (nf != N - K) return POLAR_EINVAL;
+
+    polar_code *c = new (std::nothrow) polar_code();
+    if (!c) return POLAR_ENOMEM;
+    c->N = N;
+    c->n = 0;
+    while ((1u << c->n) < N) ++c->n;
+    c->K = K;
+    c->k = K - crc_len;
+    c->L = L;
+    c->crc_len = crc_len;
+    c->crc_poly = crc_poly;
+    c->flags = flags;
+    c->frozen.assign(frozen_mask, frozen_mask + N);
+    for (uint32_t i = 0; i < N; ++i) c->frozen[i] = frozen_mask[i] ? 1 : 0;
+    for (uint32_t i = 0; i < N; ++i)
+        if (!c->frozen[i]) c->info.push_back((uint16_t)i);
+
+    TreeBuilder tb;
+    tb.c = c;
+    tb.prefix.assign(N + 1, 0u);
+    for (uint32_t i = 0; i < N; ++i) tb.prefix[i + 1] = tb.prefix[i] + c->frozen[i];
+    tb.build((int)c->n, 0, 1);
+    c->ops = std::move(tb.ops);
+    c->sched = std::move(tb.sched);
+    c->n_leaves = tb.leaves;
+    c->n_r0 = tb.r0;
+    c->n_r1 = tb.r1;
+    c->n_rep = tb.rep;
+    c->n_spc = tb.spc;
+    if (crc_len > 0) build_syndrome(c);
+    for (int d = 0; d < 2; ++d) {
+        if (!make_shape(c, d, default_warps(c), 0, c->shape[d])) {
+            delete c;
+            return POLAR_EUNSUPPORTED;
+        }
+    }
+
+    c->host_only = (flags & POLAR_HOST_ONLY) != 0;
+    if (!c->host_only) {
+        if (cudaGetDevice(&c->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+            delete c;
+            return POLAR_ECUDA;
+        }
+        cudaError_t e = upload(&c->d_ops, c->ops);
+        if (e == cudaSuccess) e = upload(&c->d_info, c->info);
+        if (e == cudaSuccess) e = upload(&c->d_syn, c->syn);
+        if (e != cudaSuccess) {
+            free_device(c);
+            delete c;
+            return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
+        }
+    }
+    *out = c;
+    return POLAR_OK;
+}
+
+int polar_code_destroy(polar_code_t *code) {
+    if (!code) return POLAR_OK;
+    free_device(code);
+    delete code;
+    return POLAR_OK;
+}
+
+int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dtype, uint32_t n_frames,
+                      uint8_t *info_bits_dev, float *path_metric_dev, uint8_t *crc_ok_dev, int32_t *winner_slot_dev,
+                      polar_stream_t stream) {
+    if (!code || code->host_only) return POLAR_EINVAL;
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const LaunchShape &sh = code->shape[llr_dtype];
+    int occ = occupancy(llr_dtype, sh);
+    if (occ <= 0) return POLAR_ECUDA;
+    const uint64_t groups_needed = n_frames;
+    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
+    const uint64_t need_ctas = (groups_needed + sh.groups_per_cta - 1) / sh.groups_per_cta;
+    if (grid > need_ctas) grid = need_ctas;
+
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.ops = code->d_ops;
+    p.n_ops = (int)code->ops.size();
+    p.N = (int)code->N;
+    p.n = (int)code->n;
+    p.L = (int)code->L;
+    p.K = (int)code->K;
+    p.k = (int)code->k;
+    p.crc_len = (int)code->crc_len;
+    p.llr = llr_dev;
+    p.bits = info_bits_dev;
+    p.kb = (int)((code->k + 7) / 8);
+    p.pm = path_metric_dev;
+    p.ok = crc_ok_dev;
+    p.slot = winner_slot_dev;
+    p.syn = code->d_syn;
+    p.info = code->d_info;
+    p.n_frames = n_frames;
+    p.groups_per_cta = sh.groups_per_cta;
+    p.lay = sh.lay;
+
+    void *scratch = nullptr;
+    if (sh.lay.gbytes > 0) {
+        const size_t bytes = (size_t)grid * sh.groups_per_cta * sh.lay.gbytes;
+        if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) return POLAR_ENOMEM;
+        p.scratch = (uint8_t *)scratch;
+    }
+    cudaError_t e = launch_decode(llr_dtype, sh, p, (int)grid, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
+    if (!c || !info) return POLAR_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->N = c->N;
+    info->K = c->K;
+    info->k = c->k;
+    info->L = c->L;
+    info->crc_len = c->crc_len;
+    info->n_ops = (uint32_t)c->ops.size();
+    info->n_leaves = c->n_leaves;
+    info->n_rate0 = c->n_r0;
+    info->n_rate1 = c->n_r1;
+    info->n_rep = c->n_rep;
+    info->n_spc = c->n_spc;
+    for (int d = 0; d < 2; ++d) {
+        info->warps_per_frame[d] = (uint32_t)c->shape[d].warps;
+        info->frames_per_cta[d] = (uint32_t)c->shape[d].groups_per_cta;
+        info->smem_per_frame[d] = c->shape[d].lay.bytes;
+        info->scratch_per_frame[d] = c->shape[d].lay.gbytes;
+        info->spill_mask[d] = c->shape[d].lay.spill_mask;
+    }
+    return POLAR_OK;
+}
+
+int polar_code_schedule(const polar_code_t *c, int32_t *ops_out, uint32_t cap, uint32_t *n_ops) {
+    if (!c || !n_ops) return POLAR_EINVAL;
+    const uint32_t cnt = (uint32_t)(c->sched.size() / 3);
+    *n_ops = cnt;
+    if (!ops_out || cap < cnt) return POLAR_EINVAL;
+    std::memcpy(ops_out, c->sched.data(), c->sched.size() * sizeof(int32_t));
+    return POLAR_OK;
+}
+
+int polar_code_op_count(const polar_code_t *c, uint64_t *ops_per_frame) {
+    if (!c || !ops_per_frame) return POLAR_EINVAL;
+    uint64_t tot = 0, la = 1;
+    uint64_t lg = 0;
+    while ((1u << lg) < c->L) ++lg;
+    if (lg == 0) lg = 1;
+    for (uint32_t op : c->ops) {
+        const uint32_t kind = op_kind(op);
+        const uint64_t nv = 1ull << op_stage(op);
+        switch (kind) {
+            case OP_F:
+            case OP_G: tot += 2 * (nv / 2) * la; break;
+            case OP_COMB: tot += std::max<uint64_t>(1, nv / 64) * la; break;
+            case OP_R0: tot += 2 * nv * la; break;
+            default: {
+                uint64_t C;
+                if (kind == OP_R1) { tot += 3 * nv * la; C = nv == 1 ? 2 : 4; }
+                else if (kind == OP_REP) { tot += 4 * nv * la; C = 2; }
+                else { tot += 5 * nv * la; C = c->L == 2 ? 2 : 8; }
+                if (C * la > c->L) tot += C * la * lg;
+                la = std::min<uint64_t>(c->L, C * la);
+            }
+        }
+    }
+    tot += (uint64_t)c->L * c->N * c->n / 32 + (uint64_t)c->L * c->K;
+    *ops_per_frame = tot;
+    return POLAR_OK;
+}
+
+int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_frame, uint32_t smem_budget) {
+    if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
+    LaunchShape sh;
+    if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh)) return POLAR_EINVAL;
+    c->shape[llr_dtype] = sh;
+    return POLAR_OK;
+}
+
+}  // extern "C"

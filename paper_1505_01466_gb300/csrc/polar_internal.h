@@ -1,0 +1,90 @@
+// polar_internal.h -- shared between the host runtime (polar_capi.cu) and the
+// decode kernels (polar_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace polar {
+
+constexpr int kMaxLogN = 12;   // N <= 4096
+constexpr int kMaxL = 32;      // one warp lane per path in the final pick
+
+// Operation kinds of the unrolled schedule (Listing 2 of the paper).
+enum OpKind : uint32_t {
+    OP_F = 0,      // alpha_l = F(alpha_v)                      Eq. (1)
+    OP_G = 1,      // alpha_r = G(alpha_v, beta_l)              Eq. (2)
+    OP_COMB = 2,   // beta_v = [beta_l ^ beta_r, beta_r]        Eq. (3)
+    OP_R0 = 3,     // Rate-0 leaf                               Sec. III-B
+    OP_R1 = 4,     // Rate-1 leaf                               Sec. III-C
+    OP_REP = 5,    // repetition leaf                           Sec. III-E
+    OP_SPC = 6     // single-parity-check leaf                  Sec. III-D
+};
+
+// One schedule entry: kind | stage j << 4 | dest << 8.
+//   j     stage of the node (N_v = 2^j)
+//   dest  where the node's beta goes: 0 = left-child buffer BL[j],
+//         1 = right-child / root buffer BR
+__host__ __device__ inline uint32_t op_make(uint32_t kind, uint32_t j, uint32_t dest) {
+    return kind | (j << 4) | (dest << 8);
+}
+__host__ __device__ inline uint32_t op_kind(uint32_t op) { return op & 15u; }
+__host__ __device__ inline int op_stage(uint32_t op) { return (int)((op >> 4) & 15u); }
+__host__ __device__ inline int op_dest(uint32_t op) { return (int)((op >> 8) & 1u); }
+
+// Bit-packed beta: words per path for a node of 2^j bits.
+__host__ __device__ inline int beta_words(int j) { return j >= 5 ? 1 << (j - 5) : 1; }
+
+// Per-frame memory layout. Byte offsets inside one frame-group's shared
+// memory region, or inside its global scratch region for spilled stages.
+struct Layout {
+    uint32_t chan;                 // channel LLRs (stage n), N elements
+    uint32_t alpha[kMaxLogN];      // stage j < n: L rows of 2^j elements
+    uint32_t bl[kMaxLogN];         // left-child beta of stage j: L rows of beta_words(j)
+    uint32_t br;                   // right/root beta: L rows of beta_words(n)
+    uint32_t idx[2];               // alpha stage -> physical row, [L][n+1] bytes, double buffered
+    uint32_t bidx[2];              // left-beta stage -> physical row, same shape
+    uint32_t pen[2];               // penalties, [L] float or int32, double buffered
+    uint32_t key;                  // candidate keys, 8L uint64
+    uint32_t surv;                 // survivor keys in new-slot order, L uint64
+    uint32_t cinfo;                // per-source candidate data, L x 16 bytes
+    uint32_t ubuf;                 // winner's u vector, beta_words(n) words
+    uint32_t bytes;                // total per group (multiple of 16)
+    uint32_t spill_mask;           // bit j set: alpha stage j lives in global scratch
+    uint32_t pad_;
+    uint64_t galpha[kMaxLogN];     // offsets inside the group's global scratch
+    uint64_t gbytes;               // global scratch bytes per group
+};
+
+struct Params {
+    const uint32_t *ops;
+    int n_ops;
+    int N, n, L, K, k, crc_len;
+    const void *llr;               // [n_frames][N]
+    uint8_t *bits;                 // [n_frames][kb]
+    int kb;
+    float *pm;
+    uint8_t *ok;
+    int32_t *slot;
+    const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
+    const uint16_t *info;          // [K] information positions, ascending
+    uint32_t n_frames;
+    uint8_t *scratch;              // global scratch (spilled stages), gbytes per group
+    int groups_per_cta;
+    Layout lay;
+};
+
+struct LaunchShape {
+    int warps;                     // warps per frame group (1, 2, 4)
+    int groups_per_cta;
+    int threads;                   // per CTA
+    uint32_t smem;                 // dynamic shared memory per CTA
+    Layout lay;
+};
+
+// Launch one decode (kernels are instantiated for float / int8 and 1, 2, 4 warps).
+cudaError_t launch_decode(int dtype, const LaunchShape &shape, const Params &p, int grid,
+                          cudaStream_t stream);
+// Resident CTAs per SM for a shape (0 if it cannot launch).
+int occupancy(int dtype, const LaunchShape &shape);
+}  // namespace polar

@@ -1,0 +1,183 @@
+"""Thin ctypes binding of ``libpolar_gb300.so`` (C ABI in include/polar.h).
+
+Argument marshalling only: every step of the decode runs in the CUDA
+kernels behind the C ABI. PyTorch supplies device memory and streams. There
+is no CPU fallback -- if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpolar_gb300.so")
+
+POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
+POLAR_EUNSUPPORTED, POLAR_ETIMEDOUT, POLAR_EBUSY = -4, -5, -6
+LLR_F32, LLR_I8 = 0, 1
+SPC_MAX_4, SPC_ANY, NO_SPECIAL_NODES, HOST_ONLY = 0, 1, 2, 0x100
+
+# Every symbol include/polar.h declares.
+EXPORTED = [
+    "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror",
+    "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
+]
+
+
+class PolarError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib().polar_strerror(status).decode()} ({status})")
+
+
+class CodeInfo(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_uint32), ("K", ctypes.c_uint32), ("k", ctypes.c_uint32), ("L", ctypes.c_uint32),
+        ("crc_len", ctypes.c_uint32), ("n_ops", ctypes.c_uint32), ("n_leaves", ctypes.c_uint32),
+        ("n_rate0", ctypes.c_uint32), ("n_rate1", ctypes.c_uint32), ("n_rep", ctypes.c_uint32),
+        ("n_spc", ctypes.c_uint32), ("warps_per_frame", ctypes.c_uint32 * 2),
+        ("frames_per_cta", ctypes.c_uint32 * 2), ("smem_per_frame", ctypes.c_uint32 * 2),
+        ("scratch_per_frame", ctypes.c_uint64 * 2), ("spill_mask", ctypes.c_uint32 * 2),
+    ]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built; run paper_1505_01466_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        lib.polar_code_create.argtypes = [ctypes.POINTER(vp), u32, u32, vp, u32, u64, u32, u32]
+        lib.polar_code_destroy.argtypes = [vp]
+        lib.polar_list_decode.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
+        lib.polar_strerror.argtypes = [i32]
+        lib.polar_strerror.restype = ctypes.c_char_p
+        lib.polar_code_get_info.argtypes = [vp, ctypes.POINTER(CodeInfo)]
+        lib.polar_code_schedule.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
+        lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
+        lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32]
+        for name in EXPORTED:
+            if name != "polar_strerror":
+                getattr(lib, name).restype = i32
+        _LIB = lib
+    return _LIB
+
+
+def load_library():
+    """Load the C-ABI library (raises if it is not built)."""
+    return _lib()
+
+
+def _check(status: int, what: str):
+    if status != POLAR_OK:
+        raise PolarError(status, what)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class PolarCode:
+    """A polar-CRC code prepared for list decoding on the GPU.
+
+    frozen_mask: N bytes, nonzero = frozen. crc_len / crc_poly: the outer
+    CRC (MSB-first, register starts at 0). L: list size (power of two <= 32).
+    mode: SPC_MAX_4 (default), SPC_ANY or NO_SPECIAL_NODES.
+    """
+
+    def __init__(self, frozen_mask, crc_len: int = 0, crc_poly: int = 0, L: int = 8,
+                 mode: int = SPC_MAX_4, host_only: bool = False):
+        mask = np.ascontiguousarray(np.asarray(frozen_mask).astype(np.uint8) != 0, dtype=np.uint8)
+        self.N = int(mask.size)
+        self.K = int((mask == 0).sum())
+        self.crc_len = int(crc_len)
+        self.k = self.K - self.crc_len
+        self.L = int(L)
+        self.frozen = mask
+        flags = int(mode) | (HOST_ONLY if host_only else 0)
+        h = ctypes.c_void_p()
+        st = _lib().polar_code_create(ctypes.byref(h), self.N, self.K, mask.ctypes.data_as(ctypes.c_void_p),
+                                      self.crc_len, int(crc_poly), self.L, flags)
+        _check(st, "polar_code_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().polar_code_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        ci = CodeInfo()
+        _check(_lib().polar_code_get_info(self._h, ctypes.byref(ci)), "polar_code_get_info")
+        out = {}
+        for name, _ in CodeInfo._fields_:
+            v = getattr(ci, name)
+            out[name] = list(v) if hasattr(v, "__len__") else int(v)
+        return out
+
+    def schedule(self):
+        n = ctypes.c_uint32(0)
+        _lib().polar_code_schedule(self._h, None, 0, ctypes.byref(n))
+        buf = np.zeros(3 * max(n.value, 1), dtype=np.int32)
+        _check(_lib().polar_code_schedule(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value,
+                                          ctypes.byref(n)), "polar_code_schedule")
+        return [tuple(int(v) for v in buf[3 * i: 3 * i + 3]) for i in range(n.value)]
+
+    def op_count(self) -> int:
+        v = ctypes.c_uint64(0)
+        _check(_lib().polar_code_op_count(self._h, ctypes.byref(v)), "polar_code_op_count")
+        return int(v.value)
+
+    def set_launch(self, dtype: int, warps_per_frame: int, smem_budget: int = 0):
+        _check(_lib().polar_code_set_launch(self._h, dtype, warps_per_frame, smem_budget), "polar_code_set_launch")
+
+    def decode_into(self, llr, bits, pm, ok=None, slot=None, stream=None):
+        """Enqueue a decode of ``llr`` ([F, N] float32 or int8 CUDA tensor)."""
+        import torch
+        if llr.dtype == torch.float32:
+            dt = LLR_F32
+        elif llr.dtype == torch.int8:
+            dt = LLR_I8
+        else:
+            raise TypeError("llr must be float32 or int8")
+        if not llr.is_cuda or not llr.is_contiguous() or llr.shape[-1] != self.N:
+            raise ValueError("llr must be a contiguous CUDA tensor [F, N]")
+        F = llr.numel() // self.N
+        st = _lib().polar_list_decode(
+            self._h, ctypes.c_void_p(llr.data_ptr()), dt, F,
+            ctypes.c_void_p(bits.data_ptr()), ctypes.c_void_p(pm.data_ptr()),
+            ctypes.c_void_p(ok.data_ptr() if ok is not None else 0),
+            ctypes.c_void_p(slot.data_ptr() if slot is not None else 0), _stream_handle(stream))
+        _check(st, "polar_list_decode")
+
+    def decode(self, llr, stream=None):
+        """Decode; returns (payload bits [F, ceil(k/8)] uint8, penalty [F], crc_ok [F], slot [F])."""
+        import torch
+        F = llr.numel() // self.N
+        dev = llr.device
+        bits = torch.empty((F, (self.k + 7) // 8), dtype=torch.uint8, device=dev)
+        pm = torch.empty(F, dtype=torch.float32, device=dev)
+        ok = torch.empty(F, dtype=torch.uint8, device=dev)
+        slot = torch.empty(F, dtype=torch.int32, device=dev)
+        self.decode_into(llr, bits, pm, ok, slot, stream)
+        return bits, pm, ok, slot

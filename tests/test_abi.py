@@ -1,0 +1,125 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, validates its arguments, and builds the same decoding
+schedule as the oracle (host code only, POLAR_HOST_ONLY codes)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1505_01466_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def polar():
+    from paper_1505_01466_gb300 import build
+    build.build()
+    import paper_1505_01466_gb300.polar as polar
+    polar.load_library()
+    return polar
+
+
+def _declared_symbols():
+    syms = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            syms |= set(re.findall(r"POLAR_API\s+[\w\s\*]*?\b(polar_\w+)\s*\(", text))
+    return syms
+
+
+def test_library_exports_every_declared_symbol(polar):
+    lib = polar.load_library()
+    declared = _declared_symbols()
+    assert "polar_list_decode" in declared and "polar_code_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(polar.EXPORTED)
+
+
+def test_strerror(polar):
+    lib = polar.load_library()
+    for st in range(0, -7, -1):
+        assert lib.polar_strerror(st)
+    assert lib.polar_strerror(-99) == b"unknown status"
+
+
+def _create(polar, N, K, mask, crc_len=0, poly=0, L=4, flags=0):
+    h = ctypes.c_void_p()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    st = polar.load_library().polar_code_create(ctypes.byref(h), N, K, m.ctypes.data_as(ctypes.c_void_p),
+                                               crc_len, poly, L, flags | polar.HOST_ONLY)
+    if st == 0:
+        polar.load_library().polar_code_destroy(h)
+    else:
+        assert not h.value
+    return st
+
+
+def test_create_validation(polar):
+    fr = I.ga_frozen_mask(64, 32, 2.0)
+    assert _create(polar, 64, 32, fr) == polar.POLAR_OK
+    assert _create(polar, 63, 32, fr[:63]) == polar.POLAR_EINVAL      # not a power of two
+    assert _create(polar, 4, 2, fr[:4]) == polar.POLAR_EINVAL          # N < 8
+    assert _create(polar, 64, 31, fr) == polar.POLAR_EINVAL            # mask has N-K ones
+    assert _create(polar, 64, 32, fr, crc_len=32) == polar.POLAR_EINVAL  # crc_len >= K
+    assert _create(polar, 64, 32, fr, crc_len=33) == polar.POLAR_EINVAL
+    assert _create(polar, 64, 32, fr, L=3) == polar.POLAR_EUNSUPPORTED
+    assert _create(polar, 64, 32, fr, L=64) == polar.POLAR_EUNSUPPORTED
+    assert _create(polar, 64, 32, fr, flags=7) == polar.POLAR_EINVAL
+    h = ctypes.c_void_p()
+    assert polar.load_library().polar_code_create(None, 64, 32, fr.ctypes.data_as(ctypes.c_void_p), 0, 0, 4, 0) \
+        == polar.POLAR_EINVAL
+    assert polar.load_library().polar_code_create(ctypes.byref(h), 64, 32, None, 0, 0, 4, 0) == polar.POLAR_EINVAL
+    assert polar.load_library().polar_code_destroy(None) == polar.POLAR_OK
+
+
+def test_decode_rejects_host_only_and_bad_args(polar):
+    fr = I.ga_frozen_mask(64, 32, 2.0)
+    code = polar.PolarCode(fr, 8, I.CRC8_POLY, 4, host_only=True)
+    lib = polar.load_library()
+    st = lib.polar_list_decode(code.handle, ctypes.c_void_p(16), 0, 1, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                               None, None, None)
+    assert st == polar.POLAR_EINVAL
+    assert lib.polar_list_decode(None, None, 0, 1, None, None, None, None, None) == polar.POLAR_EINVAL
+
+
+@pytest.mark.parametrize("mode", ["SPC_MAX_4", "SPC_ANY", "NO_SPECIAL_NODES"])
+def test_schedule_matches_oracle(polar, oracle_mod, mode):
+    omode = {"SPC_MAX_4": oracle_mod.SPC4, "SPC_ANY": oracle_mod.SPC_ANY,
+             "NO_SPECIAL_NODES": oracle_mod.BITWISE}[mode]
+    rng = np.random.default_rng(8)
+    for _ in range(30):
+        N = int(rng.choice([8, 16, 64, 256, 1024]))
+        K = int(rng.integers(1, N + 1))
+        fr = np.ones(N, np.uint8)
+        fr[rng.choice(N, K, replace=False)] = 0
+        code = polar.PolarCode(fr, 0, 0, 4, mode=getattr(polar, mode), host_only=True)
+        assert code.schedule() == oracle_mod.schedule(fr, omode)
+    for N, K, d, r in [(256, 128, 2.0, 120 / 256), (1024, 860, 4.0, 828 / 1024), (2048, 1723, 4.0, 1691 / 2048)]:
+        fr = I.ga_frozen_mask(N, K, d, r)
+        code = polar.PolarCode(fr, 32, I.CRC32_POLY, 32, mode=getattr(polar, mode), host_only=True)
+        assert code.schedule() == oracle_mod.schedule(fr, omode)
+
+
+def test_code_info_and_op_count(polar):
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    code = polar.PolarCode(fr, 32, I.CRC32_POLY, 32, host_only=True)
+    info = code.info()
+    assert info["n_leaves"] == info["n_rate0"] + info["n_rate1"] + info["n_rep"] + info["n_spc"]
+    assert info["k"] == 1691
+    # every leaf is one entry, every inner node three (F, G, Combine)
+    assert info["n_ops"] == info["n_leaves"] + 3 * (info["n_leaves"] - 1)
+    # shared memory per frame fits a CTA; larger stages spilled to global scratch
+    for d in (0, 1):
+        assert info["smem_per_frame"][d] * info["frames_per_cta"][d] <= 232448
+    assert code.op_count() > 2048 * 11  # at least one path's F/G work
+    # a smaller budget moves more alpha stages to global scratch
+    code.set_launch(1, 4, 40000)
+    assert code.info()["smem_per_frame"][1] <= 40000
+    assert code.info()["spill_mask"][1] != 0
+    with pytest.raises(polar.PolarError):
+        code.set_launch(1, 3, 0)

@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA decoder (through the C ABI) against the CPU oracle.
+
+Payload bits, winning slot and CRC flag must be identical; the penalty must
+be identical for int8 LLRs (exact integers) and within 1e-5 relative for
+float32 (the float sums follow the same canonical order on both sides, so
+they are expected to be identical too).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1505_01466_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+NT = os.cpu_count() or 1
+MODES = {"SPC_MAX_4": 0, "SPC_ANY": 1, "NO_SPECIAL_NODES": 2}
+OMODE = {0: 0, 1: 1, 2: 2}   # library mode -> oracle mode (same numbering)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def gpu_decode(torch, code, llr_np):
+    llr = torch.from_numpy(np.ascontiguousarray(llr_np)).cuda()
+    bits, pm, ok, slot = code.decode(llr)
+    torch.cuda.synchronize()
+    return bits.cpu().numpy(), pm.cpu().numpy(), ok.cpu().numpy(), slot.cpu().numpy()
+
+
+def assert_parity(g, o, dtype, what=""):
+    gb, gpm, gok, gsl = g
+    ob, opm, ook, osl = o
+    bad = np.flatnonzero((gb != ob).any(axis=1) | (gsl != osl) | (gok != ook))
+    assert bad.size == 0, f"{what}: {bad.size} frames differ, first {bad[:8]}"
+    if dtype == "i8":
+        assert np.array_equal(gpm, opm), what
+    else:
+        np.testing.assert_allclose(gpm, opm, rtol=1e-5, atol=0, err_msg=what)
+
+
+def run_case(torch, oracle_mod, frozen, crc_len, poly, L, llr_np, mode=0, launch=None):
+    from paper_1505_01466_gb300.polar import PolarCode
+    code = PolarCode(frozen, crc_len, poly, L, mode=mode)
+    if launch is not None:
+        code.set_launch(1 if llr_np.dtype == np.int8 else 0, *launch)
+    g = gpu_decode(torch, code, llr_np)
+    o = oracle_mod.decode(frozen, L, llr_np, crc_len, poly, OMODE[mode], n_threads=NT)
+    code.close()
+    return g, o
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_config_256_128_crc8_L4_all_frames(torch_cuda, oracle_mod, dtype):
+    # (256,128) CRC-8 L=4, GA design 2 dB, Eb/N0 2.5 dB, 10^4 frames.
+    fr = I.ga_frozen_mask(256, 128, 2.0, 120 / 256)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 2.5, 10000, seed=101)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    g, o = run_case(torch_cuda, oracle_mod, fr, 8, I.CRC8_POLY, 4, llr)
+    assert_parity(g, o, dtype, "(256,128) L=4")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("mode", list(MODES))
+def test_random_codes_all_list_sizes(torch_cuda, oracle_mod, dtype, mode):
+    rng = np.random.default_rng(hash((dtype, mode)) % 2 ** 32)
+    for N in (8, 16, 32, 64, 128, 512):
+        for L in (1, 2, 4, 8, 16, 32):
+            K = int(rng.integers(max(2, N // 8), N))
+            crc = 8 if K > 12 else 0
+            fr = I.ga_frozen_mask(N, K, float(rng.uniform(0, 4)), max(K - crc, 1) / N)
+            snr = float(rng.uniform(-1.0, 3.0))
+            f = I.make_frames(fr, crc, I.CRC8_POLY, snr, 24, seed=int(rng.integers(1 << 30)))
+            llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+            g, o = run_case(torch_cuda, oracle_mod, fr, crc, I.CRC8_POLY, L, llr, MODES[mode])
+            assert_parity(g, o, dtype, f"N={N} K={K} L={L} mode={mode}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("L", [2, 4, 8, 32])
+def test_config_1024_860_crc32_sampled(torch_cuda, oracle_mod, dtype, L):
+    fr = I.ga_frozen_mask(1024, 860, 4.0, 828 / 1024)
+    for snr in (3.5, 4.5):
+        f = I.make_frames(fr, 32, I.CRC32_POLY, snr, 256 if L < 32 else 96, seed=int(snr * 100) + L)
+        llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+        g, o = run_case(torch_cuda, oracle_mod, fr, 32, I.CRC32_POLY, L, llr)
+        assert_parity(g, o, dtype, f"(1024,860) L={L} {snr} dB")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("L", [8, 32])
+def test_config_2048_1723_crc32_sampled(torch_cuda, oracle_mod, dtype, L):
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 64, seed=2048 + L)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    g, o = run_case(torch_cuda, oracle_mod, fr, 32, I.CRC32_POLY, L, llr)
+    assert_parity(g, o, dtype, f"(2048,1723) L={L}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_launch_shapes_and_spills_agree(torch_cuda, oracle_mod, dtype):
+    fr = I.ga_frozen_mask(1024, 512, 2.0, 480 / 1024)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 1.5, 48, seed=77)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    o = oracle_mod.decode(fr, 16, llr, 32, I.CRC32_POLY, 0, n_threads=NT)
+    from paper_1505_01466_gb300.polar import PolarCode
+    for warps in (1, 2, 4):
+        for budget in (0, 60000, 20000):
+            code = PolarCode(fr, 32, I.CRC32_POLY, 16)
+            try:
+                code.set_launch(1 if dtype == "i8" else 0, warps, budget)
+            except Exception:
+                continue
+            g = gpu_decode(torch_cuda, code, llr)
+            assert_parity(g, o, dtype, f"warps={warps} budget={budget} info={code.info()}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_edge_cases(torch_cuda, oracle_mod, dtype):
+    from paper_1505_01466_gb300.polar import PolarCode
+    rng = np.random.default_rng(5)
+    cases = []
+    # rate-1 code (root is a Rate-1 leaf), repetition code (root is a Rep leaf)
+    cases.append((np.zeros(32, np.uint8), 0))
+    cases.append((np.array([1] * 63 + [0], np.uint8), 0))
+    # single-parity-check code of length 4 under SPC_ANY handled by mode below
+    cases.append((I.ga_frozen_mask(128, 64, 1.0), 8))
+    for fr, crc in cases:
+        N = fr.size
+        llrs = [np.zeros((4, N), np.float32),                         # all-zero LLRs: ties everywhere
+                -np.ones((4, N), np.float32) * 3,                    # all negative
+                rng.integers(-2, 3, (16, N)).astype(np.float32),     # many ties
+                rng.normal(0, 40, (16, N)).astype(np.float32)]      # saturating in int8
+        for x in llrs:
+            llr = I.quantize_i8(x / 4.0) if dtype == "i8" else x
+            for L in (1, 2, 8, 32):
+                for mode in (0, 1, 2):
+                    g, o = run_case(torch_cuda, oracle_mod, fr, crc, I.CRC8_POLY, L, llr, mode)
+                    assert_parity(g, o, dtype, f"edge N={N} L={L} mode={mode}")
+    # -128 in int8 input is read as -127
+    if dtype == "i8":
+        fr = I.ga_frozen_mask(64, 32, 1.0)
+        x = rng.integers(-128, 128, (8, 64)).astype(np.int8)
+        g, o = run_case(torch_cuda, oracle_mod, fr, 0, 0, 4, x)
+        assert_parity(g, o, dtype, "-128 input")
+    # zero frames is a no-op
+    code = PolarCode(I.ga_frozen_mask(64, 32, 1.0), 0, 0, 4)
+    t = torch_cuda.zeros((0, 64), dtype=torch_cuda.float32, device="cuda")
+    code.decode(t)
+
+
+def test_deterministic_and_stream_safe(torch_cuda, oracle_mod):
+    from paper_1505_01466_gb300.polar import PolarCode
+    fr = I.ga_frozen_mask(1024, 860, 4.0, 828 / 1024)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 2000, seed=9)
+    code = PolarCode(fr, 32, I.CRC32_POLY, 8)
+    llr = torch_cuda.from_numpy(f.llr_f32).cuda()
+    ref = code.decode(llr)
+    s1, s2 = torch_cuda.cuda.Stream(), torch_cuda.cuda.Stream()
+    outs = []
+    for s in (s1, s2, s1, s2):
+        with torch_cuda.cuda.stream(s):
+            outs.append(code.decode(llr, stream=s))
+    torch_cuda.cuda.synchronize()
+    for out in outs:
+        for a, b in zip(out, ref):
+            assert torch_cuda.equal(a, b)
