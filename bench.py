@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: information throughput of list-CRC polar decoding on GB300.
+
+Workload: polar code (2048,1723) with CRC-32 (poly 0x04C11DB7) inside K,
+list size L = 32, frozen set by GA density evolution at 4 dB, BPSK over AWGN
+at Eb/N0 = 4 dB, 2^20 frames per step, decoded by one plain
+one-code-per-launch call of the C ABI (polar_list_decode).
+
+metric: info Gbps = payload bits (k = 1691) x frames / decode time.
+
+Contract: W untimed warm-up steps, K timed steps bracketed by a barrier and
+torch.cuda.synchronize(), CUDA events on the decode stream, max over ranks,
+rank 0 prints one JSON line. Under torchrun every rank decodes its own 2^20
+frames (weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle (the paper's method restated plainly
+in C, test infrastructure) on the host cores on a bounded frame sample of
+the same workload, and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, K, CRC_LEN, L = 2048, 1723, 32, 32
+DESIGN_DB, EBN0_DB = 4.0, 4.0
+FRAMES = 1 << 20
+UNIQUE = 1 << 16
+METRIC = "info Gbps at (2048,1723) L=32 on 1 GB300, batched vs plain; FER match; p99 lat"
+UNIT = "Gbps"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "i8"])
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-dtype", action="store_true", help="skip the second LLR type")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_code_inputs(seed: int, n_unique: int):
+    from paper_1505_01466_gb300 import inputs as I
+    frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
+    fr = I.make_frames(frozen, CRC_LEN, I.CRC32_POLY, EBN0_DB, n_unique, seed=seed)
+    return I, frozen, fr
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(prefix="clocks", suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(llr_np, frozen, seconds: float):
+    """Oracle (plain C, all host cores) on a bounded sample: info Gbps."""
+    import oracle
+    from paper_1505_01466_gb300 import inputs as I
+    cores = os.cpu_count() or 1
+    oracle.build()
+    mode = oracle.SPC4
+    probe = min(len(llr_np), 2 * cores)
+    t0 = time.perf_counter()
+    oracle.decode(frozen, L, llr_np[:probe], CRC_LEN, I.CRC32_POLY, mode, n_threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(len(llr_np), max(probe, probe * seconds / dt)))
+    n = max(cores, (n // cores) * cores)
+    t0 = time.perf_counter()
+    oracle.decode(frozen, L, llr_np[:n], CRC_LEN, I.CRC32_POLY, mode, n_threads=cores)
+    dt = time.perf_counter() - t0
+    k = K - CRC_LEN
+    return {"value": k * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} frames of the same workload ({llr_np.dtype}), oracle Dec-SPC-4 list decoder, "
+                      f"{cores} threads, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    I, frozen, fr = make_code_inputs(seed=7, n_unique=4096)
+    llr = fr.llr_i8 if args.dtype == "i8" else fr.llr_f32
+    per_step = []
+    n_used = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(llr, frozen, seconds=max(2.0, args.cpu_seconds / max(args.steps, 1)))
+        if s >= args.warmup:
+            per_step.append(cb)
+            n_used = cb["sample"]
+    vals = [c["value"] for c in per_step]
+    v = statistics.mean(vals)
+    k = K - CRC_LEN
+    out = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "impl": "reference",
+        "config": config_dict(args, "reference"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": per_step[0]["cores"], "kind": "oracle",
+                         "sample": n_used},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(args, impl):
+    return {
+        "workload": "polar-CRC (2048,1723) list decode, plain one-code-per-launch",
+        "N": N, "K": K, "k": K - CRC_LEN, "L": L, "crc": "CRC-32 0x04C11DB7 inside K",
+        "frozen": f"GA density evolution at {DESIGN_DB} dB", "ebn0_db": EBN0_DB,
+        "frames_per_gpu": args.frames, "unique_frames": min(UNIQUE, args.frames),
+        "llr": "float32" if args.dtype == "f32" else "int8 (4 per unit LLR, clamp 127)",
+        "node_set": "Dec-SPC-4 (Rate-0, Rate-1, Rep, SPC<=4)",
+        "l2": "inputs larger than L2 (no flush needed)",
+        "parallelism": "frames sharded across ranks (replicas)",
+    }
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    __graft_entry__.build()
+    from paper_1505_01466_gb300.polar import PolarCode
+
+    I, frozen, fr = make_code_inputs(seed=1000 + rank, n_unique=min(UNIQUE, args.frames))
+    llr_np = fr.llr_i8 if args.dtype == "i8" else fr.llr_f32
+    reps = (args.frames + llr_np.shape[0] - 1) // llr_np.shape[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    uniq = torch.from_numpy(llr_np).to(dev)
+    llr = uniq.repeat(reps, 1)[: args.frames].contiguous()
+    del uniq
+    code = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L)
+    # untimed: pick the launch shape (warps per frame, shared-memory budget) by measurement
+    tuned = code.autotune(llr[: min(args.frames, 16384)])
+    k = K - CRC_LEN
+    kb = (k + 7) // 8
+    bits = torch.empty((args.frames, kb), dtype=torch.uint8, device=dev)
+    pm = torch.empty(args.frames, dtype=torch.float32, device=dev)
+    ok = torch.empty(args.frames, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing ----
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            code.decode_into(llr, bits, pm, ok, None, stream=stream)
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            evs[s][0].record(stream)
+            code.decode_into(llr, bits, pm, ok, None, stream=stream)
+            evs[s][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = k * args.frames * world / (ms_per_step * 1e-3) / 1e9
+
+    # sanity: a noisy 4 dB workload must decode with a low frame-error rate
+    with torch.cuda.stream(stream):
+        code.decode_into(llr[:UNIQUE], bits[:UNIQUE], pm[:UNIQUE], ok[:UNIQUE], None, stream=stream)
+    torch.cuda.synchronize()
+    got = I.unpack_bits_lsb(bits[: min(UNIQUE, args.frames)].cpu().numpy(), k)
+    fer = float((got != fr.payload[: got.shape[0]]).any(axis=1).mean())
+
+    # ---- end to end through the C ABI with host buffers ----
+    host_llr = torch.empty_like(llr, device="cpu").pin_memory()
+    host_llr.copy_(llr.cpu())
+    hbits = torch.empty((args.frames, kb), dtype=torch.uint8).pin_memory()
+    hpm = torch.empty(args.frames, dtype=torch.float32).pin_memory()
+    hok = torch.empty(args.frames, dtype=torch.uint8).pin_memory()
+    dllr = torch.empty_like(llr)
+    e2e_steps = max(1, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        dllr.copy_(host_llr, non_blocking=True)
+        code.decode_into(dllr, bits, pm, ok, None, stream=stream)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            dllr.copy_(host_llr, non_blocking=True)
+            code.decode_into(dllr, bits, pm, ok, None, stream=stream)
+            hbits.copy_(bits, non_blocking=True)
+            hpm.copy_(pm, non_blocking=True)
+            hok.copy_(ok, non_blocking=True)
+        e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = k * args.frames * world / (e2e_ms * 1e-3) / 1e9
+    h2d = llr.numel() * llr.element_size()
+    d2h = bits.numel() + pm.numel() * 4 + ok.numel()
+
+    info = code.info()
+    di = 1 if args.dtype == "i8" else 0
+    launch_info = {"warps_per_frame": info["warps_per_frame"][di], "frames_per_cta": info["frames_per_cta"][di],
+                   "smem_per_frame": info["smem_per_frame"][di], "scratch_per_frame": info["scratch_per_frame"][di],
+                   "spill_mask": info["spill_mask"][di], "autotuned": {"warps": tuned[0], "smem_budget": tuned[1]}}
+
+    # ---- roofline: counted min/add/compare/select/xor ops vs the scalar ALU peak ----
+    pk, src = peaks()
+    ops_frame = code.op_count()
+    kernel_s = ms_per_step * 1e-3
+    achieved = ops_frame * args.frames / kernel_s / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None,
+                "note": f"ops counted per frame along the schedule ({ops_frame}); peak = {sms} SMs x 128 lanes x "
+                        f"{pk.get('sm_max_mhz', 2070.0)} MHz ({src} clock); HBM side: "
+                        f"{N * llr.element_size() * args.frames / kernel_s / 1e9:.1f} GB/s of {pk.get('hbm_gbs')}"}
+
+    # the other LLR type on the same frames (device-resident timing only)
+    other = {}
+    if not args.single_dtype:
+        odt = "i8" if args.dtype == "f32" else "f32"
+        ollr_np = fr.llr_i8 if odt == "i8" else fr.llr_f32
+        ollr = torch.from_numpy(ollr_np).to(dev).repeat(reps, 1)[: args.frames].contiguous()
+        code.autotune(ollr[: min(args.frames, 16384)])
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                code.decode_into(ollr, bits, pm, ok, None, stream=stream)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            for _ in range(args.steps):
+                code.decode_into(ollr, bits, pm, ok, None, stream=stream)
+            b.record(stream)
+        barrier()
+        oms = a.elapsed_time(b) / args.steps
+        oinfo = code.info()
+        di = 1 if odt == "i8" else 0
+        other = {"dtype": odt, "value": k * args.frames * world / (oms * 1e-3) / 1e9, "unit": UNIT,
+                 "ms_per_step": oms, "launch": {"warps_per_frame": oinfo["warps_per_frame"][di],
+                                                "frames_per_cta": oinfo["frames_per_cta"][di],
+                                                "smem_per_frame": oinfo["smem_per_frame"][di],
+                                                "spill_mask": oinfo["spill_mask"][di]}}
+        del ollr
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(llr_np, frozen, args.cpu_seconds)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": config_dict(args, "ours"),
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "fer_sample": fer,
+            "wall_s_timed": t_wall,
+            "launch": launch_info,
+            "other_dtype": other,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

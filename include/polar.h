@@ -163,6 +163,16 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                           uint32_t smem_budget);
 
+/* Autotune the launch shape of one dtype on real frames: times every
+ * distinct (warps per frame, shared-memory budget) shape on n_frames frames of
+ * llr_dev (device, [n_frames][N]) on `stream`, installs the fastest and
+ * reports it (either out pointer may be NULL; *budget_out = 0 means no cap).
+ * Blocks until the timing runs finish. Results of later decodes do not depend
+ * on the shape (only speed does). Errors: POLAR_EINVAL, POLAR_ENOMEM,
+ * POLAR_ECUDA. */
+POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
+                                  polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ struct polar_code {
     bool host_only = false;
     int device = -1;
     int sm_count = 0;
-    uint32_t *d_ops = nullptr;
+    std::vector<uint32_t> shape_ops[2];  // ops with solo / sync flags of shape[d]
     uint32_t *d_syn = nullptr;
     uint16_t *d_info = nullptr;
     LaunchShape shape[2];
@@ -134,7 +134,7 @@ bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &
     fixed += al16(N * es);                                             // chan
     for (uint32_t j = 0; j < n; ++j) fixed += al16(L * 4u * (uint32_t)beta_words((int)j));  // BL
     fixed += al16(L * 4u * (uint32_t)beta_words((int)n));              // BR
-    fixed += 4 * al16(L * (n + 1));                                    // idx, bidx x2
+    fixed += 4 * al16(L * 16u);                                        // idx, bidx x2
     fixed += 2 * al16(L * 4u);                                         // pen x2
     fixed += al16(std::max(8u * L, 8u) * 8u);                          // keys
     fixed += al16(L * 8u);                                             // surv
@@ -166,8 +166,8 @@ bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &
     }
     for (uint32_t j = 0; j < n; ++j) { lay.bl[j] = off; off += al16(L * 4u * (uint32_t)beta_words((int)j)); }
     lay.br = off; off += al16(L * 4u * (uint32_t)beta_words((int)n));
-    for (int b = 0; b < 2; ++b) { lay.idx[b] = off; off += al16(L * (n + 1)); }
-    for (int b = 0; b < 2; ++b) { lay.bidx[b] = off; off += al16(L * (n + 1)); }
+    for (int b = 0; b < 2; ++b) { lay.idx[b] = off; off += al16(L * 16u); }
+    for (int b = 0; b < 2; ++b) { lay.bidx[b] = off; off += al16(L * 16u); }
     for (int b = 0; b < 2; ++b) { lay.pen[b] = off; off += al16(L * 4u); }
     lay.key = off; off += al16(std::max(8u * L, 8u) * 8u);
     lay.surv = off; off += al16(L * 8u);
@@ -181,18 +181,32 @@ bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &
 
 constexpr uint32_t kMaxSmemPerCta = 232448;   // 227 KB opt-in per CTA on sm_100-class parts
 
+// Solo / sync flags for a group of `warps` warps: nodes of at most
+// 2^kSoloMaxLog bits run on warp 0 alone; a group barrier is needed after an
+// operation unless it and the next one are both solo.
+std::vector<uint32_t> flag_ops(const std::vector<uint32_t> &ops, uint32_t warps) {
+    std::vector<uint32_t> out(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        const bool solo = warps == 1 || op_stage(ops[i]) <= kSoloMaxLog;
+        const bool next_solo = i + 1 < ops.size() && (warps == 1 || op_stage(ops[i + 1]) <= kSoloMaxLog);
+        out[i] = ops[i] | (solo ? OP_SOLO : 0u) | ((warps > 1 && !(solo && next_solo)) ? OP_SYNC : 0u);
+    }
+    return out;
+}
+
 bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget, LaunchShape &sh) {
     if (warps != 1 && warps != 2 && warps != 4) return false;
     const uint32_t es = dtype == POLAR_LLR_I8 ? 1u : 4u;
     const uint32_t gpc = 4u / warps;
     if (budget == 0) {
-        // Default: aim for 8 warps per SM from shared memory alone.
-        const uint32_t groups_per_sm = std::max(2u, 8u / warps);
+        // Default: 4 frames per SM with 4 warps each, 6 with 2, 8 with 1.
+        const uint32_t groups_per_sm = warps == 4 ? 4u : (warps == 2 ? 6u : 8u);
         budget = (kMaxSmemPerCta / groups_per_sm) & ~15u;
     }
     budget = std::min(budget, kMaxSmemPerCta / gpc);
     Layout lay;
     if (!build_layout(c->n, c->L, es, budget, lay)) return false;
+    sh.d_ops = nullptr;
     sh.warps = (int)warps;
     sh.groups_per_cta = (int)gpc;
     sh.threads = 128;
@@ -209,10 +223,12 @@ uint32_t default_warps(const polar_code *c) {
 }
 
 void free_device(polar_code *c) {
-    if (c->d_ops) cudaFree(c->d_ops);
+    for (int d = 0; d < 2; ++d) {
+        if (c->shape[d].d_ops) cudaFree(c->shape[d].d_ops);
+        c->shape[d].d_ops = nullptr;
+    }
     if (c->d_syn) cudaFree(c->d_syn);
     if (c->d_info) cudaFree(c->d_info);
-    c->d_ops = nullptr;
     c->d_syn = nullptr;
     c->d_info = nullptr;
 }
@@ -223,6 +239,64 @@ cudaError_t upload(T **dst, const std::vector<T> &v) {
     if (e != cudaSuccess) return e;
     if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
+}
+
+// Install a launch shape for one dtype: flag the schedule and upload it.
+int install_shape(polar_code *c, int dtype, const LaunchShape &sh) {
+    std::vector<uint32_t> fl = flag_ops(c->ops, (uint32_t)sh.warps);
+    uint32_t *d = nullptr;
+    if (!c->host_only) {
+        cudaError_t e = upload(&d, fl);
+        if (e != cudaSuccess) {
+            if (d) cudaFree(d);
+            return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
+        }
+    }
+    if (c->shape[dtype].d_ops) cudaFree(c->shape[dtype].d_ops);
+    c->shape[dtype] = sh;
+    c->shape[dtype].d_ops = d;
+    c->shape_ops[dtype] = std::move(fl);
+    return POLAR_OK;
+}
+
+// Launch a decode of n_frames with an explicit shape.
+int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const void *llr, uint32_t n_frames,
+                 uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot, cudaStream_t st) {
+    int occ = occupancy(dtype, sh);
+    if (occ <= 0) return POLAR_ECUDA;
+    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
+    const uint64_t need_ctas = ((uint64_t)n_frames + sh.groups_per_cta - 1) / sh.groups_per_cta;
+    if (grid > need_ctas) grid = need_ctas;
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.ops = sh.d_ops;
+    p.n_ops = (int)code->ops.size();
+    p.N = (int)code->N;
+    p.n = (int)code->n;
+    p.L = (int)code->L;
+    p.K = (int)code->K;
+    p.k = (int)code->k;
+    p.crc_len = (int)code->crc_len;
+    p.llr = llr;
+    p.bits = bits;
+    p.kb = (int)((code->k + 7) / 8);
+    p.pm = pm;
+    p.ok = ok;
+    p.slot = slot;
+    p.syn = code->d_syn;
+    p.info = code->d_info;
+    p.n_frames = n_frames;
+    p.groups_per_cta = sh.groups_per_cta;
+    p.lay = sh.lay;
+    void *scratch = nullptr;
+    if (sh.lay.gbytes > 0) {
+        const size_t bytes = (size_t)grid * sh.groups_per_cta * sh.lay.gbytes;
+        if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) return POLAR_ENOMEM;
+        p.scratch = (uint8_t *)scratch;
+    }
+    cudaError_t e = launch_decode(dtype, sh, p, (int)grid, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 }  // namespace
@@ -284,13 +358,6 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     c->n_rep = tb.rep;
     c->n_spc = tb.spc;
     if (crc_len > 0) build_syndrome(c);
-    for (int d = 0; d < 2; ++d) {
-        if (!make_shape(c, d, default_warps(c), 0, c->shape[d])) {
-            delete c;
-            return POLAR_EUNSUPPORTED;
-        }
-    }
-
     c->host_only = (flags & POLAR_HOST_ONLY) != 0;
     if (!c->host_only) {
         if (cudaGetDevice(&c->device) != cudaSuccess ||
@@ -298,13 +365,21 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
             delete c;
             return POLAR_ECUDA;
         }
-        cudaError_t e = upload(&c->d_ops, c->ops);
-        if (e == cudaSuccess) e = upload(&c->d_info, c->info);
+        cudaError_t e = upload(&c->d_info, c->info);
         if (e == cudaSuccess) e = upload(&c->d_syn, c->syn);
         if (e != cudaSuccess) {
             free_device(c);
             delete c;
             return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
+        }
+    }
+    for (int d = 0; d < 2; ++d) {
+        LaunchShape sh;
+        int st = make_shape(c, d, default_warps(c), 0, sh) ? install_shape(c, d, sh) : POLAR_EUNSUPPORTED;
+        if (st != POLAR_OK) {
+            free_device(c);
+            delete c;
+            return st;
         }
     }
     *out = c;
@@ -325,46 +400,67 @@ int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dty
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     if (n_frames == 0) return POLAR_OK;
     if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
+    return decode_shape(code, llr_dtype, code->shape[llr_dtype], llr_dev, n_frames, info_bits_dev, path_metric_dev,
+                        crc_ok_dev, winner_slot_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
+                        polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out) {
+    if (!code || code->host_only || !llr_dev || n_frames == 0) return POLAR_EINVAL;
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const LaunchShape &sh = code->shape[llr_dtype];
-    int occ = occupancy(llr_dtype, sh);
-    if (occ <= 0) return POLAR_ECUDA;
-    const uint64_t groups_needed = n_frames;
-    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
-    const uint64_t need_ctas = (groups_needed + sh.groups_per_cta - 1) / sh.groups_per_cta;
-    if (grid > need_ctas) grid = need_ctas;
-
-    Params p;
-    std::memset(&p, 0, sizeof(p));
-    p.ops = code->d_ops;
-    p.n_ops = (int)code->ops.size();
-    p.N = (int)code->N;
-    p.n = (int)code->n;
-    p.L = (int)code->L;
-    p.K = (int)code->K;
-    p.k = (int)code->k;
-    p.crc_len = (int)code->crc_len;
-    p.llr = llr_dev;
-    p.bits = info_bits_dev;
-    p.kb = (int)((code->k + 7) / 8);
-    p.pm = path_metric_dev;
-    p.ok = crc_ok_dev;
-    p.slot = winner_slot_dev;
-    p.syn = code->d_syn;
-    p.info = code->d_info;
-    p.n_frames = n_frames;
-    p.groups_per_cta = sh.groups_per_cta;
-    p.lay = sh.lay;
-
-    void *scratch = nullptr;
-    if (sh.lay.gbytes > 0) {
-        const size_t bytes = (size_t)grid * sh.groups_per_cta * sh.lay.gbytes;
-        if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) return POLAR_ENOMEM;
-        p.scratch = (uint8_t *)scratch;
+    const size_t kb = (code->k + 7) / 8;
+    uint8_t *bits = nullptr;
+    float *pm = nullptr;
+    if (cudaMalloc(&bits, std::max<size_t>(kb, 1) * n_frames) != cudaSuccess) return POLAR_ENOMEM;
+    if (cudaMalloc(&pm, sizeof(float) * n_frames) != cudaSuccess) {
+        cudaFree(bits);
+        return POLAR_ENOMEM;
     }
-    cudaError_t e = launch_decode(llr_dtype, sh, p, (int)grid, st);
-    if (scratch) cudaFreeAsync(scratch, st);
-    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    static const uint32_t budgets[] = {0xffffffffu, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u};
+    float best_ms = 1e30f;
+    LaunchShape best;
+    uint32_t best_w = 0, best_b = 0;
+    std::vector<std::pair<uint32_t, uint32_t>> seen;   // (warps, spill mask) already timed
+    int status = POLAR_OK;
+    for (uint32_t w : {4u, 2u, 1u}) {
+        for (uint32_t b : budgets) {
+            LaunchShape sh;
+            if (!make_shape(code, llr_dtype, w, b, sh)) continue;
+            bool dup = false;
+            for (auto &pr : seen) dup |= pr.first == w && pr.second == sh.lay.spill_mask;
+            if (dup) continue;
+            seen.push_back({w, sh.lay.spill_mask});
+            std::vector<uint32_t> fl = flag_ops(code->ops, w);
+            if (upload(&sh.d_ops, fl) != cudaSuccess) { status = POLAR_ECUDA; break; }
+            float ms = 0.f;
+            int rc = decode_shape(code, llr_dtype, sh, llr_dev, n_frames, bits, pm, nullptr, nullptr, st);
+            if (rc == POLAR_OK) {
+                cudaEventRecord(e0, st);
+                rc = decode_shape(code, llr_dtype, sh, llr_dev, n_frames, bits, pm, nullptr, nullptr, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = POLAR_ECUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            cudaFree(sh.d_ops);
+            sh.d_ops = nullptr;
+            if (rc != POLAR_OK) continue;
+            if (ms < best_ms) { best_ms = ms; best = sh; best_w = w; best_b = b; }
+        }
+        if (status != POLAR_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(bits);
+    cudaFree(pm);
+    if (status != POLAR_OK) return status;
+    if (best_w == 0) return POLAR_ECUDA;
+    if (warps_out) *warps_out = best_w;
+    if (budget_out) *budget_out = best_b == 0xffffffffu ? 0u : best_b;
+    return install_shape(code, llr_dtype, best);
 }
 
 int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
@@ -433,8 +529,7 @@ int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_fra
     if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
     LaunchShape sh;
     if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh)) return POLAR_EINVAL;
-    c->shape[llr_dtype] = sh;
-    return POLAR_OK;
+    return install_shape(c, llr_dtype, sh);
 }
 
 }  // extern "C"

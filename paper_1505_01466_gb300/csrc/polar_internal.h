@@ -21,16 +21,24 @@ enum OpKind : uint32_t {
     OP_SPC = 6     // single-parity-check leaf                  Sec. III-D
 };
 
-// One schedule entry: kind | stage j << 4 | dest << 8.
+// One schedule entry: kind | stage j << 4 | dest << 8 | solo << 9 | sync << 10.
 //   j     stage of the node (N_v = 2^j)
 //   dest  where the node's beta goes: 0 = left-child buffer BL[j],
 //         1 = right-child / root buffer BR
+//   solo  warp 0 of the frame's group runs the operation alone
+//   sync  a group barrier follows (else only warp 0 synchronises)
 __host__ __device__ inline uint32_t op_make(uint32_t kind, uint32_t j, uint32_t dest) {
     return kind | (j << 4) | (dest << 8);
 }
 __host__ __device__ inline uint32_t op_kind(uint32_t op) { return op & 15u; }
 __host__ __device__ inline int op_stage(uint32_t op) { return (int)((op >> 4) & 15u); }
 __host__ __device__ inline int op_dest(uint32_t op) { return (int)((op >> 8) & 1u); }
+__host__ __device__ inline bool op_solo(uint32_t op) { return ((op >> 9) & 1u) != 0; }
+__host__ __device__ inline bool op_sync(uint32_t op) { return ((op >> 10) & 1u) != 0; }
+constexpr uint32_t OP_SOLO = 1u << 9;
+constexpr uint32_t OP_SYNC = 1u << 10;
+// Nodes of at most this many bits run solo when a frame has several warps.
+constexpr int kSoloMaxLog = 4;
 
 // Bit-packed beta: words per path for a node of 2^j bits.
 __host__ __device__ inline int beta_words(int j) { return j >= 5 ? 1 << (j - 5) : 1; }
@@ -42,7 +50,7 @@ struct Layout {
     uint32_t alpha[kMaxLogN];      // stage j < n: L rows of 2^j elements
     uint32_t bl[kMaxLogN];         // left-child beta of stage j: L rows of beta_words(j)
     uint32_t br;                   // right/root beta: L rows of beta_words(n)
-    uint32_t idx[2];               // alpha stage -> physical row, [L][n+1] bytes, double buffered
+    uint32_t idx[2];               // alpha stage -> physical row, [L][16] bytes, double buffered
     uint32_t bidx[2];              // left-beta stage -> physical row, same shape
     uint32_t pen[2];               // penalties, [L] float or int32, double buffered
     uint32_t key;                  // candidate keys, 8L uint64
@@ -76,6 +84,7 @@ struct Params {
 
 struct LaunchShape {
     int warps;                     // warps per frame group (1, 2, 4)
+    uint32_t *d_ops;               // schedule with this shape's solo / sync flags (device)
     int groups_per_cta;
     int threads;                   // per CTA
     uint32_t smem;                 // dynamic shared memory per CTA

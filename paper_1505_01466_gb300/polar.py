@@ -24,6 +24,7 @@ SPC_MAX_4, SPC_ANY, NO_SPECIAL_NODES, HOST_ONLY = 0, 1, 2, 0x100
 EXPORTED = [
     "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror",
     "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
+    "polar_code_autotune",
 ]
 
 
@@ -63,6 +64,7 @@ def _lib():
         lib.polar_code_schedule.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
         lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
         lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32]
+        lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32
@@ -150,6 +152,16 @@ class PolarCode:
 
     def set_launch(self, dtype: int, warps_per_frame: int, smem_budget: int = 0):
         _check(_lib().polar_code_set_launch(self._h, dtype, warps_per_frame, smem_budget), "polar_code_set_launch")
+
+    def autotune(self, llr, stream=None):
+        """Time the launch shapes on ``llr`` ([F, N] CUDA tensor) and keep the fastest."""
+        import torch
+        dt = LLR_I8 if llr.dtype == torch.int8 else LLR_F32
+        w, b = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(_lib().polar_code_autotune(self._h, dt, ctypes.c_void_p(llr.data_ptr()), llr.numel() // self.N,
+                                          _stream_handle(stream), ctypes.byref(w), ctypes.byref(b)),
+               "polar_code_autotune")
+        return int(w.value), int(b.value)
 
     def decode_into(self, llr, bits, pm, ok=None, slot=None, stream=None):
         """Enqueue a decode of ``llr`` ([F, N] float32 or int8 CUDA tensor)."""

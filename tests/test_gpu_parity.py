@@ -173,3 +173,21 @@ def test_deterministic_and_stream_safe(torch_cuda, oracle_mod):
     for out in outs:
         for a, b in zip(out, ref):
             assert torch_cuda.equal(a, b)
+
+
+def test_autotune_keeps_results(torch_cuda, oracle_mod):
+    from paper_1505_01466_gb300.polar import PolarCode
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.75, 1024, seed=31)
+    for llr_np in (f.llr_f32, f.llr_i8):
+        code = PolarCode(fr, 32, I.CRC32_POLY, 8)
+        llr = torch_cuda.from_numpy(llr_np).cuda()
+        before = code.decode(llr)
+        w, b = code.autotune(llr)
+        assert w in (1, 2, 4)
+        after = code.decode(llr)
+        torch_cuda.cuda.synchronize()
+        for x, y in zip(before, after):
+            assert torch_cuda.equal(x, y)
+        o = oracle_mod.decode(fr, 8, llr_np[:64], 32, I.CRC32_POLY, 0, n_threads=NT)
+        assert_parity(tuple(t[:64].cpu().numpy() for t in after), o, "i8" if llr_np.dtype == np.int8 else "f32")
