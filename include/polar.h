@@ -173,6 +173,41 @@ POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t 
 POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out);
 
+/* Allocation-free variant of polar_list_decode. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while decoding -- work captured into a CUDA graph that must
+ * not hold allocation nodes, real-time paths that may not take allocator
+ * locks or fail for lack of memory after start-up, and hosts that give the
+ * decoder a fixed memory budget.
+ *
+ * Same arguments, outputs and results as polar_list_decode. Instead of
+ * taking scratch from the stream-ordered allocator, the alpha stages that do
+ * not fit in shared memory go to one fixed device array built into the
+ * library, of polar_noalloc_scratch_bytes() bytes (64 MiB); every GPU that
+ * loads the library holds it until the process exits. The call performs no
+ * allocation of any kind.
+ *   - The first call on a device looks up that array's device address (with
+ *     the device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - The kernel is persistent: when the full grid would need more scratch
+ *     than the array holds, fewer CTAs are launched (slower, same results).
+ *     A launch shape whose single CTA needs more than the array is refused
+ *     with POLAR_EUNSUPPORTED (choose a smaller list size or a shape with a
+ *     larger shared-memory budget).
+ *   - Every call uses the same array and leaves its last contents there.
+ *     Nothing in it needs to start at zero (each frame writes every stage row
+ *     before reading it), but calls whose kernels overlap on the GPU -- on
+ *     different streams, or from different threads -- race on the array and
+ *     must not be issued.
+ * Errors: as polar_list_decode, plus POLAR_EINVAL when the current device is
+ * not the device the code was created on. */
+POLAR_API int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int llr_dtype,
+                                        uint32_t n_frames, uint8_t *info_bits_dev, float *path_metric_dev,
+                                        uint8_t *crc_ok_dev, int32_t *winner_slot_dev, polar_stream_t stream);
+
+/* Size in bytes of the fixed scratch array used by polar_list_decode_noalloc. */
+POLAR_API size_t polar_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

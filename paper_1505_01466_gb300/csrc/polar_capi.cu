@@ -299,6 +299,36 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
+// ---- allocation-free decoding ----------------------------------------------
+// Some callers cannot allocate device memory while they decode: code running
+// inside a captured CUDA graph that must not contain allocation nodes, real-
+// time paths that must not take allocator locks or risk an out-of-memory
+// failure after start-up, and hosts that hand the decoder a fixed memory
+// budget. For them the spilled alpha stages live in one fixed array that is
+// part of the library image: every GPU that loads the library holds these
+// kNoAllocScratchBytes until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the array on the current device. The name of a
+// __device__ array in host code is only a host-side stand-in, so the address
+// is looked up once per device (with that device current) and cached.
+int noalloc_scratch(int device, uint8_t **out) {
+    if (device < 0 || device >= kMaxDevices) return POLAR_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return POLAR_ECUDA;
+        g_noalloc_ptr[device] = ptr;
+    }
+    *out = (uint8_t *)g_noalloc_ptr[device];
+    return POLAR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -462,6 +492,61 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     if (budget_out) *budget_out = best_b == 0xffffffffu ? 0u : best_b;
     return install_shape(code, llr_dtype, best);
 }
+
+int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int llr_dtype, uint32_t n_frames,
+                              uint8_t *info_bits_dev, float *path_metric_dev, uint8_t *crc_ok_dev,
+                              int32_t *winner_slot_dev, polar_stream_t stream) {
+    if (!code || code->host_only) return POLAR_EINVAL;
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
+    if (dev != code->device) return POLAR_EINVAL;
+    const LaunchShape &sh = code->shape[llr_dtype];
+    const int occ = occupancy(llr_dtype, sh);
+    if (occ <= 0) return POLAR_ECUDA;
+    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
+    const uint64_t need_ctas = ((uint64_t)n_frames + sh.groups_per_cta - 1) / sh.groups_per_cta;
+    if (grid > need_ctas) grid = need_ctas;
+    uint8_t *scratch = nullptr;
+    const uint64_t per_cta = (uint64_t)sh.groups_per_cta * sh.lay.gbytes;
+    if (per_cta > 0) {
+        // The kernel is persistent, so fewer CTAs still decode every frame;
+        // a shape whose single CTA needs more than the array is refused.
+        if (per_cta > kNoAllocScratchBytes) return POLAR_EUNSUPPORTED;
+        const uint64_t fit = kNoAllocScratchBytes / per_cta;
+        if (grid > fit) grid = fit;
+        const int st = noalloc_scratch(dev, &scratch);
+        if (st != POLAR_OK) return st;
+    }
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.ops = sh.d_ops;
+    p.n_ops = (int)code->ops.size();
+    p.N = (int)code->N;
+    p.n = (int)code->n;
+    p.L = (int)code->L;
+    p.K = (int)code->K;
+    p.k = (int)code->k;
+    p.crc_len = (int)code->crc_len;
+    p.llr = llr_dev;
+    p.bits = info_bits_dev;
+    p.kb = (int)((code->k + 7) / 8);
+    p.pm = path_metric_dev;
+    p.ok = crc_ok_dev;
+    p.slot = winner_slot_dev;
+    p.syn = code->d_syn;
+    p.info = code->d_info;
+    p.n_frames = n_frames;
+    p.groups_per_cta = sh.groups_per_cta;
+    p.lay = sh.lay;
+    p.scratch = scratch;
+    const cudaError_t e = launch_decode(llr_dtype, sh, p, (int)grid, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+size_t polar_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
 
 int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
     if (!c || !info) return POLAR_EINVAL;

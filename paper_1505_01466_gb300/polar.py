@@ -24,7 +24,7 @@ SPC_MAX_4, SPC_ANY, NO_SPECIAL_NODES, HOST_ONLY = 0, 1, 2, 0x100
 EXPORTED = [
     "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror",
     "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
-    "polar_code_autotune",
+    "polar_code_autotune", "polar_list_decode_noalloc", "polar_noalloc_scratch_bytes",
 ]
 
 
@@ -65,9 +65,12 @@ def _lib():
         lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
         lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32]
         lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.polar_list_decode_noalloc.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
+        lib.polar_noalloc_scratch_bytes.argtypes = []
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32
+        lib.polar_noalloc_scratch_bytes.restype = ctypes.c_size_t
         _LIB = lib
     return _LIB
 
