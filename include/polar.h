@@ -173,6 +173,63 @@ POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t 
 POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out);
 
+/* ---- Batched form --------------------------------------------------------
+ * Frames of several codes (mixed N, rate and L) decoded by one persistent
+ * launch. Frame f uses codes[frame_code[f]]; its LLRs start at byte
+ * llr_offset[f] of one packed device buffer (rows of N_f elements in frame
+ * order) and its payload at byte bits_offset[f] of one packed output buffer
+ * (rows of ceil(k_f/8) bytes); polar_batch_layout reports both. Work items are
+ * ordered by decreasing decode cost and taken from a device counter by the
+ * frame groups of the persistent kernel, so large and small codes share the
+ * GPU without one launch per code. All codes must be created on the current
+ * device; the plan keeps pointers to them (destroy the plan first). The plan
+ * owns its device tables and global scratch (allocated at plan / shape time,
+ * so runs and graph replays allocate nothing). Results are identical to
+ * polar_list_decode of each frame with its code. */
+typedef struct polar_batch polar_batch_t;
+
+typedef struct {
+    uint32_t n_frames, n_codes;
+    uint32_t warps_per_frame, frames_per_cta;
+    uint32_t smem_per_frame;       /* bytes per frame group (largest class) */
+    uint32_t grid;                 /* CTAs of the persistent launch */
+    uint64_t scratch_bytes;        /* global scratch owned by the plan */
+    uint64_t llr_bytes, bits_bytes;/* sizes of the packed input / output buffers */
+} polar_batch_info_t;
+
+/* frame_code: host [n_frames], values < n_codes; flags must be 0. Errors:
+ * POLAR_EINVAL (bad handle, index, dtype, code on another device),
+ * POLAR_ENOMEM, POLAR_ECUDA. */
+POLAR_API int polar_batch_plan(polar_batch_t **out, polar_code_t *const *codes, uint32_t n_codes,
+                               const uint32_t *frame_code, uint32_t n_frames, int llr_dtype, uint32_t flags);
+POLAR_API int polar_batch_destroy(polar_batch_t *batch);
+/* Sizes of the packed buffers and (optionally, host arrays of n_frames) the
+ * per-frame byte offsets. */
+POLAR_API int polar_batch_layout(const polar_batch_t *batch, uint64_t *llr_bytes, uint64_t *bits_bytes,
+                                 uint64_t *llr_offsets, uint64_t *bits_offsets);
+/* Enqueue the batched decode on `stream`: llr_dev (packed input), bits_dev
+ * (packed payload output), pm_dev [n_frames] penalties, ok_dev / slot_dev
+ * [n_frames] (may be NULL). Runs of one plan must not overlap on the GPU
+ * (they share the plan's work counter and scratch). */
+POLAR_API int polar_batch_run(polar_batch_t *batch, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
+                              uint8_t *ok_dev, int32_t *slot_dev, polar_stream_t stream);
+/* Choose warps per frame and the shared-memory budget per frame (larger
+ * alpha stages go to the plan's global scratch). */
+POLAR_API int polar_batch_set_launch(polar_batch_t *batch, uint32_t warps_per_frame, uint32_t smem_budget);
+/* Autotuner: times every (warps per frame, budget) shape on the plan's own
+ * frames (llr_dev as for polar_batch_run; bits_dev / pm_dev are scratch
+ * outputs), keeps the fastest, reports it. Blocks until done. */
+POLAR_API int polar_batch_autotune(polar_batch_t *batch, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
+                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out);
+/* Capture one run (counter reset + persistent launch) into a CUDA graph owned
+ * by the plan, for the given buffers; `stream` must not be the legacy default
+ * stream. polar_batch_replay launches that graph on any stream. A later
+ * set_launch / autotune / capture drops the graph. */
+POLAR_API int polar_batch_capture(polar_batch_t *batch, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
+                                  uint8_t *ok_dev, int32_t *slot_dev, polar_stream_t stream);
+POLAR_API int polar_batch_replay(polar_batch_t *batch, polar_stream_t stream);
+POLAR_API int polar_batch_get_info(const polar_batch_t *batch, polar_batch_info_t *info);
+
 /* Allocation-free variant of polar_list_decode. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory while decoding -- work captured into a CUDA graph that must

@@ -259,6 +259,24 @@ int install_shape(polar_code *c, int dtype, const LaunchShape &sh) {
     return POLAR_OK;
 }
 
+CodeView make_view(const polar_code *code, const LaunchShape &sh) {
+    CodeView v;
+    std::memset(&v, 0, sizeof(v));
+    v.ops = sh.d_ops;
+    v.syn = code->d_syn;
+    v.info = code->d_info;
+    v.n_ops = (int)code->ops.size();
+    v.N = (int)code->N;
+    v.n = (int)code->n;
+    v.L = (int)code->L;
+    v.K = (int)code->K;
+    v.k = (int)code->k;
+    v.kb = (int)((code->k + 7) / 8);
+    v.crc_len = (int)code->crc_len;
+    v.lay = sh.lay;
+    return v;
+}
+
 // Launch a decode of n_frames with an explicit shape.
 int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const void *llr, uint32_t n_frames,
                  uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot, cudaStream_t st) {
@@ -269,25 +287,14 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
     if (grid > need_ctas) grid = need_ctas;
     Params p;
     std::memset(&p, 0, sizeof(p));
-    p.ops = sh.d_ops;
-    p.n_ops = (int)code->ops.size();
-    p.N = (int)code->N;
-    p.n = (int)code->n;
-    p.L = (int)code->L;
-    p.K = (int)code->K;
-    p.k = (int)code->k;
-    p.crc_len = (int)code->crc_len;
+    p.cv = make_view(code, sh);
     p.llr = llr;
     p.bits = bits;
-    p.kb = (int)((code->k + 7) / 8);
     p.pm = pm;
     p.ok = ok;
     p.slot = slot;
-    p.syn = code->d_syn;
-    p.info = code->d_info;
     p.n_frames = n_frames;
     p.groups_per_cta = sh.groups_per_cta;
-    p.lay = sh.lay;
     void *scratch = nullptr;
     if (sh.lay.gbytes > 0) {
         const size_t bytes = (size_t)grid * sh.groups_per_cta * sh.lay.gbytes;
@@ -522,31 +529,296 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
     }
     Params p;
     std::memset(&p, 0, sizeof(p));
-    p.ops = sh.d_ops;
-    p.n_ops = (int)code->ops.size();
-    p.N = (int)code->N;
-    p.n = (int)code->n;
-    p.L = (int)code->L;
-    p.K = (int)code->K;
-    p.k = (int)code->k;
-    p.crc_len = (int)code->crc_len;
+    p.cv = make_view(code, sh);
     p.llr = llr_dev;
     p.bits = info_bits_dev;
-    p.kb = (int)((code->k + 7) / 8);
     p.pm = path_metric_dev;
     p.ok = crc_ok_dev;
     p.slot = winner_slot_dev;
-    p.syn = code->d_syn;
-    p.info = code->d_info;
     p.n_frames = n_frames;
     p.groups_per_cta = sh.groups_per_cta;
-    p.lay = sh.lay;
     p.scratch = scratch;
     const cudaError_t e = launch_decode(llr_dtype, sh, p, (int)grid, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 size_t polar_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
+// ---- batched form ------------------------------------------------------------
+struct polar_batch {
+    int dtype = 0;
+    int device = -1;
+    int sm_count = 0;
+    uint32_t n_frames = 0;
+    std::vector<const polar_code *> codes;
+    std::vector<uint32_t> frame_code;
+    std::vector<uint64_t> llr_off, bits_off;
+    uint64_t llr_bytes = 0, bits_bytes = 0;
+    // current launch shape
+    int warps = 4;
+    uint32_t budget = 0;
+    int groups_per_cta = 1;
+    uint32_t group_bytes = 0, view_bytes = 0, cta_smem = 0;
+    uint64_t gbytes = 0;
+    int grid = 0;
+    // device state
+    std::vector<uint32_t *> d_ops;     // per class, flagged for `warps`
+    CodeView *d_classes = nullptr;
+    BatchItem *d_items = nullptr;
+    uint32_t *d_counter = nullptr;
+    uint8_t *d_scratch = nullptr;
+    uint64_t scratch_bytes = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+void batch_free_shape(polar_batch *b) {
+    for (uint32_t *p : b->d_ops) if (p) cudaFree(p);
+    b->d_ops.clear();
+    if (b->d_classes) cudaFree(b->d_classes);
+    if (b->d_scratch) cudaFree(b->d_scratch);
+    b->d_classes = nullptr;
+    b->d_scratch = nullptr;
+    b->scratch_bytes = 0;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// Lay out every class for `warps` warps per frame and a shared-memory budget
+// per frame, upload the class table and size the global scratch.
+int batch_shape(polar_batch *b, int warps, uint32_t budget) {
+    if (warps != 1 && warps != 2 && warps != 4) return POLAR_EINVAL;
+    const int gpc = 4 / warps;
+    const uint32_t view_bytes = al16((uint32_t)sizeof(CodeView) + 16u);
+    if (budget == 0) budget = (kMaxSmemPerCta / (warps == 4 ? 4u : (warps == 2 ? 6u : 8u))) & ~15u;
+    budget = std::min<uint32_t>(budget, kMaxSmemPerCta / gpc - view_bytes);
+    const uint32_t es = b->dtype == POLAR_LLR_I8 ? 1u : 4u;
+    std::vector<CodeView> views(b->codes.size());
+    uint32_t gb = 0;
+    uint64_t gs = 0;
+    for (size_t c = 0; c < b->codes.size(); ++c) {
+        Layout lay;
+        if (!build_layout(b->codes[c]->n, b->codes[c]->L, es, budget, lay)) return POLAR_EINVAL;
+        LaunchShape sh;
+        std::memset(&sh, 0, sizeof(sh));
+        sh.lay = lay;
+        views[c] = make_view(b->codes[c], sh);
+        gb = std::max(gb, lay.bytes);
+        gs = std::max<uint64_t>(gs, lay.gbytes);
+    }
+    const uint32_t group_bytes = view_bytes + gb;
+    const uint32_t cta_smem = group_bytes * (uint32_t)gpc;
+    if (cta_smem > kMaxSmemPerCta) return POLAR_EINVAL;
+    const int occ = occupancy_batch(b->dtype, warps, cta_smem);
+    if (occ <= 0) return POLAR_ECUDA;
+    batch_free_shape(b);
+    for (size_t c = 0; c < b->codes.size(); ++c) {
+        uint32_t *d = nullptr;
+        if (upload(&d, flag_ops(b->codes[c]->ops, (uint32_t)warps)) != cudaSuccess) return POLAR_ECUDA;
+        b->d_ops.push_back(d);
+        views[c].ops = d;
+    }
+    if (upload(&b->d_classes, views) != cudaSuccess) return POLAR_ECUDA;
+    uint64_t grid = (uint64_t)occ * (uint64_t)b->sm_count;
+    const uint64_t need = ((uint64_t)b->n_frames + gpc - 1) / gpc;
+    if (grid > need) grid = need;
+    if (grid == 0) grid = 1;
+    b->scratch_bytes = grid * (uint64_t)gpc * gs;
+    if (b->scratch_bytes > 0) {
+        if (cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) return POLAR_ENOMEM;
+    }
+    b->warps = warps;
+    b->budget = budget;
+    b->groups_per_cta = gpc;
+    b->group_bytes = group_bytes;
+    b->view_bytes = view_bytes;
+    b->cta_smem = cta_smem;
+    b->gbytes = gs;
+    b->grid = (int)grid;
+    return POLAR_OK;
+}
+
+int batch_launch(polar_batch *b, const void *llr, uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot,
+                 cudaStream_t st) {
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return POLAR_ECUDA;
+    BatchParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.classes = b->d_classes;
+    p.items = b->d_items;
+    p.n_items = b->n_frames;
+    p.counter = b->d_counter;
+    p.llr = (const uint8_t *)llr;
+    p.bits = bits;
+    p.pm = pm;
+    p.ok = ok;
+    p.slot = slot;
+    p.scratch = b->d_scratch;
+    p.gbytes = b->gbytes;
+    p.group_bytes = b->group_bytes;
+    p.view_bytes = b->view_bytes;
+    p.groups_per_cta = b->groups_per_cta;
+    return launch_batch(b->dtype, b->warps, p, b->grid, b->cta_smem, st) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+}  // namespace
+
+int polar_batch_plan(polar_batch_t **out, polar_code_t *const *codes, uint32_t n_codes, const uint32_t *frame_code,
+                     uint32_t n_frames, int llr_dtype, uint32_t flags) {
+    if (!out) return POLAR_EINVAL;
+    *out = nullptr;
+    if (!codes || n_codes == 0 || (!frame_code && n_frames > 0) || flags != 0) return POLAR_EINVAL;
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
+    for (uint32_t c = 0; c < n_codes; ++c)
+        if (!codes[c] || codes[c]->host_only || codes[c]->device != dev) return POLAR_EINVAL;
+    for (uint32_t f = 0; f < n_frames; ++f)
+        if (frame_code[f] >= n_codes) return POLAR_EINVAL;
+    polar_batch *b = new (std::nothrow) polar_batch();
+    if (!b) return POLAR_ENOMEM;
+    b->dtype = llr_dtype;
+    b->device = dev;
+    b->sm_count = codes[0]->sm_count;
+    b->n_frames = n_frames;
+    b->codes.assign(codes, codes + n_codes);
+    b->frame_code.assign(frame_code, frame_code + n_frames);
+    const uint64_t es = llr_dtype == POLAR_LLR_I8 ? 1 : 4;
+    b->llr_off.resize(n_frames);
+    b->bits_off.resize(n_frames);
+    for (uint32_t f = 0; f < n_frames; ++f) {
+        const polar_code *c = codes[frame_code[f]];
+        b->llr_off[f] = b->llr_bytes;
+        b->bits_off[f] = b->bits_bytes;
+        b->llr_bytes += (uint64_t)c->N * es;
+        b->bits_bytes += (c->k + 7) / 8;
+    }
+    // work items: classes by decreasing cost, frames in order within a class
+    std::vector<uint64_t> cost(n_codes, 0);
+    for (uint32_t c = 0; c < n_codes; ++c) polar_code_op_count(codes[c], &cost[c]);
+    std::vector<uint32_t> order(n_codes);
+    for (uint32_t c = 0; c < n_codes; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t x) { return cost[a] > cost[x]; });
+    std::vector<std::vector<uint32_t>> per(n_codes);
+    for (uint32_t f = 0; f < n_frames; ++f) per[frame_code[f]].push_back(f);
+    std::vector<BatchItem> items;
+    items.reserve(n_frames);
+    for (uint32_t c : order)
+        for (uint32_t f : per[c]) items.push_back(BatchItem{c, f, b->llr_off[f], b->bits_off[f]});
+    int st = POLAR_OK;
+    if (upload(&b->d_items, items) != cudaSuccess || cudaMalloc(&b->d_counter, sizeof(uint32_t)) != cudaSuccess)
+        st = POLAR_ENOMEM;
+    if (st == POLAR_OK) st = batch_shape(b, 4, 0);
+    if (st != POLAR_OK) {
+        polar_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return POLAR_OK;
+}
+
+int polar_batch_destroy(polar_batch_t *b) {
+    if (!b) return POLAR_OK;
+    batch_free_shape(b);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_counter) cudaFree(b->d_counter);
+    delete b;
+    return POLAR_OK;
+}
+
+int polar_batch_layout(const polar_batch_t *b, uint64_t *llr_bytes, uint64_t *bits_bytes, uint64_t *llr_offsets,
+                       uint64_t *bits_offsets) {
+    if (!b) return POLAR_EINVAL;
+    if (llr_bytes) *llr_bytes = b->llr_bytes;
+    if (bits_bytes) *bits_bytes = b->bits_bytes;
+    if (llr_offsets) std::memcpy(llr_offsets, b->llr_off.data(), b->llr_off.size() * sizeof(uint64_t));
+    if (bits_offsets) std::memcpy(bits_offsets, b->bits_off.data(), b->bits_off.size() * sizeof(uint64_t));
+    return POLAR_OK;
+}
+
+int polar_batch_run(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, float *pm_dev, uint8_t *ok_dev,
+                    int32_t *slot_dev, polar_stream_t stream) {
+    if (!b || (b->n_frames > 0 && (!llr_dev || !pm_dev || !bits_dev))) return POLAR_EINVAL;
+    if (b->n_frames == 0) return POLAR_OK;
+    return batch_launch(b, llr_dev, bits_dev, pm_dev, ok_dev, slot_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int polar_batch_set_launch(polar_batch_t *b, uint32_t warps_per_frame, uint32_t smem_budget) {
+    if (!b) return POLAR_EINVAL;
+    return batch_shape(b, (int)warps_per_frame, smem_budget);
+}
+
+int polar_batch_autotune(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
+                         polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out) {
+    if (!b || !llr_dev || !bits_dev || !pm_dev) return POLAR_EINVAL;
+    if (b->n_frames == 0) return POLAR_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    static const uint32_t budgets[] = {0u, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u};
+    float best = 1e30f;
+    int bw = 0;
+    uint32_t bb = 0;
+    for (int w : {4, 2, 1}) {
+        for (uint32_t bud : budgets) {
+            if (batch_shape(b, w, bud) != POLAR_OK) continue;
+            if (batch_launch(b, llr_dev, bits_dev, pm_dev, nullptr, nullptr, st) != POLAR_OK) continue;
+            cudaEventRecord(e0, st);
+            const int rc = batch_launch(b, llr_dev, bits_dev, pm_dev, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || rc != POLAR_OK) continue;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bw = w; bb = bud; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bw == 0) return POLAR_ECUDA;
+    if (warps_out) *warps_out = (uint32_t)bw;
+    if (budget_out) *budget_out = bb;
+    return batch_shape(b, bw, bb);
+}
+
+int polar_batch_capture(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, float *pm_dev, uint8_t *ok_dev,
+                        int32_t *slot_dev, polar_stream_t stream) {
+    if (!b || b->n_frames == 0 || !llr_dev || !bits_dev || !pm_dev) return POLAR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!st) return POLAR_EINVAL;       // the legacy default stream cannot be captured
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return POLAR_ECUDA;
+    const int rc = batch_launch(b, llr_dev, bits_dev, pm_dev, ok_dev, slot_dev, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != POLAR_OK || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return POLAR_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    return ei == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+int polar_batch_replay(polar_batch_t *b, polar_stream_t stream) {
+    if (!b || !b->graph) return POLAR_EINVAL;
+    return cudaGraphLaunch(b->graph, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+int polar_batch_get_info(const polar_batch_t *b, polar_batch_info_t *info) {
+    if (!b || !info) return POLAR_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->n_frames = b->n_frames;
+    info->n_codes = (uint32_t)b->codes.size();
+    info->warps_per_frame = (uint32_t)b->warps;
+    info->frames_per_cta = (uint32_t)b->groups_per_cta;
+    info->smem_per_frame = b->group_bytes;
+    info->grid = (uint32_t)b->grid;
+    info->scratch_bytes = b->scratch_bytes;
+    info->llr_bytes = b->llr_bytes;
+    info->bits_bytes = b->bits_bytes;
+    return POLAR_OK;
+}
 
 int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
     if (!c || !info) return POLAR_EINVAL;

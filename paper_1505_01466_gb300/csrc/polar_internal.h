@@ -64,22 +64,50 @@ struct Layout {
     uint64_t gbytes;               // global scratch bytes per group
 };
 
-struct Params {
-    const uint32_t *ops;
+// Everything the decoder needs about one code (and one launch shape).
+struct CodeView {
+    const uint32_t *ops;           // schedule with solo / sync flags
+    const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
+    const uint16_t *info;          // [K] information positions, ascending
     int n_ops;
-    int N, n, L, K, k, crc_len;
+    int N, n, L, K, k, kb, crc_len;
+    Layout lay;
+};
+
+struct Params {                    // plain form: one code
+    CodeView cv;
     const void *llr;               // [n_frames][N]
     uint8_t *bits;                 // [n_frames][kb]
-    int kb;
     float *pm;
     uint8_t *ok;
     int32_t *slot;
-    const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
-    const uint16_t *info;          // [K] information positions, ascending
     uint32_t n_frames;
-    uint8_t *scratch;              // global scratch (spilled stages), gbytes per group
+    uint8_t *scratch;              // global scratch (spilled stages), lay.gbytes per group
     int groups_per_cta;
-    Layout lay;
+};
+
+struct BatchItem {                 // one frame of a batched launch
+    uint32_t cls;                  // index into the class table
+    uint32_t frame;                // output index (pm, ok, slot)
+    uint64_t llr_off;              // byte offset of the frame's LLR row
+    uint64_t bits_off;             // byte offset of the frame's payload row
+};
+
+struct BatchParams {               // batched form: frames of several codes
+    const CodeView *classes;
+    const BatchItem *items;        // ordered by decreasing cost
+    uint32_t n_items;
+    uint32_t *counter;             // work counter, zero at launch
+    const uint8_t *llr;
+    uint8_t *bits;
+    float *pm;
+    uint8_t *ok;
+    int32_t *slot;
+    uint8_t *scratch;
+    uint64_t gbytes;               // global scratch per group
+    uint32_t group_bytes;          // shared memory per group (view + frame region)
+    uint32_t view_bytes;           // CodeView copy + work slot, 16-byte aligned
+    int groups_per_cta;
 };
 
 struct LaunchShape {
@@ -96,4 +124,7 @@ cudaError_t launch_decode(int dtype, const LaunchShape &shape, const Params &p, 
                           cudaStream_t stream);
 // Resident CTAs per SM for a shape (0 if it cannot launch).
 int occupancy(int dtype, const LaunchShape &shape);
+// Batched form: 128-thread CTAs of `warps`-warp groups with `smem` bytes each.
+cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, cudaStream_t stream);
+int occupancy_batch(int dtype, int warps, uint32_t smem);
 }  // namespace polar

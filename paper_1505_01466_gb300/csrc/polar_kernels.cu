@@ -322,23 +322,20 @@ __device__ __forceinline__ P reg_tree(P (&x)[16], int nv) {
 }
 
 // ---------------------------------------------------------------------------
+// Decode one frame: channel row -> payload bits, penalty, CRC flag, slot.
+// Called by all W*32 threads of one frame group.
 template <typename T, int W>
-__global__ void __launch_bounds__(128) decode_kernel(const Params P) {
+__device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uint8_t *Gs, const uint8_t *src,
+                                             uint8_t *bits_row, float *pm_out, uint8_t *ok_out, int32_t *slot_out,
+                                             int gidx, int gtid) {
     typedef typename Arith<T>::P PT;
     typedef typename Arith<T>::K KT;
     constexpr KT KINF = Arith<T>::KINF;
     constexpr int GT = W * 32;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    const Layout &lay = P.lay;
-    const int gidx = threadIdx.x / GT;
-    const int gtid = threadIdx.x - gidx * GT;
-    const int lane = threadIdx.x & 31;
+    const Layout &lay = cv.lay;
+    const int lane = gtid & 31;
     const int wig = gtid >> 5;
-    uint8_t *S = smem_raw + (size_t)gidx * lay.bytes;
-    const int ggid = blockIdx.x * P.groups_per_cta + gidx;
-    const int ngroups = gridDim.x * P.groups_per_cta;
-    uint8_t *Gs = P.scratch ? P.scratch + (size_t)ggid * lay.gbytes : nullptr;
-    const int n = P.n, N = P.N, L = P.L;
+    const int n = cv.n, N = cv.N, L = cv.L;
     const int bwn = beta_words(n);
 
     T *chan = reinterpret_cast<T *>(S + lay.chan);
@@ -348,11 +345,10 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
     uint32_t *br = reinterpret_cast<uint32_t *>(S + lay.br);
     uint32_t *ubuf = reinterpret_cast<uint32_t *>(S + lay.ubuf);
 
-    for (uint32_t f = ggid; f < P.n_frames; f += ngroups) {
+    {
         // ---------------- channel LLRs -> stage n ----------------
         {
             const size_t nbytes = (size_t)N * sizeof(T);
-            const uint8_t *src = reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes;
             if (((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (nbytes & 15u) == 0) {
                 const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
                 uint4 *d4 = reinterpret_cast<uint4 *>(chan);
@@ -383,9 +379,9 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
         if (gtid == 0) reinterpret_cast<PT *>(S + lay.pen[0])[0] = (PT)0;
         gsync<W>(gidx);
 
-        uint32_t op = __ldg(P.ops);
-        for (int o = 0; o < P.n_ops; ++o) {
-            const uint32_t opn = (o + 1 < P.n_ops) ? __ldg(P.ops + o + 1) : 0u;
+        uint32_t op = __ldg(cv.ops);
+        for (int o = 0; o < cv.n_ops; ++o) {
+            const uint32_t opn = (o + 1 < cv.n_ops) ? __ldg(cv.ops + o + 1) : 0u;
             const uint32_t kind = op_kind(op);
             const int j = op_stage(op);
             const int dest = op_dest(op);
@@ -804,12 +800,12 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
         // ---------------- final pick (Sec. II-B) ----------------
         PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
         uint32_t *synb = reinterpret_cast<uint32_t *>(S + lay.cinfo);
-        if (P.crc_len > 0) {
+        if (cv.crc_len > 0) {
             const int nbytes = N >> 3;
             for (int p = wig; p < La; p += W) {
                 const uint8_t *xb = reinterpret_cast<const uint8_t *>(br + p * bwn);
                 uint32_t acc = 0;
-                for (int b = lane; b < nbytes; b += 32) acc ^= __ldg(P.syn + ((b << 8) | xb[b]));
+                for (int b = lane; b < nbytes; b += 32) acc ^= __ldg(cv.syn + ((b << 8) | xb[b]));
                 for (int off = 16; off >= 1; off >>= 1) acc ^= __shfl_xor_sync(FULL, acc, off);
                 if (lane == 0) synb[p] = acc;
             }
@@ -818,7 +814,7 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
         if (wig == 0) {
             unsigned long long key = ~0ull;
             if (lane < La) {
-                const bool okp = P.crc_len == 0 || synb[lane] == 0u;
+                const bool okp = cv.crc_len == 0 || synb[lane] == 0u;
                 key = ((unsigned long long)(okp ? 0u : 1u) << 63) |
                       ((unsigned long long)Arith<T>::pbits(penc[lane]) << 8) | (unsigned long long)lane;
             }
@@ -866,25 +862,79 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
                 if (r < R && w < bwn) ubuf[w] = U[r];
             }
             if (lane == 0) {
-                P.pm[f] = Arith<T>::to_out(penc[win]);
-                if (P.ok) P.ok[f] = (uint8_t)okw;
-                if (P.slot) P.slot[f] = win;
+                *pm_out = Arith<T>::to_out(penc[win]);
+                if (ok_out) *ok_out = (uint8_t)okw;
+                if (slot_out) *slot_out = win;
             }
         }
         gsync<W>(gidx);
-        for (int b = gtid; b < P.kb; b += GT) {
+        for (int b = gtid; b < cv.kb; b += GT) {
             uint32_t byte = 0;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const int pos = 8 * b + t;
-                if (pos < P.k) {
-                    const uint32_t u = __ldg(P.info + pos);
+                if (pos < cv.k) {
+                    const uint32_t u = __ldg(cv.info + pos);
                     byte |= ((ubuf[u >> 5] >> (u & 31u)) & 1u) << t;
                 }
             }
-            P.bits[(size_t)f * P.kb + b] = (uint8_t)byte;
+            bits_row[b] = (uint8_t)byte;
         }
         gsync<W>(gidx);
+    }
+}
+
+// Plain form: one code, frames f = group, group + n_groups, ...
+template <typename T, int W>
+__global__ void __launch_bounds__(128) decode_kernel(const Params P) {
+    constexpr int GT = W * 32;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int gidx = threadIdx.x / GT;
+    const int gtid = threadIdx.x - gidx * GT;
+    uint8_t *S = smem_raw + (size_t)gidx * P.cv.lay.bytes;
+    const int ggid = blockIdx.x * P.groups_per_cta + gidx;
+    const int ngroups = gridDim.x * P.groups_per_cta;
+    uint8_t *Gs = P.scratch ? P.scratch + (size_t)ggid * P.cv.lay.gbytes : nullptr;
+    const size_t nbytes = (size_t)P.cv.N * sizeof(T);
+    for (uint32_t f = ggid; f < P.n_frames; f += ngroups) {
+        decode_frame<T, W>(P.cv, S, Gs, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
+                           P.bits + (size_t)f * P.cv.kb, P.pm + f, P.ok ? P.ok + f : nullptr,
+                           P.slot ? P.slot + f : nullptr, gidx, gtid);
+    }
+}
+
+// Batched form: frames of several codes in one persistent launch. Groups take
+// work items (ordered by decreasing cost) from a device counter; the code of
+// an item is copied into the group's shared memory when it changes.
+template <typename T, int W>
+__global__ void __launch_bounds__(128) batch_kernel(const BatchParams B) {
+    constexpr int GT = W * 32;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int gidx = threadIdx.x / GT;
+    const int gtid = threadIdx.x - gidx * GT;
+    uint8_t *region = smem_raw + (size_t)gidx * B.group_bytes;
+    CodeView *cvs = reinterpret_cast<CodeView *>(region);
+    uint32_t *slot_word = reinterpret_cast<uint32_t *>(region + sizeof(CodeView));
+    uint8_t *S = region + B.view_bytes;
+    const int ggid = blockIdx.x * B.groups_per_cta + gidx;
+    uint8_t *Gs = B.scratch ? B.scratch + (size_t)ggid * B.gbytes : nullptr;
+    uint32_t loaded = 0xffffffffu;
+    for (;;) {
+        if (gtid == 0) *slot_word = atomicAdd(B.counter, 1u);
+        gsync<W>(gidx);
+        const uint32_t it = *slot_word;
+        gsync<W>(gidx);
+        if (it >= B.n_items) break;
+        const BatchItem item = B.items[it];
+        if (item.cls != loaded) {
+            const uint32_t *srcw = reinterpret_cast<const uint32_t *>(B.classes + item.cls);
+            uint32_t *dstw = reinterpret_cast<uint32_t *>(cvs);
+            for (int t = gtid; t < (int)(sizeof(CodeView) / 4); t += GT) dstw[t] = srcw[t];
+            loaded = item.cls;
+            gsync<W>(gidx);
+        }
+        decode_frame<T, W>(*cvs, S, Gs, B.llr + item.llr_off, B.bits + item.bits_off, B.pm + item.frame,
+                           B.ok ? B.ok + item.frame : nullptr, B.slot ? B.slot + item.frame : nullptr, gidx, gtid);
     }
 }
 
@@ -908,7 +958,50 @@ int occ_one(const LaunchShape &sh) {
     return nb;
 }
 
+template <typename T, int W>
+cudaError_t launch_batch_one(const BatchParams &b, int grid, uint32_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_kernel<T, W><<<grid, 128, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T, int W>
+int occ_batch_one(uint32_t smem) {
+    if (cudaFuncSetAttribute(batch_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T, W>, 128, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
 }  // namespace
+
+cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, cudaStream_t st) {
+    if (dtype == 0) {
+        if (warps == 1) return launch_batch_one<float, 1>(b, grid, smem, st);
+        if (warps == 2) return launch_batch_one<float, 2>(b, grid, smem, st);
+        if (warps == 4) return launch_batch_one<float, 4>(b, grid, smem, st);
+    } else {
+        if (warps == 1) return launch_batch_one<int8_t, 1>(b, grid, smem, st);
+        if (warps == 2) return launch_batch_one<int8_t, 2>(b, grid, smem, st);
+        if (warps == 4) return launch_batch_one<int8_t, 4>(b, grid, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int occupancy_batch(int dtype, int warps, uint32_t smem) {
+    if (dtype == 0) {
+        if (warps == 1) return occ_batch_one<float, 1>(smem);
+        if (warps == 2) return occ_batch_one<float, 2>(smem);
+        if (warps == 4) return occ_batch_one<float, 4>(smem);
+    } else {
+        if (warps == 1) return occ_batch_one<int8_t, 1>(smem);
+        if (warps == 2) return occ_batch_one<int8_t, 2>(smem);
+        if (warps == 4) return occ_batch_one<int8_t, 4>(smem);
+    }
+    return 0;
+}
 
 cudaError_t launch_decode(int dtype, const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
     if (dtype == 0) {

@@ -271,3 +271,39 @@ def pack_bits_lsb(bits: np.ndarray) -> np.ndarray:
 def unpack_bits_lsb(packed: np.ndarray, nbits: int) -> np.ndarray:
     return np.unpackbits(np.asarray(packed, dtype=np.uint8), axis=-1, count=nbits,
                          bitorder="little")
+
+
+# --------------------------------------------------------------------------
+# Mixed-code workloads (batched and serving forms).
+# --------------------------------------------------------------------------
+BATCH_NS = (256, 512, 1024, 2048, 4096)
+BATCH_RATES = (0.25, 0.5, 0.75, 0.84, 0.9)
+BATCH_LS = (2, 4, 8, 16, 32)
+
+
+def batch_classes(ns=BATCH_NS, rates=BATCH_RATES, ls=BATCH_LS):
+    """(N, K, L) for every class; K = round(rate * N) counts the CRC."""
+    return [(N, int(round(r * N)), L) for N in ns for r in rates for L in ls]
+
+
+def zipf_class_counts(n_frames: int, n_classes: int, seed: int, s: float = 1.2) -> np.ndarray:
+    """Frame count per class: Zipf(s) over class ranks, the ranks being a seeded
+    permutation of the classes; counts sum to n_frames (largest remainders)."""
+    rng = np.random.Generator(np.random.Philox(key=np.uint64(seed)))
+    rank_of = rng.permutation(n_classes)            # class c has rank rank_of[c] (0 = most frequent)
+    w = 1.0 / (rank_of + 1.0) ** s
+    p = w / w.sum()
+    raw = p * n_frames
+    counts = np.floor(raw).astype(np.int64)
+    rem = n_frames - int(counts.sum())
+    order = np.argsort(-(raw - counts), kind="stable")
+    counts[order[:rem]] += 1
+    return counts
+
+
+def frame_order(counts: np.ndarray, seed: int) -> np.ndarray:
+    """Class index of every frame, shuffled in arrival order (seeded)."""
+    rng = np.random.Generator(np.random.Philox(key=np.uint64(seed + 1)))
+    fc = np.repeat(np.arange(counts.size, dtype=np.uint32), counts)
+    rng.shuffle(fc)
+    return fc

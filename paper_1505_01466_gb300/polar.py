@@ -25,6 +25,8 @@ EXPORTED = [
     "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror",
     "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
     "polar_code_autotune", "polar_list_decode_noalloc", "polar_noalloc_scratch_bytes",
+    "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
+    "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
 ]
 
 
@@ -42,6 +44,14 @@ class CodeInfo(ctypes.Structure):
         ("n_spc", ctypes.c_uint32), ("warps_per_frame", ctypes.c_uint32 * 2),
         ("frames_per_cta", ctypes.c_uint32 * 2), ("smem_per_frame", ctypes.c_uint32 * 2),
         ("scratch_per_frame", ctypes.c_uint64 * 2), ("spill_mask", ctypes.c_uint32 * 2),
+    ]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_frames", ctypes.c_uint32), ("n_codes", ctypes.c_uint32), ("warps_per_frame", ctypes.c_uint32),
+        ("frames_per_cta", ctypes.c_uint32), ("smem_per_frame", ctypes.c_uint32), ("grid", ctypes.c_uint32),
+        ("scratch_bytes", ctypes.c_uint64), ("llr_bytes", ctypes.c_uint64), ("bits_bytes", ctypes.c_uint64),
     ]
 
 
@@ -67,6 +77,15 @@ def _lib():
         lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.polar_list_decode_noalloc.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
         lib.polar_noalloc_scratch_bytes.argtypes = []
+        lib.polar_batch_plan.argtypes = [ctypes.POINTER(vp), vp, u32, vp, u32, i32, u32]
+        lib.polar_batch_destroy.argtypes = [vp]
+        lib.polar_batch_layout.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), vp, vp]
+        lib.polar_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.polar_batch_set_launch.argtypes = [vp, u32, u32]
+        lib.polar_batch_autotune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.polar_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.polar_batch_replay.argtypes = [vp, vp]
+        lib.polar_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32
@@ -196,3 +215,74 @@ class PolarCode:
         slot = torch.empty(F, dtype=torch.int32, device=dev)
         self.decode_into(llr, bits, pm, ok, slot, stream)
         return bits, pm, ok, slot
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+class PolarBatch:
+    """Frames of several codes decoded by one persistent launch (batched form).
+
+    codes: list of PolarCode; frame_code: host int array [n_frames] of indices
+    into ``codes``; dtype: LLR_F32 or LLR_I8. Inputs / outputs are packed
+    buffers laid out by :meth:`layout`.
+    """
+
+    def __init__(self, codes, frame_code, dtype=LLR_I8):
+        self.codes = list(codes)
+        fc = np.ascontiguousarray(np.asarray(frame_code, dtype=np.uint32))
+        self.n_frames = int(fc.size)
+        self.dtype = int(dtype)
+        handles = (ctypes.c_void_p * len(self.codes))(*[c.handle.value for c in self.codes])
+        h = ctypes.c_void_p()
+        _check(_lib().polar_batch_plan(ctypes.byref(h), ctypes.cast(handles, ctypes.c_void_p), len(self.codes),
+                                       fc.ctypes.data_as(ctypes.c_void_p), self.n_frames, self.dtype, 0),
+               "polar_batch_plan")
+        self._h = h
+        self.frame_code = fc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().polar_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        """(llr_bytes, bits_bytes, llr_offsets [F] uint64, bits_offsets [F] uint64)."""
+        a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        lo = np.zeros(max(self.n_frames, 1), dtype=np.uint64)
+        bo = np.zeros(max(self.n_frames, 1), dtype=np.uint64)
+        _check(_lib().polar_batch_layout(self._h, ctypes.byref(a), ctypes.byref(b), lo.ctypes.data_as(ctypes.c_void_p),
+                                         bo.ctypes.data_as(ctypes.c_void_p)), "polar_batch_layout")
+        return int(a.value), int(b.value), lo[: self.n_frames], bo[: self.n_frames]
+
+    def info(self) -> dict:
+        bi = BatchInfo()
+        _check(_lib().polar_batch_get_info(self._h, ctypes.byref(bi)), "polar_batch_get_info")
+        return {name: int(getattr(bi, name)) for name, _ in BatchInfo._fields_}
+
+    def set_launch(self, warps_per_frame: int, smem_budget: int = 0):
+        _check(_lib().polar_batch_set_launch(self._h, warps_per_frame, smem_budget), "polar_batch_set_launch")
+
+    def run(self, llr, bits, pm, ok=None, slot=None, stream=None):
+        _check(_lib().polar_batch_run(self._h, _ptr(llr), _ptr(bits), _ptr(pm), _ptr(ok), _ptr(slot),
+                                      _stream_handle(stream)), "polar_batch_run")
+
+    def autotune(self, llr, bits, pm, stream=None):
+        w, b = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        _check(_lib().polar_batch_autotune(self._h, _ptr(llr), _ptr(bits), _ptr(pm), _stream_handle(stream),
+                                           ctypes.byref(w), ctypes.byref(b)), "polar_batch_autotune")
+        return int(w.value), int(b.value)
+
+    def capture(self, llr, bits, pm, ok=None, slot=None, stream=None):
+        _check(_lib().polar_batch_capture(self._h, _ptr(llr), _ptr(bits), _ptr(pm), _ptr(ok), _ptr(slot),
+                                          _stream_handle(stream)), "polar_batch_capture")
+
+    def replay(self, stream=None):
+        _check(_lib().polar_batch_replay(self._h, _stream_handle(stream)), "polar_batch_replay")

@@ -123,3 +123,13 @@ def test_pack_roundtrip():
     assert p.shape == (3, 2)
     assert p[0, 0] == sum(int(b[0, i]) << i for i in range(8))
     assert np.array_equal(I.unpack_bits_lsb(p, 13), b)
+
+
+def test_batch_zipf_mix_counts():
+    classes = I.batch_classes()
+    assert len(classes) == 125
+    counts = I.zipf_class_counts(1 << 20, 125, seed=1)
+    assert counts.sum() == 1 << 20 and (counts > 0).all()
+    assert counts.max() / counts.min() > 100          # uneven (Zipf s = 1.2)
+    fc = I.frame_order(counts, seed=1)
+    assert np.array_equal(np.bincount(fc, minlength=125), counts)
