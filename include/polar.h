@@ -230,6 +230,53 @@ POLAR_API int polar_batch_capture(polar_batch_t *batch, const void *llr_dev, uin
 POLAR_API int polar_batch_replay(polar_batch_t *batch, polar_stream_t stream);
 POLAR_API int polar_batch_get_info(const polar_batch_t *batch, polar_batch_info_t *info);
 
+/* ---- Serving form (continuous batching) ------------------------------------
+ * A request is n_frames frames of one code, submitted from the host at any
+ * time. A library-owned engine thread admits pending requests, in arrival
+ * order, as device memory (an arena of device_mem_budget bytes allocated at
+ * create) and frame slots (max_frames_in_flight) free up; copies their LLRs
+ * to the device; and launches everything admitted as one batched launch on
+ * one of three streams, while earlier batches are still running on the
+ * others -- so requests that arrive while others are on the GPU join the
+ * next batch and their work overlaps on the device. Results are copied back
+ * and kept until polled. Results equal polar_list_decode of the same frames
+ * (only timing depends on the mix). Latency = submit to results on the host. */
+typedef struct polar_server polar_server_t;
+
+typedef struct {
+    uint64_t completed, frames, info_bits;        /* since the last reset */
+    uint64_t pending, admitted, batches_in_flight;
+    uint64_t batches, max_batches_in_flight;     /* launches so far, most launches on the GPU at once */
+    double p50_us, p99_us, max_us, mean_us;       /* request latency (submit -> results on host) */
+    double span_us;                               /* first submit -> last completion */
+} polar_server_stats_t;
+
+enum { POLAR_SERVER_PAUSED = 1 };   /* create with admission paused (tests) */
+
+/* warps_per_frame 0 = 4; smem_budget 0 = default per-frame shared-memory budget. */
+POLAR_API int polar_server_create(polar_server_t **out, size_t device_mem_budget, uint32_t max_frames_in_flight,
+                                  uint32_t warps_per_frame, uint32_t smem_budget, uint32_t flags);
+/* Stops the engine after the batches in flight and frees everything; results
+ * not yet polled are dropped. */
+POLAR_API int polar_server_destroy(polar_server_t *server);
+/* Copies the host LLRs ([n_frames][N] of llr_dtype) and queues the request.
+ * POLAR_EINVAL if the request can never fit the arena / frame slots,
+ * POLAR_EBUSY if the pending queue is full (retry later). */
+POLAR_API int polar_server_submit(polar_server_t *server, const polar_code_t *code, const void *llr_host,
+                                  int llr_dtype, uint32_t n_frames, uint64_t *ticket);
+/* Non-blocking. *done = 1 and host outputs written (packed payload rows
+ * [n][ceil(k/8)], penalties, CRC flags; any may be NULL) when finished; the
+ * ticket is then released. */
+POLAR_API int polar_server_poll(polar_server_t *server, uint64_t ticket, uint8_t *bits_host, float *pm_host,
+                                uint8_t *ok_host, int *done);
+/* Bounded wait for one request: POLAR_OK when done, POLAR_ETIMEDOUT after
+ * timeout_ms, POLAR_ECUDA if the engine stopped on an error. */
+POLAR_API int polar_server_wait(polar_server_t *server, uint64_t ticket, uint32_t timeout_ms);
+/* Pause / resume admission (requests stay queued while paused). */
+POLAR_API int polar_server_pause(polar_server_t *server, int paused);
+/* Counters and latency percentiles; reset != 0 clears them afterwards. */
+POLAR_API int polar_server_stats(polar_server_t *server, polar_server_stats_t *stats, int reset);
+
 /* Allocation-free variant of polar_list_decode. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory while decoding -- work captured into a CUDA graph that must

@@ -7,11 +7,17 @@
 // sit in shared memory and which spill to global scratch).
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/polar.h"
@@ -887,6 +893,543 @@ int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_fra
     LaunchShape sh;
     if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh)) return POLAR_EINVAL;
     return install_shape(c, llr_dtype, sh);
+}
+
+}  // extern "C"
+
+// ---- serving form (continuous batching) ---------------------------------------
+namespace {
+
+double now_us() {
+    return (double)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count() * 1e-3;
+}
+
+// First-fit allocator over [0, size) with coalescing.
+struct RangeAlloc {
+    std::map<uint64_t, uint64_t> free_;
+    void init(uint64_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(uint64_t sz, uint64_t &off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= sz) {
+                off = it->first;
+                const uint64_t rem = it->second - sz, o2 = it->first + sz;
+                free_.erase(it);
+                if (rem) free_[o2] = rem;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t sz) {
+        if (!sz) return;
+        auto it = free_.emplace(off, sz).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct SrvReq {
+    uint64_t ticket = 0;
+    const polar_code *code = nullptr;
+    int dtype = 0;
+    uint32_t n = 0;
+    std::vector<uint8_t> llr;                 // host copy taken at submit
+    uint64_t arena_off = 0, arena_sz = 0, llr_sz = 0, bits_sz = 0;
+    uint64_t fslot = 0;                       // first frame slot
+    std::vector<uint8_t> bits, ok;
+    std::vector<float> pm;
+    bool done = false;
+    double t_submit = 0.0, t_done = 0.0;
+};
+
+constexpr int kSrvStreams = 3;
+constexpr uint32_t kSrvMaxCodes = 512;
+
+}  // namespace
+
+struct polar_server {
+    int device = -1, sm_count = 0;
+    uint64_t arena_bytes = 0;
+    uint32_t max_frames = 0, max_pending = 0;
+    int warps = 4;
+    uint32_t smem_budget = 0;
+    uint8_t *d_arena = nullptr, *h_arena = nullptr;
+    float *d_pm = nullptr, *h_pm = nullptr;
+    uint8_t *d_ok = nullptr, *h_ok = nullptr;
+    RangeAlloc arena, frames;
+    // registered codes: one class table per dtype
+    std::vector<const polar_code *> codes;
+    std::unordered_map<const polar_code *, uint32_t> code_idx;
+    std::vector<uint32_t *> class_ops;
+    CodeView *d_classes[2] = {nullptr, nullptr};
+    uint32_t frame_bytes[2] = {0, 0};         // largest per-frame shared layout
+    uint64_t gbytes[2] = {0, 0};              // largest per-frame global scratch
+    // streams, each with one batch in flight at most
+    cudaStream_t streams[kSrvStreams] = {};
+    cudaEvent_t done_ev[kSrvStreams] = {};
+    bool busy[kSrvStreams] = {};
+    std::vector<SrvReq *> batch[kSrvStreams];
+    uint32_t *d_counters = nullptr;
+    uint8_t *d_scratch[kSrvStreams] = {};
+    uint64_t scratch_sz[kSrvStreams] = {};
+    BatchItem *d_items[kSrvStreams] = {}, *h_items[kSrvStreams] = {};
+    uint64_t items_cap[kSrvStreams] = {};
+    // queues
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<SrvReq *> pending, admitted;
+    std::unordered_map<uint64_t, SrvReq *> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false, paused = false;
+    int error = POLAR_OK;
+    std::thread worker;
+    // statistics since the last reset
+    std::vector<double> lat_us;
+    uint64_t frames_done = 0, bits_done = 0, batches = 0, max_inflight = 0;
+    double t_first = 0.0, t_last = 0.0;
+};
+
+namespace {
+
+// Register a code: its class views (both dtypes) for the server's launch shape.
+int srv_register(polar_server *s, const polar_code *c, uint32_t &idx) {
+    auto it = s->code_idx.find(c);
+    if (it != s->code_idx.end()) { idx = it->second; return POLAR_OK; }
+    if (s->codes.size() >= kSrvMaxCodes) return POLAR_EUNSUPPORTED;
+    uint32_t *ops = nullptr;
+    if (upload(&ops, flag_ops(c->ops, (uint32_t)s->warps)) != cudaSuccess) return POLAR_ECUDA;
+    idx = (uint32_t)s->codes.size();
+    for (int d = 0; d < 2; ++d) {
+        Layout lay;
+        if (!build_layout(c->n, c->L, d == POLAR_LLR_I8 ? 1u : 4u, s->smem_budget, lay)) {
+            cudaFree(ops);
+            return POLAR_EUNSUPPORTED;
+        }
+        LaunchShape sh;
+        std::memset(&sh, 0, sizeof(sh));
+        sh.lay = lay;
+        sh.d_ops = ops;
+        CodeView v = make_view(c, sh);
+        if (cudaMemcpy(s->d_classes[d] + idx, &v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(ops);
+            return POLAR_ECUDA;
+        }
+        s->frame_bytes[d] = std::max(s->frame_bytes[d], lay.bytes);
+        if (lay.gbytes > s->gbytes[d]) s->gbytes[d] = lay.gbytes;
+    }
+    s->codes.push_back(c);
+    s->class_ops.push_back(ops);
+    s->code_idx[c] = idx;
+    return POLAR_OK;
+}
+
+uint32_t srv_view_bytes() { return al16((uint32_t)sizeof(CodeView) + 16u); }
+
+// Shared memory per CTA and grid for a dtype's batches.
+void srv_shape(const polar_server *s, int d, uint32_t &group_bytes, uint32_t &cta_smem, int &gpc) {
+    gpc = 4 / s->warps;
+    group_bytes = srv_view_bytes() + s->frame_bytes[d];
+    cta_smem = group_bytes * (uint32_t)gpc;
+}
+
+// Admit a pending request if its memory fits: copy its LLRs to the pinned
+// mirror of its arena region (the copy to the device goes with its batch).
+bool srv_admit(polar_server *s, SrvReq *r) {
+    uint32_t idx;
+    if (srv_register(s, r->code, idx) != POLAR_OK) return false;
+    const uint64_t es = r->dtype == POLAR_LLR_I8 ? 1 : 4;
+    r->llr_sz = (uint64_t)r->n * r->code->N * es;
+    r->bits_sz = (uint64_t)r->n * ((r->code->k + 7) / 8);
+    r->arena_sz = ((r->llr_sz + 255) & ~uint64_t(255)) + ((r->bits_sz + 255) & ~uint64_t(255));
+    uint64_t off = 0, fs = 0;
+    if (!s->arena.alloc(r->arena_sz, off)) return false;
+    if (!s->frames.alloc(r->n, fs)) {
+        s->arena.release(off, r->arena_sz);
+        return false;
+    }
+    r->arena_off = off;
+    r->fslot = fs;
+    std::memcpy(s->h_arena + off, r->llr.data(), r->llr_sz);
+    return true;
+}
+
+int srv_grow_scratch(polar_server *s, int stream, uint64_t need) {
+    if (need <= s->scratch_sz[stream]) return POLAR_OK;
+    if (s->d_scratch[stream]) {
+        cudaStreamSynchronize(s->streams[stream]);
+        cudaFree(s->d_scratch[stream]);
+        s->d_scratch[stream] = nullptr;
+        s->scratch_sz[stream] = 0;
+    }
+    if (cudaMalloc(&s->d_scratch[stream], need) != cudaSuccess) return POLAR_ENOMEM;
+    s->scratch_sz[stream] = need;
+    return POLAR_OK;
+}
+
+// Launch every admitted request of one dtype as one batch on stream i.
+int srv_launch(polar_server *s, int i) {
+    const int d = s->admitted.front()->dtype;
+    std::vector<SrvReq *> take;
+    std::deque<SrvReq *> rest;
+    for (SrvReq *r : s->admitted) {
+        if (r->dtype == d) take.push_back(r);
+        else rest.push_back(r);
+    }
+    s->admitted.swap(rest);
+    uint64_t n_items = 0;
+    for (SrvReq *r : take) n_items += r->n;
+    if (n_items > s->items_cap[i]) {
+        if (s->d_items[i]) cudaFree(s->d_items[i]);
+        if (s->h_items[i]) cudaFreeHost(s->h_items[i]);
+        s->d_items[i] = nullptr;
+        s->h_items[i] = nullptr;
+        s->items_cap[i] = 0;
+        const uint64_t cap = std::max<uint64_t>(n_items, 4096);
+        if (cudaMalloc(&s->d_items[i], cap * sizeof(BatchItem)) != cudaSuccess ||
+            cudaMallocHost(&s->h_items[i], cap * sizeof(BatchItem)) != cudaSuccess)
+            return POLAR_ENOMEM;
+        s->items_cap[i] = cap;
+    }
+    // items: larger codes first
+    std::vector<SrvReq *> ord = take;
+    std::stable_sort(ord.begin(), ord.end(), [](SrvReq *a, SrvReq *b) {
+        return (uint64_t)a->code->N * a->code->L > (uint64_t)b->code->N * b->code->L;
+    });
+    const uint64_t es = d == POLAR_LLR_I8 ? 1 : 4;
+    uint64_t t = 0;
+    for (SrvReq *r : ord) {
+        const uint32_t cls = s->code_idx[r->code];
+        const uint64_t kb = (r->code->k + 7) / 8;
+        const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
+        for (uint32_t f = 0; f < r->n; ++f)
+            s->h_items[i][t++] = BatchItem{cls, (uint32_t)(r->fslot + f), r->arena_off + (uint64_t)f * r->code->N * es,
+                                           bits_base + f * kb};
+    }
+    cudaStream_t st = s->streams[i];
+    uint32_t group_bytes, cta_smem;
+    int gpc;
+    srv_shape(s, d, group_bytes, cta_smem, gpc);
+    const int occ = occupancy_batch(d, s->warps, cta_smem);
+    if (occ <= 0) return POLAR_ECUDA;
+    uint64_t grid = (uint64_t)occ * s->sm_count;
+    const uint64_t need = (n_items + gpc - 1) / gpc;
+    if (grid > need) grid = need;
+    int rc = srv_grow_scratch(s, i, (uint64_t)occ * s->sm_count * gpc * s->gbytes[d]);
+    if (rc != POLAR_OK) return rc;
+    bool okc = cudaMemcpyAsync(s->d_items[i], s->h_items[i], n_items * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                               st) == cudaSuccess;
+    for (SrvReq *r : take)
+        okc &= cudaMemcpyAsync(s->d_arena + r->arena_off, s->h_arena + r->arena_off, r->llr_sz, cudaMemcpyHostToDevice,
+                               st) == cudaSuccess;
+    okc &= cudaMemsetAsync(s->d_counters + i, 0, sizeof(uint32_t), st) == cudaSuccess;
+    BatchParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.classes = s->d_classes[d];
+    p.items = s->d_items[i];
+    p.n_items = (uint32_t)n_items;
+    p.counter = s->d_counters + i;
+    p.llr = s->d_arena;
+    p.bits = s->d_arena;
+    p.pm = s->d_pm;
+    p.ok = s->d_ok;
+    p.slot = nullptr;
+    p.scratch = s->d_scratch[i];
+    p.gbytes = s->gbytes[d];
+    p.group_bytes = group_bytes;
+    p.view_bytes = srv_view_bytes();
+    p.groups_per_cta = gpc;
+    okc &= launch_batch(d, s->warps, p, (int)grid, cta_smem, st) == cudaSuccess;
+    for (SrvReq *r : take) {
+        const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
+        okc &= cudaMemcpyAsync(s->h_arena + bits_base, s->d_arena + bits_base, r->bits_sz, cudaMemcpyDeviceToHost,
+                               st) == cudaSuccess;
+        okc &= cudaMemcpyAsync(s->h_pm + r->fslot, s->d_pm + r->fslot, r->n * sizeof(float), cudaMemcpyDeviceToHost,
+                               st) == cudaSuccess;
+        okc &= cudaMemcpyAsync(s->h_ok + r->fslot, s->d_ok + r->fslot, r->n, cudaMemcpyDeviceToHost, st) ==
+               cudaSuccess;
+    }
+    okc &= cudaEventRecord(s->done_ev[i], st) == cudaSuccess;
+    s->busy[i] = true;
+    s->batch[i] = take;
+    ++s->batches;
+    uint64_t inflight = 0;
+    for (int q = 0; q < kSrvStreams; ++q) inflight += s->busy[q] ? 1u : 0u;
+    s->max_inflight = std::max(s->max_inflight, inflight);
+    return okc ? POLAR_OK : POLAR_ECUDA;
+}
+
+void srv_finish(polar_server *s, int i) {
+    const double t = now_us();
+    for (SrvReq *r : s->batch[i]) {
+        const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
+        r->bits.assign(s->h_arena + bits_base, s->h_arena + bits_base + r->bits_sz);
+        r->pm.assign(s->h_pm + r->fslot, s->h_pm + r->fslot + r->n);
+        r->ok.assign(s->h_ok + r->fslot, s->h_ok + r->fslot + r->n);
+        s->arena.release(r->arena_off, r->arena_sz);
+        s->frames.release(r->fslot, r->n);
+        r->llr.clear();
+        r->llr.shrink_to_fit();
+        r->done = true;
+        r->t_done = t;
+        s->lat_us.push_back(t - r->t_submit);
+        s->frames_done += r->n;
+        s->bits_done += (uint64_t)r->n * r->code->k;
+        if (s->t_first == 0.0 || r->t_submit < s->t_first) s->t_first = r->t_submit;
+        s->t_last = t;
+    }
+    s->batch[i].clear();
+    s->busy[i] = false;
+}
+
+void srv_engine(polar_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool progress = false;
+        for (int i = 0; i < kSrvStreams; ++i) {
+            if (!s->busy[i]) continue;
+            const cudaError_t q = cudaEventQuery(s->done_ev[i]);
+            if (q == cudaSuccess) {
+                srv_finish(s, i);
+                progress = true;
+            } else if (q != cudaErrorNotReady) {
+                s->error = POLAR_ECUDA;
+                s->stop = true;
+            }
+        }
+        if (progress) s->cv.notify_all();
+        if (!s->paused) {
+            while (!s->pending.empty() && srv_admit(s, s->pending.front())) {
+                s->admitted.push_back(s->pending.front());
+                s->pending.pop_front();
+                progress = true;
+            }
+            for (int i = 0; i < kSrvStreams && !s->admitted.empty(); ++i) {
+                if (s->busy[i]) continue;
+                const int rc = srv_launch(s, i);
+                if (rc != POLAR_OK) {
+                    s->error = rc;
+                    s->stop = true;
+                    break;
+                }
+                progress = true;
+            }
+        }
+        if (!progress) s->cv.wait_for(lk, std::chrono::microseconds(40));
+    }
+    s->cv.notify_all();
+}
+
+void srv_free(polar_server *s) {
+    for (int i = 0; i < kSrvStreams; ++i) {
+        if (s->streams[i]) cudaStreamSynchronize(s->streams[i]);
+        if (s->d_scratch[i]) cudaFree(s->d_scratch[i]);
+        if (s->d_items[i]) cudaFree(s->d_items[i]);
+        if (s->h_items[i]) cudaFreeHost(s->h_items[i]);
+        if (s->done_ev[i]) cudaEventDestroy(s->done_ev[i]);
+        if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
+    }
+    for (uint32_t *p : s->class_ops) cudaFree(p);
+    for (int d = 0; d < 2; ++d) if (s->d_classes[d]) cudaFree(s->d_classes[d]);
+    if (s->d_counters) cudaFree(s->d_counters);
+    if (s->d_arena) cudaFree(s->d_arena);
+    if (s->h_arena) cudaFreeHost(s->h_arena);
+    if (s->d_pm) cudaFree(s->d_pm);
+    if (s->h_pm) cudaFreeHost(s->h_pm);
+    if (s->d_ok) cudaFree(s->d_ok);
+    if (s->h_ok) cudaFreeHost(s->h_ok);
+    for (auto &kv : s->reqs) delete kv.second;
+    s->reqs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int polar_server_create(polar_server_t **out, size_t device_mem_budget, uint32_t max_frames_in_flight,
+                        uint32_t warps_per_frame, uint32_t smem_budget, uint32_t flags) {
+    if (!out) return POLAR_EINVAL;
+    *out = nullptr;
+    if (device_mem_budget < 4096 || max_frames_in_flight == 0 || (flags & ~POLAR_SERVER_PAUSED)) return POLAR_EINVAL;
+    if (warps_per_frame == 0) warps_per_frame = 4;
+    if (warps_per_frame != 1 && warps_per_frame != 2 && warps_per_frame != 4) return POLAR_EINVAL;
+    polar_server *s = new (std::nothrow) polar_server();
+    if (!s) return POLAR_ENOMEM;
+    s->warps = (int)warps_per_frame;
+    const uint32_t gpc = 4u / warps_per_frame;
+    const uint32_t cap = kMaxSmemPerCta / gpc - al16((uint32_t)sizeof(CodeView) + 16u);
+    s->smem_budget = smem_budget ? std::min(smem_budget, cap)
+                                 : std::min(cap, (kMaxSmemPerCta / (warps_per_frame == 4 ? 4u : (warps_per_frame == 2 ? 6u : 8u))) & ~15u);
+    s->arena_bytes = device_mem_budget;
+    s->max_frames = max_frames_in_flight;
+    s->max_pending = 1u << 16;
+    s->paused = (flags & POLAR_SERVER_PAUSED) != 0;
+    int st = POLAR_OK;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+        st = POLAR_ECUDA;
+    if (st == POLAR_OK &&
+        (cudaMalloc(&s->d_arena, device_mem_budget) != cudaSuccess ||
+         cudaMallocHost(&s->h_arena, device_mem_budget) != cudaSuccess ||
+         cudaMalloc(&s->d_pm, sizeof(float) * max_frames_in_flight) != cudaSuccess ||
+         cudaMallocHost(&s->h_pm, sizeof(float) * max_frames_in_flight) != cudaSuccess ||
+         cudaMalloc(&s->d_ok, max_frames_in_flight) != cudaSuccess ||
+         cudaMallocHost(&s->h_ok, max_frames_in_flight) != cudaSuccess ||
+         cudaMalloc(&s->d_counters, sizeof(uint32_t) * kSrvStreams) != cudaSuccess ||
+         cudaMalloc(&s->d_classes[0], sizeof(CodeView) * kSrvMaxCodes) != cudaSuccess ||
+         cudaMalloc(&s->d_classes[1], sizeof(CodeView) * kSrvMaxCodes) != cudaSuccess))
+        st = POLAR_ENOMEM;
+    for (int i = 0; st == POLAR_OK && i < kSrvStreams; ++i) {
+        if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->done_ev[i], cudaEventDisableTiming) != cudaSuccess)
+            st = POLAR_ECUDA;
+    }
+    if (st != POLAR_OK) {
+        srv_free(s);
+        delete s;
+        return st;
+    }
+    s->arena.init(device_mem_budget);
+    s->frames.init(max_frames_in_flight);
+    s->worker = std::thread(srv_engine, s);
+    *out = s;
+    return POLAR_OK;
+}
+
+int polar_server_destroy(polar_server_t *s) {
+    if (!s) return POLAR_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    srv_free(s);
+    delete s;
+    return POLAR_OK;
+}
+
+int polar_server_submit(polar_server_t *s, const polar_code_t *code, const void *llr_host, int llr_dtype,
+                        uint32_t n_frames, uint64_t *ticket) {
+    if (!s || !code || code->host_only || !llr_host || !ticket || n_frames == 0) return POLAR_EINVAL;
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    if (code->device != s->device) return POLAR_EINVAL;
+    const uint64_t es = llr_dtype == POLAR_LLR_I8 ? 1 : 4;
+    const uint64_t llr_sz = (uint64_t)n_frames * code->N * es;
+    const uint64_t need = ((llr_sz + 255) & ~uint64_t(255)) + (((uint64_t)n_frames * ((code->k + 7) / 8) + 255) & ~uint64_t(255));
+    if (need > s->arena_bytes || n_frames > s->max_frames) return POLAR_EINVAL;   // can never fit
+    SrvReq *r = new (std::nothrow) SrvReq();
+    if (!r) return POLAR_ENOMEM;
+    r->code = code;
+    r->dtype = llr_dtype;
+    r->n = n_frames;
+    r->llr.assign((const uint8_t *)llr_host, (const uint8_t *)llr_host + llr_sz);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->error != POLAR_OK) {
+            delete r;
+            return s->error;
+        }
+        if (s->pending.size() >= s->max_pending) {
+            delete r;
+            return POLAR_EBUSY;
+        }
+        r->ticket = s->next_ticket++;
+        r->t_submit = now_us();
+        s->reqs[r->ticket] = r;
+        s->pending.push_back(r);
+        *ticket = r->ticket;
+    }
+    s->cv.notify_all();
+    return POLAR_OK;
+}
+
+int polar_server_poll(polar_server_t *s, uint64_t ticket, uint8_t *bits_host, float *pm_host, uint8_t *ok_host,
+                      int *done) {
+    if (!s || !done) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return POLAR_EINVAL;
+    SrvReq *r = it->second;
+    if (!r->done) {
+        *done = 0;
+        return s->error;
+    }
+    if (bits_host) std::memcpy(bits_host, r->bits.data(), r->bits.size());
+    if (pm_host) std::memcpy(pm_host, r->pm.data(), r->pm.size() * sizeof(float));
+    if (ok_host) std::memcpy(ok_host, r->ok.data(), r->ok.size());
+    delete r;
+    s->reqs.erase(it);
+    *done = 1;
+    return POLAR_OK;
+}
+
+int polar_server_wait(polar_server_t *s, uint64_t ticket, uint32_t timeout_ms) {
+    if (!s) return POLAR_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return POLAR_EINVAL;
+    SrvReq *r = it->second;
+    const bool ok = s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                   [&] { return r->done || s->error != POLAR_OK; });
+    if (s->error != POLAR_OK) return s->error;
+    return ok ? POLAR_OK : POLAR_ETIMEDOUT;
+}
+
+int polar_server_pause(polar_server_t *s, int paused) {
+    if (!s) return POLAR_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->paused = paused != 0;
+    }
+    s->cv.notify_all();
+    return POLAR_OK;
+}
+
+int polar_server_stats(polar_server_t *s, polar_server_stats_t *out, int reset) {
+    if (!s || !out) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->completed = s->lat_us.size();
+    out->frames = s->frames_done;
+    out->info_bits = s->bits_done;
+    out->pending = s->pending.size();
+    out->admitted = s->admitted.size();
+    for (int i = 0; i < kSrvStreams; ++i) out->batches_in_flight += s->busy[i] ? 1u : 0u;
+    out->batches = s->batches;
+    out->max_batches_in_flight = s->max_inflight;
+    if (!s->lat_us.empty()) {
+        std::vector<double> v = s->lat_us;
+        std::sort(v.begin(), v.end());
+        auto q = [&](double p) { return v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+        out->p50_us = q(0.50);
+        out->p99_us = q(0.99);
+        out->max_us = v.back();
+        double sum = 0;
+        for (double x : v) sum += x;
+        out->mean_us = sum / v.size();
+        out->span_us = s->t_last - s->t_first;
+    }
+    if (reset) {
+        s->lat_us.clear();
+        s->frames_done = s->bits_done = s->batches = s->max_inflight = 0;
+        s->t_first = s->t_last = 0.0;
+    }
+    return s->error;
 }
 
 }  // extern "C"

@@ -27,6 +27,8 @@ EXPORTED = [
     "polar_code_autotune", "polar_list_decode_noalloc", "polar_noalloc_scratch_bytes",
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
+    "polar_server_create", "polar_server_destroy", "polar_server_submit", "polar_server_poll", "polar_server_wait",
+    "polar_server_pause", "polar_server_stats",
 ]
 
 
@@ -52,6 +54,16 @@ class BatchInfo(ctypes.Structure):
         ("n_frames", ctypes.c_uint32), ("n_codes", ctypes.c_uint32), ("warps_per_frame", ctypes.c_uint32),
         ("frames_per_cta", ctypes.c_uint32), ("smem_per_frame", ctypes.c_uint32), ("grid", ctypes.c_uint32),
         ("scratch_bytes", ctypes.c_uint64), ("llr_bytes", ctypes.c_uint64), ("bits_bytes", ctypes.c_uint64),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_uint64), ("frames", ctypes.c_uint64), ("info_bits", ctypes.c_uint64),
+        ("pending", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("batches_in_flight", ctypes.c_uint64),
+        ("batches", ctypes.c_uint64), ("max_batches_in_flight", ctypes.c_uint64),
+        ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+        ("mean_us", ctypes.c_double), ("span_us", ctypes.c_double),
     ]
 
 
@@ -86,6 +98,13 @@ def _lib():
         lib.polar_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.polar_batch_replay.argtypes = [vp, vp]
         lib.polar_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+        lib.polar_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, u32, u32, u32, u32]
+        lib.polar_server_destroy.argtypes = [vp]
+        lib.polar_server_submit.argtypes = [vp, vp, vp, i32, u32, ctypes.POINTER(u64)]
+        lib.polar_server_poll.argtypes = [vp, u64, vp, vp, vp, ctypes.POINTER(i32)]
+        lib.polar_server_wait.argtypes = [vp, u64, u32]
+        lib.polar_server_pause.argtypes = [vp, i32]
+        lib.polar_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats), i32]
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32
@@ -286,3 +305,74 @@ class PolarBatch:
 
     def replay(self, stream=None):
         _check(_lib().polar_batch_replay(self._h, _stream_handle(stream)), "polar_batch_replay")
+
+
+SERVER_PAUSED = 1
+
+
+class PolarServer:
+    """Continuous-batching decode server (see polar_server_* in include/polar.h)."""
+
+    def __init__(self, device_mem_budget=1 << 30, max_frames_in_flight=1 << 18, warps_per_frame=0,
+                 smem_budget=0, paused=False):
+        h = ctypes.c_void_p()
+        _check(_lib().polar_server_create(ctypes.byref(h), int(device_mem_budget), int(max_frames_in_flight),
+                                          int(warps_per_frame), int(smem_budget), SERVER_PAUSED if paused else 0),
+               "polar_server_create")
+        self._h = h
+        self._meta = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().polar_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, code, llr) -> int:
+        """Queue host LLRs ([F, N] float32 or int8 numpy array); returns a ticket."""
+        a = np.ascontiguousarray(llr)
+        dt = LLR_I8 if a.dtype == np.int8 else LLR_F32
+        if dt == LLR_F32:
+            a = np.ascontiguousarray(a, dtype=np.float32)
+        F = a.size // code.N
+        t = ctypes.c_uint64(0)
+        _check(_lib().polar_server_submit(self._h, code.handle, a.ctypes.data_as(ctypes.c_void_p), dt, F,
+                                          ctypes.byref(t)), "polar_server_submit")
+        self._meta[t.value] = (F, (code.k + 7) // 8)
+        return int(t.value)
+
+    def poll(self, ticket):
+        """None while running, else (bits [F, kb] uint8, penalty [F], crc_ok [F])."""
+        F, kb = self._meta[ticket]
+        bits = np.zeros((F, kb), dtype=np.uint8)
+        pm = np.zeros(F, dtype=np.float32)
+        ok = np.zeros(F, dtype=np.uint8)
+        done = ctypes.c_int(0)
+        _check(_lib().polar_server_poll(self._h, ticket, bits.ctypes.data_as(ctypes.c_void_p),
+                                        pm.ctypes.data_as(ctypes.c_void_p), ok.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(done)), "polar_server_poll")
+        if not done.value:
+            return None
+        del self._meta[ticket]
+        return bits, pm, ok
+
+    def wait(self, ticket, timeout_ms=60000) -> int:
+        """POLAR_OK when done, POLAR_ETIMEDOUT when the bounded wait ran out."""
+        return int(_lib().polar_server_wait(self._h, ticket, int(timeout_ms)))
+
+    def result(self, ticket, timeout_ms=60000):
+        _check(self.wait(ticket, timeout_ms), "polar_server_wait")
+        return self.poll(ticket)
+
+    def pause(self, paused=True):
+        _check(_lib().polar_server_pause(self._h, 1 if paused else 0), "polar_server_pause")
+
+    def stats(self, reset=False) -> dict:
+        st = ServerStats()
+        _check(_lib().polar_server_stats(self._h, ctypes.byref(st), 1 if reset else 0), "polar_server_stats")
+        return {name: (getattr(st, name)) for name, _ in ServerStats._fields_}
