@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single-dtype", action="store_true", help="skip the second LLR type")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU sample")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--batch-frames", type=int, default=1 << 20)
+    ap.add_argument("--pool-frames", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-rate", type=float, default=2e5, help="offered frames per second")
     return ap.parse_args()
 
 
@@ -180,6 +186,156 @@ def config_dict(args, impl):
         "node_set": "Dec-SPC-4 (Rate-0, Rate-1, Rep, SPC<=4)",
         "l2": "inputs larger than L2 (no flush needed)",
         "parallelism": "frames sharded across ranks (replicas)",
+    }
+
+
+def measure_batched(args, torch, dev, stream, barrier):
+    """125-class Zipf mix (int8, 4 dB): one graph-replayed persistent launch vs
+    one plain launch per class, same frames."""
+    import numpy as np
+    from paper_1505_01466_gb300 import inputs as I, workloads as WL
+    from paper_1505_01466_gb300.polar import PolarCode, PolarBatch, LLR_I8
+    pools = WL.class_pools(pool_frames=args.pool_frames, seed=11)
+    codes = [PolarCode(p.frozen, p.crc_len, I.CRC32_POLY, p.L) for p in pools]
+    F = args.batch_frames
+    counts = I.zipf_class_counts(F, len(pools), seed=1)
+    fc = I.frame_order(counts, seed=1)
+    dpools = [torch.from_numpy(p.llr_i8).to(dev) for p in pools]
+    plan = PolarBatch(codes, fc, LLR_I8)
+    llr_bytes, bits_bytes, lo, bo = plan.layout()
+    packed = torch.empty(llr_bytes, dtype=torch.int8, device=dev)
+    per_class = []
+    info_bits = 0
+    for c, p in enumerate(pools):
+        sel = np.flatnonzero(fc == c)
+        info_bits += sel.size * p.k
+        rows_all = dpools[c][torch.arange(sel.size, device=dev) % dpools[c].shape[0]]
+        per_class.append(rows_all.contiguous())
+        for a in range(0, sel.size, 8192):
+            b = min(sel.size, a + 8192)
+            idx = torch.from_numpy(lo[sel[a:b]].astype(np.int64)).to(dev)[:, None] + torch.arange(p.N, device=dev)
+            packed[idx] = rows_all[a:b]
+    bits = torch.empty(bits_bytes, dtype=torch.uint8, device=dev)
+    pm = torch.empty(F, dtype=torch.float32, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    tuned = plan.autotune(packed, bits, pm, stream=stream)
+    plan.capture(packed, bits, pm, ok, None, stream=stream)
+    for _ in range(args.warmup):
+        plan.replay(stream=stream)
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(args.steps):
+            plan.replay(stream=stream)
+        b.record(stream)
+    barrier()
+    bms = a.elapsed_time(b) / args.steps
+    binfo = plan.info()
+    # plain: one launch per class on the same frames
+    outs = []
+    for c, code in enumerate(codes):
+        x = per_class[c]
+        if x.shape[0] == 0:
+            outs.append(None)
+            continue
+        code.autotune(x[: min(x.shape[0], 2048)])
+        outs.append((torch.empty((x.shape[0], (code.k + 7) // 8), dtype=torch.uint8, device=dev),
+                     torch.empty(x.shape[0], dtype=torch.float32, device=dev)))
+    def plain_step():
+        for c, code in enumerate(codes):
+            if outs[c] is not None:
+                code.decode_into(per_class[c], outs[c][0], outs[c][1], None, None, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plain_step()
+    barrier()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(args.steps):
+            plain_step()
+        b.record(stream)
+    barrier()
+    pms = a.elapsed_time(b) / args.steps
+    # the batched result equals the plain one on every frame (penalties)
+    pm_b = pm.cpu().numpy()
+    same = True
+    for c in range(len(codes)):
+        if outs[c] is not None:
+            same &= bool(np.array_equal(pm_b[np.flatnonzero(fc == c)], outs[c][1].cpu().numpy()))
+    del packed, per_class, outs
+    return {
+        "workload": f"{len(pools)}-class mix N 256..4096 x rate 0.25..0.9 x L 2..32, CRC-32, int8 LLRs at 4 dB, "
+                    f"Zipf s=1.2 class counts, {F} frames",
+        "value": info_bits / (bms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": bms,
+        "plain_value": info_bits / (pms * 1e-3) / 1e9, "plain_ms_per_step": pms,
+        "plain_launches_per_step": sum(1 for x in counts if x > 0),
+        "graph_replay": True, "results_equal_plain": same,
+        "launch": {"warps_per_frame": binfo["warps_per_frame"], "frames_per_cta": binfo["frames_per_cta"],
+                   "smem_per_frame": binfo["smem_per_frame"], "grid": binfo["grid"],
+                   "autotuned": {"warps": tuned[0], "smem_budget": tuned[1]}},
+    }
+
+
+def measure_serving(args):
+    """Poisson request stream against the continuous-batching server."""
+    import numpy as np
+    from paper_1505_01466_gb300 import inputs as I, workloads as WL
+    from paper_1505_01466_gb300.polar import PolarCode, PolarServer
+    pools = WL.class_pools(pool_frames=args.pool_frames, seed=12, ebn0s=(3.5, 3.75, 4.0, 4.25, 4.5))
+    codes = [PolarCode(p.frozen, p.crc_len, I.CRC32_POLY, p.L) for p in pools]
+    counts = I.zipf_class_counts(1 << 20, len(pools), seed=1).astype(np.float64)
+    pcls = counts / counts.sum()
+    rng = np.random.default_rng(2024)
+    mean_size = 4096.0 / np.log(4097.0)
+    lam = args.serve_rate / mean_size                      # requests per second
+    srv = PolarServer(device_mem_budget=8 << 30, max_frames_in_flight=1 << 21)
+    # warm-up: register every code, both dtypes
+    for c, p in enumerate(pools):
+        for dt in ("f32", "i8"):
+            srv.result(srv.submit(codes[c], p.rows(0, 4, dt)))
+    srv.stats(reset=True)
+    t_end = args.serve_seconds
+    reqs = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t > t_end:
+            break
+        n = int(min(4096, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))))))
+        c = int(rng.choice(len(pools), p=pcls))
+        reqs.append((t, c, n, "i8" if rng.random() < 0.5 else "f32", int(rng.integers(1 << 20))))
+    # inputs prepared before the clock starts
+    payload = [pools[c].rows(off, n, dt) for (_, c, n, dt, off) in reqs]
+    outstanding = []
+    frames = 0
+    t0 = time.perf_counter()
+    for (ta, c, n, dt, _), x in zip(reqs, payload):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+            if outstanding:
+                tk = outstanding[0]
+                if srv.poll(tk) is not None:
+                    outstanding.pop(0)
+                    continue
+            time.sleep(min(ta - now, 2e-4))
+        outstanding.append(srv.submit(codes[c], x))
+        frames += n
+    for tk in outstanding:
+        srv.result(tk, timeout_ms=600000)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return {
+        "workload": "Poisson requests, 1..4096 frames (log-uniform), (N,K,L) from the 125-class Zipf mix, "
+                    "f32/int8 50/50, Eb/N0 3.5..4.5 dB",
+        "offered_frames_per_s": args.serve_rate, "requests": len(reqs), "frames": frames,
+        "duration_s": wall, "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+        "max_ms": st["max_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
+        "info_gbps": st["info_bits"] / (st["span_us"] * 1e-6) / 1e9 if st["span_us"] > 0 else None,
+        "batches": st["batches"], "max_batches_in_flight": st["max_batches_in_flight"],
     }
 
 
@@ -332,6 +488,13 @@ def run_ours(args):
                                                 "spill_mask": oinfo["spill_mask"][di]}}
         del ollr
 
+    batched = None
+    if not args.skip_batched:
+        batched = measure_batched(args, torch, dev, stream, barrier)
+    serving = None
+    if rank == 0 and not args.skip_serving:
+        serving = measure_serving(args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(llr_np, frozen, args.cpu_seconds)
@@ -351,6 +514,8 @@ def run_ours(args):
             "wall_s_timed": t_wall,
             "launch": launch_info,
             "other_dtype": other,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
