@@ -29,8 +29,10 @@ struct polar_code {
     uint32_t N, n, K, k, L, crc_len, flags;
     uint64_t crc_poly;
     std::vector<uint8_t> frozen;
-    std::vector<uint32_t> ops;          // unrolled schedule (device encoding)
-    std::vector<int32_t> sched;         // (kind, N_v, start) triples
+    std::vector<uint32_t> ops;          // device schedule (small subtrees as OP_SUB)
+    std::vector<uint32_t> xops;         // fully unrolled schedule (one entry per F/G/Combine/leaf)
+    std::vector<unsigned long long> desc;  // subtree descriptors, two words each
+    std::vector<int32_t> sched;         // (kind, N_v, start) triples of xops
     std::vector<uint16_t> info;         // information positions
     std::vector<uint32_t> syn;          // [N/8][256]
     uint32_t n_leaves = 0, n_r0 = 0, n_r1 = 0, n_rep = 0, n_spc = 0;
@@ -40,6 +42,7 @@ struct polar_code {
     std::vector<uint32_t> shape_ops[2];  // ops with solo / sync flags of shape[d]
     uint32_t *d_syn = nullptr;
     uint16_t *d_info = nullptr;
+    unsigned long long *d_desc = nullptr;
     LaunchShape shape[2];
 };
 
@@ -55,7 +58,8 @@ uint64_t al256(uint64_t x) { return (x + 255u) & ~uint64_t(255); }
 struct TreeBuilder {
     const polar_code *c;
     std::vector<uint32_t> prefix;   // prefix[i] = frozen count in [0, i)
-    std::vector<uint32_t> ops;
+    std::vector<uint32_t> ops, xops;
+    std::vector<unsigned long long> desc;
     std::vector<int32_t> sched;
     uint32_t leaves = 0, r0 = 0, r1 = 0, rep = 0, spc = 0;
 
@@ -73,28 +77,75 @@ struct TreeBuilder {
         return 0;
     }
 
-    void emit(uint32_t kind, int j, uint32_t dest, uint32_t start) {
-        ops.push_back(op_make(kind, (uint32_t)j, dest));
+    // one entry of the fully unrolled schedule
+    void expand(uint32_t kind, int j, uint32_t dest, uint32_t start) {
+        xops.push_back(op_make(kind, (uint32_t)j, dest));
         static const int32_t ext[7] = {0, 1, 2, 11, 12, 13, 14};
         sched.push_back(ext[kind]);
         sched.push_back(1 << j);
         sched.push_back((int32_t)start);
+        if (kind >= OP_R0) {
+            ++leaves;
+            r0 += kind == OP_R0; r1 += kind == OP_R1; rep += kind == OP_REP; spc += kind == OP_SPC;
+        }
+    }
+
+    // candidates a forking leaf generates per source path (log2)
+    uint32_t log_cands(uint32_t kind, int j) const {
+        if (kind == OP_R1) return j == 0 ? 1u : 2u;
+        if (kind == OP_REP) return 1u;
+        if (kind == OP_SPC) return c->L == 2 ? 1u : 3u;
+        return 0u;
+    }
+
+    void walk_sub(int j, uint32_t start, uint32_t dest, std::vector<uint32_t> &types, uint32_t &logm, bool &fork) {
+        const uint32_t t = classify(j, start);
+        if (t) {
+            types.push_back(t);
+            expand(t, j, dest, start);
+            if (t != OP_R0) { fork = true; logm += log_cands(t, j); }
+            return;
+        }
+        types.push_back(0);
+        const uint32_t h = 1u << (j - 1);
+        expand(OP_F, j, 0, start);
+        walk_sub(j - 1, start, 0, types, logm, fork);
+        expand(OP_G, j, 0, start);
+        walk_sub(j - 1, start + h, 1, types, logm, fork);
+        expand(OP_COMB, j, dest, start);
     }
 
     void build(int j, uint32_t start, uint32_t dest) {
+        if (j <= kSubLog) {
+            std::vector<uint32_t> types;
+            uint32_t logm = 0;
+            bool fork = false;
+            walk_sub(j, start, dest, types, logm, fork);
+            unsigned long long w[2] = {0ull, 0ull};
+            for (size_t i = 0; i < types.size(); ++i)
+                w[i / 21] |= (unsigned long long)types[i] << (3 * (i % 21));
+            const uint32_t di = (uint32_t)(desc.size() / 2);
+            desc.push_back(w[0]);
+            desc.push_back(w[1]);
+            ops.push_back(op_make(OP_SUB, (uint32_t)j, dest) | (fork ? 1u << 11 : 0u) | (std::min(logm, 6u) << 12) |
+                          (di << 15));
+            return;
+        }
         const uint32_t t = classify(j, start);
         if (t) {
-            emit(t, j, dest, start);
-            ++leaves;
-            r0 += t == OP_R0; r1 += t == OP_R1; rep += t == OP_REP; spc += t == OP_SPC;
+            expand(t, j, dest, start);
+            ops.push_back(op_make(t, (uint32_t)j, dest));
             return;
         }
         const uint32_t h = 1u << (j - 1);
-        emit(OP_F, j, 0, start);
+        expand(OP_F, j, 0, start);
+        ops.push_back(op_make(OP_F, (uint32_t)j, 0));
         build(j - 1, start, 0);
-        emit(OP_G, j, 0, start);
+        expand(OP_G, j, 0, start);
+        ops.push_back(op_make(OP_G, (uint32_t)j, 0));
         build(j - 1, start + h, 1);
-        emit(OP_COMB, j, dest, start);
+        expand(OP_COMB, j, dest, start);
+        ops.push_back(op_make(OP_COMB, (uint32_t)j, dest));
     }
 };
 
@@ -133,68 +184,64 @@ void build_syndrome(polar_code *c) {
 }
 
 // ---- memory layout of one frame --------------------------------------------
+// Small per-path tables always sit in shared memory. Alpha stages and left
+// betas exist only for stages kSubLog..n-1 (lower stages stay in registers);
+// together with the right/root beta and the channel row they go to shared
+// memory until the budget is reached, the largest ones spilling to the
+// group's global scratch first.
 bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &lay) {
     std::memset(&lay, 0, sizeof(lay));
     const uint32_t N = 1u << n;
-    uint32_t fixed = 0;
-    fixed += al16(N * es);                                             // chan
-    for (uint32_t j = 0; j < n; ++j) fixed += al16(L * 4u * (uint32_t)beta_words((int)j));  // BL
-    fixed += al16(L * 4u * (uint32_t)beta_words((int)n));              // BR
-    fixed += 4 * al16(L * 16u);                                        // idx, bidx x2
-    fixed += 2 * al16(L * 4u);                                         // pen x2
-    fixed += al16(std::max(8u * L, 8u) * 8u);                          // keys
-    fixed += al16(L * 8u);                                             // surv
-    fixed += al16(L * 16u);                                            // cinfo
-    fixed += al16(4u * (uint32_t)beta_words((int)n));                  // ubuf
-    std::vector<uint32_t> abytes(n);
-    uint32_t total = fixed;
-    for (uint32_t j = 0; j < n; ++j) {
-        abytes[j] = al16(L * (1u << j) * es);
-        total += abytes[j];
+    const uint32_t lo = std::min<uint32_t>((uint32_t)kSubLog, n);
+    struct Buf { int kind; uint32_t j; uint32_t bytes; bool spill; };
+    std::vector<Buf> bufs;
+    for (uint32_t j = lo; j < n; ++j) bufs.push_back({0, j, al16(L * (1u << j) * es), false});
+    for (uint32_t j = lo; j < n; ++j) bufs.push_back({1, j, al16(L * 4u * (uint32_t)beta_words((int)j)), false});
+    bufs.push_back({2, 0, al16(L * 4u * (uint32_t)beta_words((int)n)), false});
+    bufs.push_back({3, 0, al16(N * es), false});
+    const uint32_t fixed = 4 * al16(L * 16u) + 2 * al16(L * 4u) + al16(L * 8u) + al16(4u * (uint32_t)beta_words((int)n));
+    uint64_t total = fixed;
+    for (const Buf &bf : bufs) total += bf.bytes;
+    while (total > budget) {
+        int pick = -1;
+        for (size_t i = 0; i < bufs.size(); ++i)
+            if (!bufs[i].spill && (pick < 0 || bufs[i].bytes > bufs[(size_t)pick].bytes)) pick = (int)i;
+        if (pick < 0) return false;
+        bufs[(size_t)pick].spill = true;
+        total -= bufs[(size_t)pick].bytes;
     }
-    uint32_t spill = 0;
-    for (int j = (int)n - 1; j >= 0 && total > budget; --j) {
-        spill |= 1u << j;
-        total -= abytes[j];
-    }
-    if (total > budget) return false;
     uint32_t off = 0;
-    lay.chan = off; off += al16(N * es);
     uint64_t goff = 0;
-    for (uint32_t j = 0; j < n; ++j) {
-        if ((spill >> j) & 1u) {
-            lay.galpha[j] = goff;
-            goff = al256(goff + abytes[j]);
-        } else {
-            lay.alpha[j] = off;
-            off += abytes[j];
-        }
+    for (const Buf &bf : bufs) {
+        uint32_t *so = nullptr;
+        uint64_t *go = nullptr;
+        if (bf.kind == 0) { so = &lay.alpha[bf.j]; go = &lay.galpha[bf.j]; if (bf.spill) lay.spill_mask |= 1u << bf.j; }
+        else if (bf.kind == 1) { so = &lay.bl[bf.j]; go = &lay.gbl[bf.j]; if (bf.spill) lay.bl_spill |= 1u << bf.j; }
+        else if (bf.kind == 2) { so = &lay.br; go = &lay.gbr; if (bf.spill) lay.flags |= LAY_BR_GLOBAL; }
+        else { so = &lay.chan; go = &lay.gchan; if (bf.spill) lay.flags |= LAY_CHAN_GLOBAL; }
+        if (bf.spill) { *go = goff; goff = al256(goff + bf.bytes); }
+        else { *so = off; off += bf.bytes; }
     }
-    for (uint32_t j = 0; j < n; ++j) { lay.bl[j] = off; off += al16(L * 4u * (uint32_t)beta_words((int)j)); }
-    lay.br = off; off += al16(L * 4u * (uint32_t)beta_words((int)n));
     for (int b = 0; b < 2; ++b) { lay.idx[b] = off; off += al16(L * 16u); }
     for (int b = 0; b < 2; ++b) { lay.bidx[b] = off; off += al16(L * 16u); }
     for (int b = 0; b < 2; ++b) { lay.pen[b] = off; off += al16(L * 4u); }
-    lay.key = off; off += al16(std::max(8u * L, 8u) * 8u);
     lay.surv = off; off += al16(L * 8u);
-    lay.cinfo = off; off += al16(L * 16u);
     lay.ubuf = off; off += al16(4u * (uint32_t)beta_words((int)n));
     lay.bytes = off;
-    lay.spill_mask = spill;
     lay.gbytes = goff;
     return true;
 }
 
 constexpr uint32_t kMaxSmemPerCta = 232448;   // 227 KB opt-in per CTA on sm_100-class parts
 
-// Solo / sync flags for a group of `warps` warps: nodes of at most
-// 2^kSoloMaxLog bits run on warp 0 alone; a group barrier is needed after an
+// Solo / sync flags for a group of `warps` warps: leaves and subtrees run on
+// warp 0 alone (one lane per path); a group barrier is needed after an
 // operation unless it and the next one are both solo.
 std::vector<uint32_t> flag_ops(const std::vector<uint32_t> &ops, uint32_t warps) {
     std::vector<uint32_t> out(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {
-        const bool solo = warps == 1 || op_stage(ops[i]) <= kSoloMaxLog;
-        const bool next_solo = i + 1 < ops.size() && (warps == 1 || op_stage(ops[i + 1]) <= kSoloMaxLog);
+        const bool solo = warps == 1 || op_kind(ops[i]) >= OP_R0;
+        const bool next_solo = i + 1 < ops.size() && (warps == 1 || op_kind(ops[i + 1]) >= OP_R0);
         out[i] = ops[i] | (solo ? OP_SOLO : 0u) | ((warps > 1 && !(solo && next_solo)) ? OP_SYNC : 0u);
     }
     return out;
@@ -235,8 +282,10 @@ void free_device(polar_code *c) {
     }
     if (c->d_syn) cudaFree(c->d_syn);
     if (c->d_info) cudaFree(c->d_info);
+    if (c->d_desc) cudaFree(c->d_desc);
     c->d_syn = nullptr;
     c->d_info = nullptr;
+    c->d_desc = nullptr;
 }
 
 template <typename T>
@@ -271,6 +320,7 @@ CodeView make_view(const polar_code *code, const LaunchShape &sh) {
     v.ops = sh.d_ops;
     v.syn = code->d_syn;
     v.info = code->d_info;
+    v.desc = code->d_desc;
     v.n_ops = (int)code->ops.size();
     v.N = (int)code->N;
     v.n = (int)code->n;
@@ -394,6 +444,8 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     for (uint32_t i = 0; i < N; ++i) tb.prefix[i + 1] = tb.prefix[i] + c->frozen[i];
     tb.build((int)c->n, 0, 1);
     c->ops = std::move(tb.ops);
+    c->xops = std::move(tb.xops);
+    c->desc = std::move(tb.desc);
     c->sched = std::move(tb.sched);
     c->n_leaves = tb.leaves;
     c->n_r0 = tb.r0;
@@ -410,6 +462,7 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
         }
         cudaError_t e = upload(&c->d_info, c->info);
         if (e == cudaSuccess) e = upload(&c->d_syn, c->syn);
+        if (e == cudaSuccess) e = upload(&c->d_desc, c->desc);
         if (e != cudaSuccess) {
             free_device(c);
             delete c;
@@ -834,7 +887,7 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
     info->k = c->k;
     info->L = c->L;
     info->crc_len = c->crc_len;
-    info->n_ops = (uint32_t)c->ops.size();
+    info->n_ops = (uint32_t)c->xops.size();
     info->n_leaves = c->n_leaves;
     info->n_rate0 = c->n_r0;
     info->n_rate1 = c->n_r1;
@@ -865,7 +918,7 @@ int polar_code_op_count(const polar_code_t *c, uint64_t *ops_per_frame) {
     uint64_t lg = 0;
     while ((1u << lg) < c->L) ++lg;
     if (lg == 0) lg = 1;
-    for (uint32_t op : c->ops) {
+    for (uint32_t op : c->xops) {
         const uint32_t kind = op_kind(op);
         const uint64_t nv = 1ull << op_stage(op);
         switch (kind) {

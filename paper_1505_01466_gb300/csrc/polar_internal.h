@@ -18,8 +18,13 @@ enum OpKind : uint32_t {
     OP_R0 = 3,     // Rate-0 leaf                               Sec. III-B
     OP_R1 = 4,     // Rate-1 leaf                               Sec. III-C
     OP_REP = 5,    // repetition leaf                           Sec. III-E
-    OP_SPC = 6     // single-parity-check leaf                  Sec. III-D
+    OP_SPC = 6,    // single-parity-check leaf                  Sec. III-D
+    OP_SUB = 7     // a whole subtree of <= 2^kSubLog bits in registers
 };
+
+// Subtrees rooted at this stage or below run as one OP_SUB operation: warp 0,
+// one lane per path, LLRs / beta / penalty in registers.
+constexpr int kSubLog = 4;
 
 // One schedule entry: kind | stage j << 4 | dest << 8 | solo << 9 | sync << 10.
 //   j     stage of the node (N_v = 2^j)
@@ -37,38 +42,50 @@ __host__ __device__ inline bool op_solo(uint32_t op) { return ((op >> 9) & 1u) !
 __host__ __device__ inline bool op_sync(uint32_t op) { return ((op >> 10) & 1u) != 0; }
 constexpr uint32_t OP_SOLO = 1u << 9;
 constexpr uint32_t OP_SYNC = 1u << 10;
-// Nodes of at most this many bits run solo when a frame has several warps.
-constexpr int kSoloMaxLog = 4;
+// OP_SUB only: bit 11 = the subtree forks paths, bits 12..14 = log2 of the
+// product of its leaves' candidate counts (saturated at 6; the live paths
+// become min(L, L_a * 2^m)), bits 15.. = index of its descriptor.
+__host__ __device__ inline bool op_sub_fork(uint32_t op) { return ((op >> 11) & 1u) != 0; }
+__host__ __device__ inline int op_sub_logmult(uint32_t op) { return (int)((op >> 12) & 7u); }
+__host__ __device__ inline uint32_t op_sub_desc(uint32_t op) { return op >> 15; }
+// Subtree descriptor: pre-order node kinds, 3 bits each (0 = inner node,
+// OP_R0 .. OP_SPC = leaf), 21 per 64-bit word, two words per subtree.
 
 // Bit-packed beta: words per path for a node of 2^j bits.
 __host__ __device__ inline int beta_words(int j) { return j >= 5 ? 1 << (j - 5) : 1; }
 
 // Per-frame memory layout. Byte offsets inside one frame-group's shared
-// memory region, or inside its global scratch region for spilled stages.
+// memory region, or inside its global scratch region for buffers that do not
+// fit the shared-memory budget ("spilled"). Alpha and left-beta buffers exist
+// only for stages kSubLog..n-1: lower stages live in registers (OP_SUB).
 struct Layout {
+    uint32_t alpha[kMaxLogN];      // stage j: L rows of 2^j elements
+    uint32_t bl[kMaxLogN];         // left-child beta of stage j: L rows of beta_words(j) words
+    uint32_t br;                   // right/root beta: L rows of beta_words(n) words
     uint32_t chan;                 // channel LLRs (stage n), N elements
-    uint32_t alpha[kMaxLogN];      // stage j < n: L rows of 2^j elements
-    uint32_t bl[kMaxLogN];         // left-child beta of stage j: L rows of beta_words(j)
-    uint32_t br;                   // right/root beta: L rows of beta_words(n)
     uint32_t idx[2];               // alpha stage -> physical row, [L][16] bytes, double buffered
     uint32_t bidx[2];              // left-beta stage -> physical row, same shape
     uint32_t pen[2];               // penalties, [L] float or int32, double buffered
-    uint32_t key;                  // candidate keys, 8L uint64
-    uint32_t surv;                 // survivor keys in new-slot order, L uint64
-    uint32_t cinfo;                // per-source candidate data, L x 16 bytes
+    uint32_t surv;                 // survivor keys in new-slot order, L x 8 bytes
     uint32_t ubuf;                 // winner's u vector, beta_words(n) words
-    uint32_t bytes;                // total per group (multiple of 16)
-    uint32_t spill_mask;           // bit j set: alpha stage j lives in global scratch
-    uint32_t pad_;
-    uint64_t galpha[kMaxLogN];     // offsets inside the group's global scratch
-    uint64_t gbytes;               // global scratch bytes per group
+    uint32_t bytes;                // shared memory per group (multiple of 16)
+    uint32_t spill_mask;           // bit j: alpha stage j in global scratch
+    uint32_t bl_spill;             // bit j: left beta of stage j in global scratch
+    uint32_t flags;                // bit 0: BR in global scratch, bit 1: channel in global scratch
+    uint64_t galpha[kMaxLogN];     // global offsets of spilled buffers
+    uint64_t gbl[kMaxLogN];
+    uint64_t gbr, gchan;
+    uint64_t gbytes;               // global scratch per group
 };
+constexpr uint32_t LAY_BR_GLOBAL = 1u;
+constexpr uint32_t LAY_CHAN_GLOBAL = 2u;
 
 // Everything the decoder needs about one code (and one launch shape).
 struct CodeView {
     const uint32_t *ops;           // schedule with solo / sync flags
     const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
     const uint16_t *info;          // [K] information positions, ascending
+    const unsigned long long *desc;// subtree descriptors, two words each
     int n_ops;
     int N, n, L, K, k, kb, crc_len;
     Layout lay;

@@ -1,28 +1,30 @@
 // polar_kernels.cu -- list-CRC decoding of polar codes over the unrolled
 // Fast-SSC tree, for GB300 (sm_103a).
 //
-// One frame is decoded by a group of W warps; a CTA holds 4 / W groups and
-// every group loops over frames (persistent). All L paths of a frame advance
-// through the same unrolled schedule in lockstep, so:
+// One frame is decoded by a group of W warps (W = 1, 2, 4); a CTA holds 4 / W
+// groups and every group loops over frames (persistent). All L paths of a
+// frame advance through the same schedule in lockstep, so:
 //
-//  * alpha stage j holds one row of 2^j LLRs per physical slot. F and G
-//    (Eq. (1), (2)) read stage j+1 through the path's index-table entry and
-//    always write the path's own row of stage j: at that moment stage j is
-//    dead for every path. A fork only copies the parent's 16-byte index row
-//    -- the lazy copy of Sec. IV-A -- never LLRs.
+//  * alpha stage j (kSubLog <= j < n) holds one row of 2^j LLRs per physical
+//    slot. F and G (Eq. (1), (2)) read stage j+1 through the path's index-
+//    table entry and always write the path's own row of stage j: at that
+//    moment stage j is dead for every path. A fork only copies the parent's
+//    16-byte index row -- the lazy copy of Sec. IV-A -- never LLRs.
 //  * beta is bit-packed. Left-child outputs (BL[j]) sit behind a second
 //    index table (Sec. IV-B); the right-child / root output (BR) is consumed
 //    by the Combine (Eq. (3)) that follows at once and needs none.
-//  * nodes of at most 16 bits are "solo": warp 0 runs them alone, one lane
-//    per path for leaves, with only warp-level syncs between consecutive solo
-//    operations; larger nodes use the whole group, one element per thread.
+//  * every subtree of at most 16 bits is one operation (OP_SUB) run by warp 0
+//    with one lane per path: its LLRs, betas and penalty stay in registers, a
+//    fork moves a path's state from its parent lane by warp shuffles, and only
+//    the subtree root touches memory. Leaves of more than 16 bits also run one
+//    lane per path (vectorised scans of the path's row).
 //  * a forking leaf (Sec. III-C..E) produces keys (penalty, source * C +
-//    candidate) for each source path. Warp 0 keeps the L smallest
-//    (Algorithm 1) without shared-memory sorting: lane s holds source s's
-//    candidates sorted, the ML column is bitonic-sorted across lanes and the
-//    later columns are merged in until the L-th key can no longer move.
-//    Survivors take slots in (source, candidate) order by a warp prefix scan
-//    and inherit their parent's index rows, penalty and candidate beta.
+//    candidate) in the source lane. The L smallest survive (Algorithm 1): the
+//    ML column is bitonic-sorted across the warp and later columns are merged
+//    in while their minimum is below the current L-th key; survivors are
+//    numbered in (source, candidate) order by a warp prefix scan.
+//  * buffers that do not fit the shared-memory budget live in a per-group
+//    global scratch region (L2-resident in practice).
 //  * the final pick (Sec. II-B) checks each path's CRC with byte tables of
 //    the syndrome of every codeword bit, and writes the winner's payload.
 //
@@ -111,10 +113,24 @@ __device__ __forceinline__ void gsync(int gidx) {
     }
 }
 
+// Buffers live in the group's shared memory or, when spilled, in its global scratch.
 template <typename T>
-__device__ __forceinline__ T *stage_ptr(const Layout &lay, uint8_t *S, uint8_t *Gs, int j) {
+__device__ __forceinline__ T *alpha_ptr(const Layout &lay, uint8_t *S, uint8_t *Gs, int j) {
     return ((lay.spill_mask >> j) & 1u) ? reinterpret_cast<T *>(Gs + lay.galpha[j])
                                         : reinterpret_cast<T *>(S + lay.alpha[j]);
+}
+__device__ __forceinline__ uint32_t *bl_ptr(const Layout &lay, uint8_t *S, uint8_t *Gs, int j) {
+    return ((lay.bl_spill >> j) & 1u) ? reinterpret_cast<uint32_t *>(Gs + lay.gbl[j])
+                                      : reinterpret_cast<uint32_t *>(S + lay.bl[j]);
+}
+__device__ __forceinline__ uint32_t *br_ptr(const Layout &lay, uint8_t *S, uint8_t *Gs) {
+    return (lay.flags & LAY_BR_GLOBAL) ? reinterpret_cast<uint32_t *>(Gs + lay.gbr)
+                                       : reinterpret_cast<uint32_t *>(S + lay.br);
+}
+template <typename T>
+__device__ __forceinline__ T *chan_ptr(const Layout &lay, uint8_t *S, uint8_t *Gs) {
+    return (lay.flags & LAY_CHAN_GLOBAL) ? reinterpret_cast<T *>(Gs + lay.gchan)
+                                         : reinterpret_cast<T *>(S + lay.chan);
 }
 
 // SPC candidate flips over the ranks of the four least reliable bits (bit r
@@ -128,9 +144,9 @@ template <typename K> __device__ __forceinline__ K kmax(K a, K b) { return a < b
 
 template <typename K>
 __device__ __forceinline__ K bsort32(K x, int lane) {   // ascending across the warp
-#pragma unroll
+#pragma unroll 1
     for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
         for (int j = k >> 1; j > 0; j >>= 1) {
             const K o = __shfl_xor_sync(FULL, x, j);
             const bool up = (lane & k) == 0;
@@ -143,7 +159,7 @@ __device__ __forceinline__ K bsort32(K x, int lane) {   // ascending across the 
 
 template <typename K>
 __device__ __forceinline__ K bmerge32(K x, int lane) {  // bitonic -> ascending
-#pragma unroll
+#pragma unroll 1
     for (int j = 16; j > 0; j >>= 1) {
         const K o = __shfl_xor_sync(FULL, x, j);
         x = ((lane & j) == 0) ? kmin(x, o) : kmax(x, o);
@@ -175,10 +191,15 @@ template <typename K>
 __device__ __forceinline__ K warp_kth(const K (&k)[8], int C, int L, int lane) {
     K B = bsort32(k[0], lane);
     K tau = __shfl_sync(FULL, B, L - 1);
+    // later columns, one per iteration (kept rolled: the body is large)
+    K q[7];
 #pragma unroll
-    for (int r = 1; r < 8; ++r) {
-        if (r >= C) break;
-        K col = k[r];
+    for (int r = 0; r < 7; ++r) q[r] = k[r + 1];
+#pragma unroll 1
+    for (int r = 1; r < C; ++r) {
+        K col = q[0];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) q[t] = q[t + 1];
         K mn = col;
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) mn = kmin(mn, __shfl_xor_sync(FULL, mn, m));
@@ -201,124 +222,630 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
     return x - v;
 }
 
-// ---- canonical team sums and least reliable bits (large leaves) -----------
+// ---- register-resident subtrees (OP_SUB) ----------------------------------
+// A subtree of at most 16 bits runs on warp 0, lane s = path s. The alpha of
+// stage j (j <= 4) lives in registers a[(1 << j) - 1 ...], left-child betas in
+// bl[j], the latest right-child beta in br. A fork moves a path's live state
+// (alpha of the stages above the leaf, pending left betas, penalty, origin)
+// from its parent lane with warp shuffles.
+template <int J> __device__ __forceinline__ constexpr int aoff() { return (1 << J) - 1; }
+
+__device__ __forceinline__ float fv(float a, float b) { return f_op(a, b); }
+__device__ __forceinline__ int fv(int a, int b) {
+    const int m = min(abs(a), abs(b));
+    return ((a ^ b) < 0) ? -m : m;
+}
+__device__ __forceinline__ float gv(float a, float b, uint32_t beta) { return g_op(a, b, beta); }
+__device__ __forceinline__ int gv(int a, int b, uint32_t beta) {
+    const int r = beta ? b - a : b + a;
+    return max(-127, min(127, r));
+}
+
 template <typename T>
-__device__ __forceinline__ void team_sums(T *row, int K, int TS, int tl, bool act, bool want1,
-                                          typename Arith<T>::P &v0, typename Arith<T>::P &v1) {
+struct Sub {
     typedef typename Arith<T>::P P;
-    P s0 = 0, s1 = 0;
-    if (act) {
-        if (K == 1) {
-            P a = Arith<T>::val(row[tl]);
-            s0 = Arith<T>::negpart(a);
-            s1 = Arith<T>::pospart(a);
-        } else if (sizeof(T) == 4) {
-            // in-lane levels of the tree, in place on the (dead) leaf input
-            float *x = reinterpret_cast<float *>(row) + tl;
-            const int hK = K >> 1;
-            for (int k = 0; k < hK; ++k) {
-                float a = x[k * TS], b = x[(k + hK) * TS];
-                x[k * TS] = Arith<float>::negpart(a) + Arith<float>::negpart(b);
-                if (want1) x[(k + hK) * TS] = Arith<float>::pospart(a) + Arith<float>::pospart(b);
-            }
-            for (int hh = hK >> 1; hh >= 1; hh >>= 1) {
-                for (int k = 0; k < hh; ++k) {
-                    x[k * TS] = x[k * TS] + x[(k + hh) * TS];
-                    if (want1) x[(hK + k) * TS] = x[(hK + k) * TS] + x[(hK + k + hh) * TS];
-                }
-            }
-            s0 = (P)x[0];
-            s1 = want1 ? (P)x[hK * TS] : (P)0;
-        } else {
-            for (int k = 0; k < K; ++k) {
-                P a = Arith<T>::val(row[tl + k * TS]);
-                s0 += Arith<T>::negpart(a);
-                s1 += Arith<T>::pospart(a);
-            }
-        }
-    }
-    for (int off = TS >> 1; off >= 1; off >>= 1) {
-        s0 = s0 + __shfl_xor_sync(FULL, s0, off, TS);
-        if (want1) s1 = s1 + __shfl_xor_sync(FULL, s1, off, TS);
-    }
-    v0 = s0;
-    v1 = s1;
-}
+    P a[31];
+    uint32_t bl[5];
+    uint32_t br;
+    P pen;
+    int orig;
+};
 
-template <typename T, int R>
-__device__ __forceinline__ void team_lrb(const T *row, int K, int TS, int tl, bool act, uint64_t (&mk)[4]) {
-    uint64_t top[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) top[r] = ~0ull;
-    if (act) {
-        for (int k = 0; k < K; ++k) {
-            const int pos = tl + k * TS;
-            uint64_t t = ((uint64_t)Arith<T>::absbits(Arith<T>::val(row[pos])) << 32) | (uint32_t)pos;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (t < top[r]) { uint64_t x = top[r]; top[r] = t; t = x; }
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        uint64_t m = top[0];
-        for (int off = TS >> 1; off >= 1; off >>= 1) {
-            uint64_t o = __shfl_xor_sync(FULL, (unsigned long long)m, off, TS);
-            m = o < m ? o : m;
-        }
-        if (top[0] == m) {
-#pragma unroll
-            for (int q = 0; q + 1 < R; ++q) top[q] = top[q + 1];
-            top[R - 1] = ~0ull;
-        }
-        mk[r] = m;
-    }
-}
-
-// Load up to 16 values of a node row into registers (lane-per-path leaves).
 template <typename T>
-__device__ __forceinline__ void load16(const T *row, int nv, bool act, typename Arith<T>::P (&a)[16]) {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) a[i] = 0;
-    if (!act) return;
-    if (sizeof(T) == 4 && nv >= 4) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (4 * q < nv) {
-                const float4 v = reinterpret_cast<const float4 *>(row)[q];
-                a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
-            }
-        }
-    } else if (sizeof(T) == 1 && nv >= 4) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (4 * q < nv) {
-                const uint32_t v = reinterpret_cast<const uint32_t *>(row)[q];
-                a[4 * q] = (int)(int8_t)(v & 0xFF);
-                a[4 * q + 1] = (int)(int8_t)((v >> 8) & 0xFF);
-                a[4 * q + 2] = (int)(int8_t)((v >> 16) & 0xFF);
-                a[4 * q + 3] = (int)(int8_t)(v >> 24);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (i < nv) a[i] = Arith<T>::val(row[i]);
+struct SubCtx {
+    typename Arith<T>::K *tab;     // survivor keys in new-slot order (shared memory)
+    int lane, La, L;
+};
+
+struct Desc {
+    unsigned long long w0, w1;
+    int pos;
+    __device__ __forceinline__ uint32_t next() {
+        const uint32_t v = pos < 21 ? (uint32_t)(w0 >> (3 * pos)) & 7u : (uint32_t)(w1 >> (3 * (pos - 21))) & 7u;
+        ++pos;
+        return v;
     }
+};
+
+// Selection (Algorithm 1) for lane-per-path leaves: keep the L smallest keys,
+// survivors renumbered in (source, candidate) order; returns lane t's new key.
+template <typename KT>
+__device__ __noinline__ KT select_keys(KT k0, KT k1, KT k2, KT k3, KT k4, KT k5, KT k6, KT k7, int C, int nc, int L,
+                                       int lane, KT *tab) {
+    const KT KINF = (KT)~(KT)0;
+    KT k[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
+    const KT tau = (nc > L) ? warp_kth(k, C, L, lane) : KINF;
+    const uint32_t cm = (uint32_t)(C - 1);
+    uint32_t sm = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (k[r] != KINF && k[r] <= tau) sm |= 1u << ((uint32_t)k[r] & cm);
+    const int base = warp_excl_scan(__popc(sm), lane);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (k[r] != KINF && k[r] <= tau) tab[base + __popc(sm & ((1u << ((uint32_t)k[r] & cm)) - 1u))] = k[r];
+    }
+    __syncwarp();
+    const int La2 = nc < L ? nc : L;
+    return lane < La2 ? tab[lane] : (KT)0;
 }
 
-// Canonical pairwise tree sum of x[0..nv) in registers (nv <= 16, power of 2).
-template <typename P>
-__device__ __forceinline__ P reg_tree(P (&x)[16], int nv) {
+template <typename T, int J>
+__device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, SubCtx<T> &cx) {
+    typedef typename Arith<T>::P P;
+    typedef typename Arith<T>::K KT;
+    constexpr KT KINF = Arith<T>::KINF;
+    constexpr int nv = 1 << J;
+    constexpr int o = aoff<J>();
+    constexpr uint32_t wmask = (nv >= 32) ? 0xffffffffu : ((1u << nv) - 1u);
+    const int lane = cx.lane;
+    const bool act = lane < cx.La;
+    if (type == OP_R0) {
+        // Rate-0 (Sec. III-B): penalty += sum |min(a, 0)| (pairwise tree), beta = 0.
+        P x[nv];
 #pragma unroll
-    for (int h = 8; h >= 1; h >>= 1) {
-        if (h < nv) {
+        for (int i = 0; i < nv; ++i) x[i] = Arith<T>::negpart(st.a[o + i]);
+#pragma unroll
+        for (int h = nv >> 1; h >= 1; h >>= 1)
 #pragma unroll
             for (int i = 0; i < h; ++i) x[i] = x[i] + x[i + h];
+        if (act) st.pen = st.pen + x[0];
+        if (side) st.br = 0u; else st.bl[J] = 0u;
+        return;
+    }
+    uint32_t hd = 0;
+#pragma unroll
+    for (int i = 0; i < nv; ++i)
+        if (st.a[o + i] < 0) hd |= 1u << i;
+    KT k[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) k[c] = KINF;
+    uint32_t mpos = 0, flag = 0;
+    int C, lc;
+    const int s = lane;
+    const P ps = st.pen;
+    if (type == OP_REP) {
+        // Repetition (Sec. III-E): the ML word listed first.
+        C = 2;
+        lc = 1;
+        P x0[nv], x1[nv];
+#pragma unroll
+        for (int i = 0; i < nv; ++i) {
+            x0[i] = Arith<T>::negpart(st.a[o + i]);
+            x1[i] = Arith<T>::pospart(st.a[o + i]);
+        }
+#pragma unroll
+        for (int h = nv >> 1; h >= 1; h >>= 1)
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                x0[i] = x0[i] + x0[i + h];
+                x1[i] = x1[i] + x1[i + h];
+            }
+        flag = (x0[0] <= x1[0]) ? 0u : 1u;
+        k[0] = Arith<T>::mk(ps + (flag ? x1[0] : x0[0]), s * 2 + 0);
+        k[1] = Arith<T>::mk(ps + (flag ? x0[0] : x1[0]), s * 2 + 1);
+    } else {
+        // least reliable positions by (|a|, index): keys |a| << 4 | i
+        unsigned long long lk[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+        if (nv <= 4) {
+            // a sorting network over the (at most four) keys
+#pragma unroll
+            for (int i = 0; i < nv; ++i) lk[i] = ((unsigned long long)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
+            if (nv >= 2) ce(lk[0], lk[1]);
+            if (nv == 4) {
+                ce(lk[2], lk[3]); ce(lk[0], lk[2]); ce(lk[1], lk[3]); ce(lk[1], lk[2]);
+            }
+        } else {
+            const int R = (type == OP_R1) ? 2 : 4;
+#pragma unroll
+            for (int i = 0; i < nv; ++i) {
+                unsigned long long v = ((unsigned long long)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
+                if (v < lk[R - 1]) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        if (r < R && v < lk[r]) { const unsigned long long t2 = lk[r]; lk[r] = v; v = t2; }
+                    }
+                }
+            }
+        }
+        P ar[4];
+        uint32_t m[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            ar[r] = Arith<T>::unabs((uint32_t)(lk[r] >> 4));
+            m[r] = (uint32_t)(lk[r] & 15u);
+        }
+        mpos = m[0] | (m[1] << 4) | (m[2] << 8) | (m[3] << 12);
+        if (type == OP_R1) {
+            // Rate-1 (Sec. III-C): HD, HD^m1, HD^m2, HD^m1^m2.
+            C = nv == 1 ? 2 : 4;
+            lc = nv == 1 ? 1 : 2;
+            k[0] = Arith<T>::mk(ps, s * C + 0);
+            k[1] = Arith<T>::mk(ps + ar[0], s * C + 1);
+            if (nv > 1) {
+                k[2] = Arith<T>::mk(ps + ar[1], s * C + 2);
+                k[3] = Arith<T>::mk(ps + (ar[0] + ar[1]), s * C + 3);
+            }
+        } else {
+            // SPC (Sec. III-D): ML = HD or HD^m1; ML ^ T, penalty from Eq. (9).
+            C = cx.L == 2 ? 2 : 8;
+            lc = cx.L == 2 ? 1 : 3;
+            flag = (__popc(hd) & 1u) ? 0u : 1u;   // q
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (c < C) {
+                    const uint32_t dm = spc_tmask(c) ^ (flag ? 0u : 1u);
+                    P inc = (P)0;
+                    bool first = true;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if ((dm >> r) & 1u) { inc = first ? ar[r] : inc + ar[r]; first = false; }
+                    k[c] = Arith<T>::mk(ps + inc, s * C + c);
+                }
+            }
+            if (C == 8) sort8(k);
         }
     }
-    return x[0];
+    if (!act) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) k[c] = KINF;
+    }
+    const int nc = cx.La * C;
+    const KT kt = select_keys<KT>(k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], C, nc, cx.L, lane, cx.tab);
+    const int La2 = nc < cx.L ? nc : cx.L;
+    const bool act2 = lane < La2;
+    const uint32_t ci = Arith<T>::kidx(kt);
+    const int src = act2 ? (int)(ci >> lc) : 0;
+    const int c = (int)(ci & (uint32_t)(C - 1));
+    const uint32_t hd_s = __shfl_sync(FULL, hd, src);
+    const uint32_t mp_s = __shfl_sync(FULL, mpos, src);
+    const uint32_t fl_s = __shfl_sync(FULL, flag, src);
+#pragma unroll
+    for (int i = o + nv; i < 31; ++i) st.a[i] = __shfl_sync(FULL, st.a[i], src);
+#pragma unroll
+    for (int jj = J; jj < 5; ++jj) st.bl[jj] = __shfl_sync(FULL, st.bl[jj], src);
+    st.orig = __shfl_sync(FULL, st.orig, src);
+    if (act2) st.pen = Arith<T>::kpen(kt);
+    uint32_t word;
+    if (type == OP_REP) {
+        word = ((fl_s != 0u) != (c == 1)) ? wmask : 0u;
+    } else {
+        const uint32_t dm = (type == OP_R1) ? (uint32_t)c : (spc_tmask(c) ^ (fl_s ? 0u : 1u));
+        word = hd_s;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+            if ((dm >> rr) & 1u) word ^= 1u << ((mp_s >> (4 * rr)) & 15u);
+    }
+    if (side) st.br = word; else st.bl[J] = word;
+    cx.La = La2;
+    __syncwarp();
+}
+
+template <typename T, int J>
+__device__ __forceinline__ void sub_node(Sub<T> &st, Desc &d, int side, SubCtx<T> &cx) {
+    const uint32_t type = d.next();
+    if (J == 0 || type != 0u) {
+        sub_leaf<T, J>(type, st, side, cx);
+        return;
+    }
+    if constexpr (J > 0) {
+        constexpr int h = 1 << (J - 1);
+#pragma unroll 1
+        for (int sd = 0; sd < 2; ++sd) {
+            if (sd == 0) {
+#pragma unroll
+                for (int i = 0; i < h; ++i) st.a[aoff<J - 1>() + i] = fv(st.a[aoff<J>() + i], st.a[aoff<J>() + i + h]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < h; ++i)
+                    st.a[aoff<J - 1>() + i] =
+                        gv(st.a[aoff<J>() + i], st.a[aoff<J>() + i + h], (st.bl[J - 1] >> i) & 1u);
+            }
+            sub_node<T, J - 1>(st, d, sd, cx);
+        }
+        constexpr uint32_t m = (1u << h) - 1u;
+        const uint32_t v = ((st.bl[J - 1] ^ st.br) & m) | ((st.br & m) << h);
+        if (side == 0) st.bl[J] = v; else st.br = v;
+    }
+}
+
+// ---- run one register subtree -------------------------------------------
+// Warp 0: load the paths' alpha rows of stage JR, walk the subtree, then write
+// the root's beta, penalties and index rows.
+template <typename T, int JR>
+__device__ __forceinline__ void run_sub(const CodeView &cv, uint8_t *S, uint8_t *Gs, uint32_t op, int La, int cur,
+                                        int lane) {
+    typedef typename Arith<T>::P PT;
+    typedef typename Arith<T>::K KT;
+    const Layout &lay = cv.lay;
+    const int n = cv.n;
+    const int dest = op_dest(op);
+    uint8_t *idxc = S + lay.idx[cur];
+    uint8_t *bidxc = S + lay.bidx[cur];
+    PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
+    Sub<T> st;
+    const bool act = lane < La;
+    const T *row = (JR == n) ? chan_ptr<T>(lay, S, Gs)
+                             : alpha_ptr<T>(lay, S, Gs, JR) + ((int)idxc[(act ? lane : 0) * 16 + JR] << JR);
+    constexpr int o = aoff<JR>();
+#pragma unroll
+    for (int i = 0; i < 31; ++i) st.a[i] = 0;
+    if (act) {
+        if (sizeof(T) == 4) {
+#pragma unroll
+            for (int q = 0; q < (1 << JR) / 4; ++q) {
+                const float4 v = reinterpret_cast<const float4 *>(row)[q];
+                st.a[o + 4 * q] = v.x; st.a[o + 4 * q + 1] = v.y; st.a[o + 4 * q + 2] = v.z; st.a[o + 4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < (1 << JR) / 4; ++q) {
+                const uint32_t v = reinterpret_cast<const uint32_t *>(row)[q];
+                st.a[o + 4 * q] = (int)(int8_t)(v & 0xFF);
+                st.a[o + 4 * q + 1] = (int)(int8_t)((v >> 8) & 0xFF);
+                st.a[o + 4 * q + 2] = (int)(int8_t)((v >> 16) & 0xFF);
+                st.a[o + 4 * q + 3] = (int)(int8_t)(v >> 24);
+            }
+        }
+        st.pen = penc[lane];
+    } else {
+        st.pen = (PT)0;
+    }
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) st.bl[jj] = 0u;
+    st.br = 0u;
+    st.orig = lane;
+    const uint32_t di = op_sub_desc(op);
+    Desc d;
+    d.w0 = __ldg(cv.desc + 2 * di);
+    d.w1 = __ldg(cv.desc + 2 * di + 1);
+    d.pos = 0;
+    SubCtx<T> cx;
+    cx.tab = reinterpret_cast<KT *>(S + lay.surv);
+    cx.lane = lane;
+    cx.La = La;
+    cx.L = cv.L;
+    sub_node<T, JR>(st, d, dest, cx);
+    const bool act2 = lane < cx.La;
+    const uint32_t beta = dest ? st.br : st.bl[JR];
+    uint32_t *bout = dest ? br_ptr(lay, S, Gs) : bl_ptr(lay, S, Gs, JR);
+    const int ostride = dest ? beta_words(n) : beta_words(JR);
+    if (act2) {
+        if (op_sub_fork(op)) {
+            const int nxt = cur ^ 1;
+            uint8_t *idxn = S + lay.idx[nxt];
+            uint8_t *bidxn = S + lay.bidx[nxt];
+            reinterpret_cast<PT *>(S + lay.pen[nxt])[lane] = st.pen;
+            reinterpret_cast<uint4 *>(idxn)[lane] = reinterpret_cast<const uint4 *>(idxc)[st.orig];
+            reinterpret_cast<uint4 *>(bidxn)[lane] = reinterpret_cast<const uint4 *>(bidxc)[st.orig];
+            if (!dest) bidxn[lane * 16 + JR] = (uint8_t)lane;
+        } else {
+            penc[lane] = st.pen;
+            if (!dest) bidxc[lane * 16 + JR] = (uint8_t)lane;
+        }
+        bout[lane * ostride] = beta;
+    }
+}
+
+// ---- large leaves (more than 16 bits), warp 0, lane s = source path s ----
+
+// Canonical sums of |min(a,0)| (v0) and |max(a,0)| (v1) over one row of nv
+// (>= 32) elements. float: the pairwise tree s[i] = x[i] + x[i + n/2] is
+// evaluated in place on the row (the leaf input is dead afterwards); int8:
+// exact integer sums.
+template <typename T>
+__device__ __forceinline__ void lane_sums(T *row, int nv, bool want1, typename Arith<T>::P &v0,
+                                          typename Arith<T>::P &v1) {
+    if (sizeof(T) == 4) {
+        float *x = reinterpret_cast<float *>(row);
+        const int h = nv >> 1;
+        for (int i = 0; i < h; i += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(x + i);
+            const float4 b = *reinterpret_cast<const float4 *>(x + h + i);
+            float4 y0, y1;
+            y0.x = Arith<float>::negpart(a.x) + Arith<float>::negpart(b.x);
+            y0.y = Arith<float>::negpart(a.y) + Arith<float>::negpart(b.y);
+            y0.z = Arith<float>::negpart(a.z) + Arith<float>::negpart(b.z);
+            y0.w = Arith<float>::negpart(a.w) + Arith<float>::negpart(b.w);
+            *reinterpret_cast<float4 *>(x + i) = y0;
+            if (want1) {
+                y1.x = Arith<float>::pospart(a.x) + Arith<float>::pospart(b.x);
+                y1.y = Arith<float>::pospart(a.y) + Arith<float>::pospart(b.y);
+                y1.z = Arith<float>::pospart(a.z) + Arith<float>::pospart(b.z);
+                y1.w = Arith<float>::pospart(a.w) + Arith<float>::pospart(b.w);
+                *reinterpret_cast<float4 *>(x + h + i) = y1;
+            }
+        }
+        for (int hh = h >> 1; hh >= 1; hh >>= 1) {
+            if (hh >= 4) {
+                for (int i = 0; i < hh; i += 4) {
+                    float4 a = *reinterpret_cast<const float4 *>(x + i);
+                    const float4 b = *reinterpret_cast<const float4 *>(x + hh + i);
+                    a.x = a.x + b.x; a.y = a.y + b.y; a.z = a.z + b.z; a.w = a.w + b.w;
+                    *reinterpret_cast<float4 *>(x + i) = a;
+                    if (want1) {
+                        float4 c = *reinterpret_cast<const float4 *>(x + h + i);
+                        const float4 d = *reinterpret_cast<const float4 *>(x + h + hh + i);
+                        c.x = c.x + d.x; c.y = c.y + d.y; c.z = c.z + d.z; c.w = c.w + d.w;
+                        *reinterpret_cast<float4 *>(x + h + i) = c;
+                    }
+                }
+            } else {
+                for (int i = 0; i < hh; ++i) {
+                    x[i] = x[i] + x[i + hh];
+                    if (want1) x[h + i] = x[h + i] + x[h + i + hh];
+                }
+            }
+        }
+        v0 = (typename Arith<T>::P)x[0];
+        v1 = want1 ? (typename Arith<T>::P)x[h] : (typename Arith<T>::P)0;
+    } else {
+        int s0 = 0, s1 = 0;
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        for (int q = 0; q < (nv >> 4); ++q) {
+            const uint4 v = r4[q];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int a = (int)(int8_t)((w[e] >> (8 * b)) & 0xFF);
+                    s0 += a < 0 ? -a : 0;
+                    s1 += a > 0 ? a : 0;
+                }
+            }
+        }
+        v0 = (typename Arith<T>::P)s0;
+        v1 = (typename Arith<T>::P)s1;
+    }
+}
+
+// Least-reliable-bit keys: |a| << 12 | position (float: 64-bit, int8: 32-bit).
+template <typename T> struct LrbKey;
+template <> struct LrbKey<float> {
+    typedef unsigned long long K;
+    static __device__ __forceinline__ K make(float a, int pos) {
+        return ((K)__float_as_uint(fabsf(a)) << 12) | (unsigned)pos;
+    }
+};
+template <> struct LrbKey<int8_t> {
+    typedef uint32_t K;
+    static __device__ __forceinline__ K make(int a, int pos) { return ((uint32_t)(a < 0 ? -a : a) << 12) | (unsigned)pos; }
+};
+
+template <typename K, int R>
+__device__ __forceinline__ void lrb_insert(K (&top)[4], K v) {
+    if (v < top[R - 1]) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (v < top[r]) { const K t = top[r]; top[r] = v; v = t; }
+        }
+    }
+}
+
+// One scan of a row: the R least reliable positions and the number of negative LLRs.
+template <typename T, int R>
+__device__ __forceinline__ void lane_lrb(const T *row, int nv, typename LrbKey<T>::K (&top)[4], int &neg) {
+    typedef typename LrbKey<T>::K K;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) top[r] = (K)~(K)0;
+    int cnt = 0;
+    if (sizeof(T) == 4) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+        for (int q = 0; q < (nv >> 2); ++q) {
+            const float4 v = r4[q];
+            cnt += (v.x < 0.f) + (v.y < 0.f) + (v.z < 0.f) + (v.w < 0.f);
+            lrb_insert<K, R>(top, LrbKey<T>::make(v.x, 4 * q));
+            lrb_insert<K, R>(top, LrbKey<T>::make(v.y, 4 * q + 1));
+            lrb_insert<K, R>(top, LrbKey<T>::make(v.z, 4 * q + 2));
+            lrb_insert<K, R>(top, LrbKey<T>::make(v.w, 4 * q + 3));
+        }
+    } else {
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        for (int q = 0; q < (nv >> 4); ++q) {
+            const uint4 v = r4[q];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                cnt += __popc(w[e] & 0x80808080u);
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    lrb_insert<K, R>(top, LrbKey<T>::make((int)(int8_t)((w[e] >> (8 * b)) & 0xFF), 16 * q + 4 * e + b));
+            }
+        }
+    }
+    neg = cnt;
+}
+
+// Hard decisions of 32 consecutive LLRs as one word (bit i <-> element i).
+template <typename T>
+__device__ __forceinline__ uint32_t hd_word(const T *p) {
+    uint32_t w = 0;
+    if (sizeof(T) == 4) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 v = r4[q];
+            w |= ((uint32_t)(v.x < 0.f) | ((uint32_t)(v.y < 0.f) << 1) | ((uint32_t)(v.z < 0.f) << 2) |
+                  ((uint32_t)(v.w < 0.f) << 3)) << (4 * q);
+        }
+    } else {
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 v = r4[h];
+            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t t = (x[e] >> 7) & 0x01010101u;              // sign bit of each byte
+                w |= (((t * 0x01020408u) >> 24) & 0xFu) << (16 * h + 4 * e);
+            }
+        }
+    }
+    return w;
+}
+
+template <typename T>
+__device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t *Gs, uint32_t kind, int j, int dest,
+                                         int La, int cur, int lane) {
+    typedef typename Arith<T>::P PT;
+    typedef typename Arith<T>::K KT;
+    typedef typename LrbKey<T>::K LK;
+    constexpr KT KINF = Arith<T>::KINF;
+    const Layout &lay = cv.lay;
+    const int n = cv.n, L = cv.L;
+    const int nv = 1 << j;
+    const int bw = nv >> 5;
+    T *stj = (j == n) ? chan_ptr<T>(lay, S, Gs) : alpha_ptr<T>(lay, S, Gs, j);
+    uint8_t *idxc = S + lay.idx[cur];
+    uint8_t *bidxc = S + lay.bidx[cur];
+    PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
+    uint32_t *bout = dest ? br_ptr(lay, S, Gs) : bl_ptr(lay, S, Gs, j);
+    const int ostride = dest ? beta_words(n) : bw;
+    const bool act = lane < La;
+    const int s = lane;
+    T *row = stj + (j == n ? 0 : ((int)idxc[(act ? s : 0) * 16 + j] << j));
+    const PT ps = act ? penc[s] : (PT)0;
+    KT k[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) k[c] = KINF;
+    uint32_t flag = 0, mp01 = 0, mp23 = 0;
+    int C = 2, lc = 1;
+    if (kind == OP_R0 || kind == OP_REP) {
+        PT v0 = 0, v1 = 0;
+        if (act) lane_sums<T>(row, nv, kind == OP_REP, v0, v1);
+        if (kind == OP_R0) {
+            // Rate-0 (Sec. III-B): no fork, penalty += sum |min(a, 0)|, beta = 0.
+            if (act) {
+                penc[s] = ps + v0;
+                for (int w = 0; w < bw; ++w) bout[s * ostride + w] = 0u;
+                if (!dest) bidxc[s * 16 + j] = (uint8_t)s;
+            }
+            return;
+        }
+        // Repetition (Sec. III-E): the ML word listed first.
+        flag = (v0 <= v1) ? 0u : 1u;
+        k[0] = Arith<T>::mk(ps + (flag ? v1 : v0), s * 2 + 0);
+        k[1] = Arith<T>::mk(ps + (flag ? v0 : v1), s * 2 + 1);
+    } else {
+        LK top[4];
+        int neg = 0;
+        if (kind == OP_R1) lane_lrb<T, 2>(row, nv, top, neg);
+        else lane_lrb<T, 4>(row, nv, top, neg);
+        PT ar[4];
+        uint32_t m[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            ar[r] = Arith<T>::unabs((uint32_t)(top[r] >> 12));
+            m[r] = (uint32_t)(top[r] & 0xFFFu);
+        }
+        mp01 = m[0] | (m[1] << 16);
+        mp23 = m[2] | (m[3] << 16);
+        if (kind == OP_R1) {
+            // Rate-1 (Sec. III-C): HD, HD^m1, HD^m2, HD^m1^m2.
+            C = 4;
+            lc = 2;
+            k[0] = Arith<T>::mk(ps, s * 4 + 0);
+            k[1] = Arith<T>::mk(ps + ar[0], s * 4 + 1);
+            k[2] = Arith<T>::mk(ps + ar[1], s * 4 + 2);
+            k[3] = Arith<T>::mk(ps + (ar[0] + ar[1]), s * 4 + 3);
+        } else {
+            // SPC (Sec. III-D): ML = HD or HD^m1; ML ^ T, penalty from Eq. (9).
+            C = L == 2 ? 2 : 8;
+            lc = L == 2 ? 1 : 3;
+            flag = (neg & 1) ? 0u : 1u;   // q
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (c < C) {
+                    const uint32_t dm = spc_tmask(c) ^ (flag ? 0u : 1u);
+                    PT inc = (PT)0;
+                    bool first = true;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if ((dm >> r) & 1u) { inc = first ? ar[r] : inc + ar[r]; first = false; }
+                    k[c] = Arith<T>::mk(ps + inc, s * C + c);
+                }
+            }
+            if (C == 8) sort8(k);
+        }
+    }
+    if (!act) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) k[c] = KINF;
+    }
+    // selection (Algorithm 1)
+    const int nc = La * C;
+    const KT tau = (nc > L) ? warp_kth(k, C, L, lane) : KINF;
+    uint32_t sm = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (k[r] != KINF && k[r] <= tau) sm |= 1u << (Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
+    const int base = warp_excl_scan(__popc(sm), lane);
+    KT *tab = reinterpret_cast<KT *>(S + lay.surv);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (k[r] != KINF && k[r] <= tau) {
+            const int c = (int)(Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
+            tab[base + __popc(sm & ((1u << c) - 1u))] = k[r];
+        }
+    }
+    __syncwarp();
+    // commit: new slot t (lane t) takes source s's rows, the new penalty and the candidate beta
+    const int La2 = nc < L ? nc : L;
+    const bool act2 = lane < La2;
+    const KT kt = act2 ? tab[lane] : (KT)0;
+    const uint32_t ci = Arith<T>::kidx(kt);
+    const int src = act2 ? (int)(ci >> lc) : 0;
+    const int c = (int)(ci & (uint32_t)(C - 1));
+    const uint32_t fl_s = __shfl_sync(FULL, flag, src);
+    const uint32_t m01 = __shfl_sync(FULL, mp01, src);
+    const uint32_t m23 = __shfl_sync(FULL, mp23, src);
+    if (act2) {
+        const int nxt = cur ^ 1;
+        uint8_t *idxn = S + lay.idx[nxt];
+        uint8_t *bidxn = S + lay.bidx[nxt];
+        reinterpret_cast<PT *>(S + lay.pen[nxt])[lane] = Arith<T>::kpen(kt);
+        reinterpret_cast<uint4 *>(idxn)[lane] = reinterpret_cast<const uint4 *>(idxc)[src];
+        reinterpret_cast<uint4 *>(bidxn)[lane] = reinterpret_cast<const uint4 *>(bidxc)[src];
+        if (!dest) bidxn[lane * 16 + j] = (uint8_t)lane;
+        uint32_t *ob = bout + lane * ostride;
+        if (kind == OP_REP) {
+            const uint32_t word = ((fl_s != 0u) != (c == 1)) ? 0xffffffffu : 0u;
+            for (int w = 0; w < bw; ++w) ob[w] = word;
+        } else {
+            const uint32_t dm = (kind == OP_R1) ? (uint32_t)c : (spc_tmask(c) ^ (fl_s ? 0u : 1u));
+            const uint32_t mm[4] = {m01 & 0xFFFFu, m01 >> 16, m23 & 0xFFFFu, m23 >> 16};
+            const T *srow = stj + (j == n ? 0 : ((int)idxc[src * 16 + j] << j));
+            for (int w = 0; w < bw; ++w) {
+                uint32_t word = hd_word<T>(srow + (w << 5));
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr)
+                    if (((dm >> rr) & 1u) && (int)(mm[rr] >> 5) == w) word ^= 1u << (mm[rr] & 31u);
+                ob[w] = word;
+            }
+        }
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -329,559 +856,283 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                                              uint8_t *bits_row, float *pm_out, uint8_t *ok_out, int32_t *slot_out,
                                              int gidx, int gtid) {
     typedef typename Arith<T>::P PT;
-    typedef typename Arith<T>::K KT;
-    constexpr KT KINF = Arith<T>::KINF;
     constexpr int GT = W * 32;
     const Layout &lay = cv.lay;
     const int lane = gtid & 31;
     const int wig = gtid >> 5;
     const int n = cv.n, N = cv.N, L = cv.L;
     const int bwn = beta_words(n);
-
-    T *chan = reinterpret_cast<T *>(S + lay.chan);
-    KT *keys = reinterpret_cast<KT *>(S + lay.key);
-    KT *survk = reinterpret_cast<KT *>(S + lay.surv);
-    uint4 *cinfo = reinterpret_cast<uint4 *>(S + lay.cinfo);
-    uint32_t *br = reinterpret_cast<uint32_t *>(S + lay.br);
+    T *chan = chan_ptr<T>(lay, S, Gs);
+    uint32_t *br = br_ptr(lay, S, Gs);
     uint32_t *ubuf = reinterpret_cast<uint32_t *>(S + lay.ubuf);
 
+    // ---------------- channel LLRs -> stage n ----------------
     {
-        // ---------------- channel LLRs -> stage n ----------------
-        {
-            const size_t nbytes = (size_t)N * sizeof(T);
-            if (((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (nbytes & 15u) == 0) {
-                const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-                uint4 *d4 = reinterpret_cast<uint4 *>(chan);
-                for (int t = gtid; t < (int)(nbytes >> 4); t += GT) {
-                    uint4 v = __ldcs(s4 + t);
-                    if (sizeof(T) == 1) {   // read -128 as -127
-                        v.x = __vmaxs4(v.x, 0x81818181u); v.y = __vmaxs4(v.y, 0x81818181u);
-                        v.z = __vmaxs4(v.z, 0x81818181u); v.w = __vmaxs4(v.w, 0x81818181u);
-                    }
-                    d4[t] = v;
+        const size_t nbytes = (size_t)N * sizeof(T);
+        if (((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (nbytes & 15u) == 0) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(chan);
+            for (int t = gtid; t < (int)(nbytes >> 4); t += GT) {
+                uint4 v = __ldcs(s4 + t);
+                if (sizeof(T) == 1) {   // read -128 as -127
+                    v.x = __vmaxs4(v.x, 0x81818181u); v.y = __vmaxs4(v.y, 0x81818181u);
+                    v.z = __vmaxs4(v.z, 0x81818181u); v.w = __vmaxs4(v.w, 0x81818181u);
                 }
-            } else {
-                for (int t = gtid; t < N; t += GT) {
-                    T v = reinterpret_cast<const T *>(src)[t];
-                    if (sizeof(T) == 1 && (int)v < -127) v = (T)-127;
-                    chan[t] = v;
-                }
+                d4[t] = v;
+            }
+        } else {
+            for (int t = gtid; t < N; t += GT) {
+                T v = reinterpret_cast<const T *>(src)[t];
+                if (sizeof(T) == 1 && (int)v < -127) v = (T)-127;
+                chan[t] = v;
             }
         }
-        // index tables start at row 0 so that no entry can point outside a stage
-        for (int t = gtid; t < L * 4; t += GT) {
-            reinterpret_cast<uint32_t *>(S + lay.idx[0])[t] = 0u;
-            reinterpret_cast<uint32_t *>(S + lay.idx[1])[t] = 0u;
-            reinterpret_cast<uint32_t *>(S + lay.bidx[0])[t] = 0u;
-            reinterpret_cast<uint32_t *>(S + lay.bidx[1])[t] = 0u;
-        }
-        int La = 1, cur = 0;
-        if (gtid == 0) reinterpret_cast<PT *>(S + lay.pen[0])[0] = (PT)0;
-        gsync<W>(gidx);
+    }
+    // index tables start at row 0 so that no entry can point outside a stage
+    for (int t = gtid; t < L * 4; t += GT) {
+        reinterpret_cast<uint32_t *>(S + lay.idx[0])[t] = 0u;
+        reinterpret_cast<uint32_t *>(S + lay.idx[1])[t] = 0u;
+        reinterpret_cast<uint32_t *>(S + lay.bidx[0])[t] = 0u;
+        reinterpret_cast<uint32_t *>(S + lay.bidx[1])[t] = 0u;
+    }
+    int La = 1, cur = 0;
+    if (gtid == 0) reinterpret_cast<PT *>(S + lay.pen[0])[0] = (PT)0;
+    gsync<W>(gidx);
 
-        uint32_t op = __ldg(cv.ops);
-        for (int o = 0; o < cv.n_ops; ++o) {
-            const uint32_t opn = (o + 1 < cv.n_ops) ? __ldg(cv.ops + o + 1) : 0u;
-            const uint32_t kind = op_kind(op);
-            const int j = op_stage(op);
-            const int dest = op_dest(op);
-            const bool solo = op_solo(op);
-            const bool runs = !solo || wig == 0;
-            const int tid = solo ? lane : gtid;
-            const int nthr = solo ? 32 : GT;
-            uint8_t *idxc = S + lay.idx[cur];
-            uint8_t *bidxc = S + lay.bidx[cur];
+    uint32_t op = __ldg(cv.ops);
+    for (int o = 0; o < cv.n_ops; ++o) {
+        const uint32_t opn = (o + 1 < cv.n_ops) ? __ldg(cv.ops + o + 1) : 0u;
+        const uint32_t kind = op_kind(op);
+        const int j = op_stage(op);
+        const int dest = op_dest(op);
+        const bool solo = op_solo(op);
+        const int tid = solo ? lane : gtid;
+        const int nthr = solo ? 32 : GT;
+        uint8_t *idxc = S + lay.idx[cur];
+        uint8_t *bidxc = S + lay.bidx[cur];
 
-            if (kind == OP_F || kind == OP_G) {
-                if (runs) {
-                    // ---------------- F / G: stage j -> stage j-1 ----------------
-                    const int jo = j - 1;
-                    const int h = 1 << jo;
-                    const T *inb = (j == n) ? chan : stage_ptr<T>(lay, S, Gs, j);
-                    T *outb = stage_ptr<T>(lay, S, Gs, jo);
-                    const bool isG = kind == OP_G;
-                    const uint32_t *blb = reinterpret_cast<const uint32_t *>(S + lay.bl[jo]);
-                    const int bwc = beta_words(jo);
-                    if (sizeof(T) == 4 && h >= 4) {
-                        const int lv = jo - 2;
-                        const int total = La << lv;
-                        for (int t = tid; t < total; t += nthr) {
-                            const int p = t >> lv, v = t & ((1 << lv) - 1);
-                            const float *in = reinterpret_cast<const float *>(inb) + (j == n ? 0 : ((int)idxc[p * 16 + j] << j));
-                            const float4 a = reinterpret_cast<const float4 *>(in)[v];
-                            const float4 b = reinterpret_cast<const float4 *>(in + h)[v];
+        if (kind == OP_F || kind == OP_G) {
+            if (!solo || wig == 0) {
+                // ---------------- F / G: stage j -> stage j-1 ----------------
+                const int jo = j - 1;
+                const int h = 1 << jo;
+                const T *inb = (j == n) ? chan : alpha_ptr<T>(lay, S, Gs, j);
+                T *outb = alpha_ptr<T>(lay, S, Gs, jo);
+                const bool isG = kind == OP_G;
+                const uint32_t *blb = bl_ptr(lay, S, Gs, jo);
+                const int bwc = beta_words(jo);
+                if (sizeof(T) == 4) {
+                    const int lv = jo - 2;             // h >= 16 here: float4 items
+                    const int total = La << lv;
+                    for (int t0 = tid; t0 < total; t0 += 2 * nthr) {
+                        float4 a[2], b[2];
+                        uint32_t nb[2] = {0u, 0u};
+                        int pp[2], vv[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int t = t0 + u * nthr;
+                            pp[u] = t < total ? t >> lv : 0;
+                            vv[u] = t < total ? t & ((1 << lv) - 1) : 0;
+                            const float *in = reinterpret_cast<const float *>(inb) +
+                                              (j == n ? 0 : ((int)idxc[pp[u] * 16 + j] << j));
+                            a[u] = reinterpret_cast<const float4 *>(in)[vv[u]];
+                            b[u] = reinterpret_cast<const float4 *>(in + h)[vv[u]];
+                            if (isG) {
+                                const int i = vv[u] << 2;
+                                nb[u] = blb[(int)bidxc[pp[u] * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            if (t0 + u * nthr >= total) break;
                             float4 r;
                             if (isG) {
-                                const int i = v << 2;
-                                const uint32_t nb = blb[(int)bidxc[p * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
-                                r.x = g_op(a.x, b.x, nb & 1u); r.y = g_op(a.y, b.y, (nb >> 1) & 1u);
-                                r.z = g_op(a.z, b.z, (nb >> 2) & 1u); r.w = g_op(a.w, b.w, (nb >> 3) & 1u);
+                                r.x = g_op(a[u].x, b[u].x, nb[u] & 1u); r.y = g_op(a[u].y, b[u].y, (nb[u] >> 1) & 1u);
+                                r.z = g_op(a[u].z, b[u].z, (nb[u] >> 2) & 1u); r.w = g_op(a[u].w, b[u].w, (nb[u] >> 3) & 1u);
                             } else {
-                                r.x = f_op(a.x, b.x); r.y = f_op(a.y, b.y); r.z = f_op(a.z, b.z); r.w = f_op(a.w, b.w);
+                                r.x = f_op(a[u].x, b[u].x); r.y = f_op(a[u].y, b[u].y);
+                                r.z = f_op(a[u].z, b[u].z); r.w = f_op(a[u].w, b[u].w);
                             }
-                            reinterpret_cast<float4 *>(reinterpret_cast<float *>(outb) + (p << jo))[v] = r;
+                            reinterpret_cast<float4 *>(reinterpret_cast<float *>(outb) + (pp[u] << jo))[vv[u]] = r;
                         }
-                    } else if (sizeof(T) == 1 && h >= 16) {
-                        const int lv = jo - 4;
-                        const int total = La << lv;
-                        for (int t = tid; t < total; t += nthr) {
-                            const int p = t >> lv, v = t & ((1 << lv) - 1);
-                            const int8_t *in = reinterpret_cast<const int8_t *>(inb) + (j == n ? 0 : ((int)idxc[p * 16 + j] << j));
-                            const uint4 a = reinterpret_cast<const uint4 *>(in)[v];
-                            const uint4 b = reinterpret_cast<const uint4 *>(in + h)[v];
+                    }
+                } else {
+                    const int lv = jo - 4;             // h >= 16 here: 16-byte items
+                    const int total = La << lv;
+                    for (int t0 = tid; t0 < total; t0 += 2 * nthr) {
+                        uint4 a[2], b[2];
+                        uint32_t nb[2] = {0u, 0u};
+                        int pp[2], vv[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int t = t0 + u * nthr;
+                            pp[u] = t < total ? t >> lv : 0;
+                            vv[u] = t < total ? t & ((1 << lv) - 1) : 0;
+                            const int8_t *in = reinterpret_cast<const int8_t *>(inb) +
+                                               (j == n ? 0 : ((int)idxc[pp[u] * 16 + j] << j));
+                            a[u] = reinterpret_cast<const uint4 *>(in)[vv[u]];
+                            b[u] = reinterpret_cast<const uint4 *>(in + h)[vv[u]];
+                            if (isG) {
+                                const int i = vv[u] << 4;
+                                nb[u] = blb[(int)bidxc[pp[u] * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            if (t0 + u * nthr >= total) break;
                             uint4 r;
                             if (isG) {
-                                const int i = v << 4;
-                                const uint32_t nb = blb[(int)bidxc[p * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
-                                r.x = g4(a.x, b.x, nb & 15u); r.y = g4(a.y, b.y, (nb >> 4) & 15u);
-                                r.z = g4(a.z, b.z, (nb >> 8) & 15u); r.w = g4(a.w, b.w, (nb >> 12) & 15u);
+                                r.x = g4(a[u].x, b[u].x, nb[u] & 15u); r.y = g4(a[u].y, b[u].y, (nb[u] >> 4) & 15u);
+                                r.z = g4(a[u].z, b[u].z, (nb[u] >> 8) & 15u); r.w = g4(a[u].w, b[u].w, (nb[u] >> 12) & 15u);
                             } else {
-                                r.x = f4(a.x, b.x); r.y = f4(a.y, b.y); r.z = f4(a.z, b.z); r.w = f4(a.w, b.w);
+                                r.x = f4(a[u].x, b[u].x); r.y = f4(a[u].y, b[u].y);
+                                r.z = f4(a[u].z, b[u].z); r.w = f4(a[u].w, b[u].w);
                             }
-                            reinterpret_cast<uint4 *>(reinterpret_cast<int8_t *>(outb) + (p << jo))[v] = r;
-                        }
-                    } else if (sizeof(T) == 1 && h >= 4) {
-                        const int lv = jo - 2;
-                        const int total = La << lv;
-                        for (int t = tid; t < total; t += nthr) {
-                            const int p = t >> lv, v = t & ((1 << lv) - 1);
-                            const int8_t *in = reinterpret_cast<const int8_t *>(inb) + (j == n ? 0 : ((int)idxc[p * 16 + j] << j));
-                            const uint32_t a = reinterpret_cast<const uint32_t *>(in)[v];
-                            const uint32_t b = reinterpret_cast<const uint32_t *>(in + h)[v];
-                            uint32_t r;
-                            if (isG) {
-                                const int i = v << 2;
-                                const uint32_t nb = blb[(int)bidxc[p * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
-                                r = g4(a, b, nb & 15u);
-                            } else {
-                                r = f4(a, b);
-                            }
-                            reinterpret_cast<uint32_t *>(reinterpret_cast<int8_t *>(outb) + (p << jo))[v] = r;
-                        }
-                    } else {
-                        const int total = La << jo;
-                        for (int t = tid; t < total; t += nthr) {
-                            const int p = t >> jo, i = t & (h - 1);
-                            const T *in = inb + (j == n ? 0 : ((int)idxc[p * 16 + j] << j));
-                            T r;
-                            if (isG) {
-                                const uint32_t bb = (blb[(int)bidxc[p * 16 + jo] * bwc + (i >> 5)] >> (i & 31)) & 1u;
-                                r = g_op(in[i], in[i + h], bb);
-                            } else {
-                                r = f_op(in[i], in[i + h]);
-                            }
-                            outb[(p << jo) + i] = r;
+                            reinterpret_cast<uint4 *>(reinterpret_cast<int8_t *>(outb) + (pp[u] << jo))[vv[u]] = r;
                         }
                     }
-                    for (int t = tid; t < La; t += nthr) idxc[t * 16 + jo] = (uint8_t)t;
                 }
-            } else if (kind == OP_COMB) {
-                if (runs) {
-                    // ---------------- Combine: [beta_l ^ beta_r, beta_r] ----------------
-                    const int jc = j - 1;
-                    const int bwc = beta_words(jc);
-                    const uint32_t *blb = reinterpret_cast<const uint32_t *>(S + lay.bl[jc]);
-                    uint32_t *out = dest ? br : reinterpret_cast<uint32_t *>(S + lay.bl[j]);
-                    const int ostride = dest ? bwn : beta_words(j);
-                    if (jc >= 5) {
-                        const int lw = jc - 5;
-                        const int total = La << lw;
-                        for (int t = tid; t < total; t += nthr) {
-                            const int p = t >> lw, w = t & (bwc - 1);
-                            const uint32_t l = blb[(int)bidxc[p * 16 + jc] * bwc + w];
-                            const uint32_t r = br[p * bwn + w];
-                            uint32_t *o2 = out + p * ostride;
-                            o2[w] = l ^ r;
-                            o2[w + bwc] = r;
-                        }
-                    } else {
-                        const int h = 1 << jc;
-                        const uint32_t m = (1u << h) - 1u;
-                        for (int t = tid; t < La; t += nthr) {
-                            const uint32_t l = blb[(int)bidxc[t * 16 + jc]];
-                            const uint32_t r = br[t * bwn];
-                            out[t * ostride] = ((l ^ r) & m) | ((r & m) << h);
-                        }
-                    }
-                    if (!dest)
-                        for (int t = tid; t < La; t += nthr) bidxc[t * 16 + j] = (uint8_t)t;
-                }
-            } else {
-                // ---------------- leaves ----------------
-                const int nv = 1 << j;
-                T *stj = (j == n) ? chan : stage_ptr<T>(lay, S, Gs, j);
-                PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
-                uint32_t *bout = dest ? br : reinterpret_cast<uint32_t *>(S + lay.bl[j]);
+                for (int t = tid; t < La; t += nthr) idxc[t * 16 + jo] = (uint8_t)t;
+            }
+        } else if (kind == OP_COMB) {
+            if (!solo || wig == 0) {
+                // ---------------- Combine: [beta_l ^ beta_r, beta_r] ----------------
+                const int jc = j - 1;                  // >= kSubLog
+                const int bwc = beta_words(jc);
+                const uint32_t *blb = bl_ptr(lay, S, Gs, jc);
+                uint32_t *out = dest ? br : bl_ptr(lay, S, Gs, j);
                 const int ostride = dest ? bwn : beta_words(j);
-                const uint32_t wmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
-                int C = 1;
-                if (kind == OP_R1) C = nv == 1 ? 2 : 4;
-                else if (kind == OP_REP) C = 2;
-                else if (kind == OP_SPC) C = L == 2 ? 2 : 8;
-                const int lc = C == 2 ? 1 : (C == 4 ? 2 : 3);
-                const int nc = La * C;
-                const int nxt = cur ^ 1;
-                uint8_t *idxn = S + lay.idx[nxt];
-                uint8_t *bidxn = S + lay.bidx[nxt];
-                PT *penn = reinterpret_cast<PT *>(S + lay.pen[nxt]);
-
-                if (nv <= 16) {
-                    // ------- small leaf: warp 0, lane s = source path s -------
-                    if (wig == 0) {
-                        const int s = lane;
-                        const bool act = s < La;
-                        const T *row = stj + (j == n ? 0 : ((int)idxc[(act ? s : 0) * 16 + j] << j));
-                        PT a[16];
-                        load16<T>(row, nv, act, a);
-                        const PT ps = act ? penc[s] : (PT)0;
-                        if (kind == OP_R0) {
-                            // Rate-0 (Sec. III-B): no fork, penalty += sum |min(a, 0)|, beta = 0.
-                            PT x[16];
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) x[i] = Arith<T>::negpart(a[i]);
-                            const PT v0 = reg_tree(x, nv);
-                            if (act) {
-                                penc[s] = ps + v0;
-                                bout[s * ostride] = 0u;
-                                if (!dest) bidxc[s * 16 + j] = (uint8_t)s;
-                            }
-                        } else {
-                            uint32_t hd = 0;
-#pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                if (i < nv && a[i] < 0) hd |= 1u << i;
-                            KT k[8];
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) k[c] = KINF;
-                            uint32_t mpos = 0, flag = 0;
-                            if (kind == OP_REP) {
-                                // Repetition (Sec. III-E): ML word listed first.
-                                PT x0[16], x1[16];
-#pragma unroll
-                                for (int i = 0; i < 16; ++i) {
-                                    x0[i] = Arith<T>::negpart(a[i]);
-                                    x1[i] = Arith<T>::pospart(a[i]);
-                                }
-                                const PT p0 = reg_tree(x0, nv), p1 = reg_tree(x1, nv);
-                                flag = (p0 <= p1) ? 0u : 1u;
-                                k[0] = Arith<T>::mk(ps + (flag ? p1 : p0), s * 2 + 0);
-                                k[1] = Arith<T>::mk(ps + (flag ? p0 : p1), s * 2 + 1);
-                            } else {
-                                // least reliable positions by (|a|, index): keys |a| << 4 | i
-                                unsigned long long lk[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-#pragma unroll
-                                for (int i = 0; i < 16; ++i) {
-                                    if (i < nv) {
-                                        unsigned long long v = ((unsigned long long)Arith<T>::absbits(a[i]) << 4) | (unsigned)i;
-#pragma unroll
-                                        for (int r = 0; r < 4; ++r) {
-                                            if (v < lk[r]) { const unsigned long long t2 = lk[r]; lk[r] = v; v = t2; }
-                                        }
-                                    }
-                                }
-                                uint32_t b[4], m[4];
-#pragma unroll
-                                for (int r = 0; r < 4; ++r) {
-                                    b[r] = (uint32_t)(lk[r] >> 4);
-                                    m[r] = (uint32_t)(lk[r] & 15u);
-                                }
-                                mpos = m[0] | (m[1] << 4) | (m[2] << 8) | (m[3] << 12);
-                                const PT a1 = Arith<T>::unabs(b[0]);
-                                if (kind == OP_R1) {
-                                    // Rate-1 (Sec. III-C): HD, HD^m1, HD^m2, HD^m1^m2.
-                                    k[0] = Arith<T>::mk(ps, s * C + 0);
-                                    k[1] = Arith<T>::mk(ps + a1, s * C + 1);
-                                    if (C == 4) {
-                                        const PT a2 = Arith<T>::unabs(b[1]);
-                                        k[2] = Arith<T>::mk(ps + a2, s * C + 2);
-                                        k[3] = Arith<T>::mk(ps + (a1 + a2), s * C + 3);
-                                    }
-                                } else {
-                                    // SPC (Sec. III-D): ML = HD or HD^m1; ML ^ T, penalty from Eq. (9).
-                                    flag = (__popc(hd) & 1u) ? 0u : 1u;   // q
-                                    PT ar[4];
-#pragma unroll
-                                    for (int r = 0; r < 4; ++r) ar[r] = Arith<T>::unabs(b[r]);
-#pragma unroll
-                                    for (int c = 0; c < 8; ++c) {
-                                        if (c < C) {
-                                            const uint32_t dm = spc_tmask(c) ^ (flag ? 0u : 1u);
-                                            PT inc = (PT)0;
-                                            bool first = true;
-#pragma unroll
-                                            for (int r = 0; r < 4; ++r)
-                                                if ((dm >> r) & 1u) { inc = first ? ar[r] : inc + ar[r]; first = false; }
-                                            k[c] = Arith<T>::mk(ps + inc, s * C + c);
-                                        }
-                                    }
-                                    if (C == 8) sort8(k);
-                                }
-                            }
-                            if (!act) {
-#pragma unroll
-                                for (int c = 0; c < 8; ++c) k[c] = KINF;
-                            }
-                            // selection (Algorithm 1): keep the L smallest keys
-                            const KT tau = (nc > L) ? warp_kth(k, C, L, lane) : KINF;
-                            uint32_t sm = 0;
-#pragma unroll
-                            for (int r = 0; r < 8; ++r)
-                                if (k[r] != KINF && k[r] <= tau) sm |= 1u << (Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
-                            const int base = warp_excl_scan(__popc(sm), lane);
-                            // commit: survivors of source s take slots in candidate order
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) {
-                                if (k[r] != KINF && k[r] <= tau) {
-                                    const int c = (int)(Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
-                                    const int t = base + __popc(sm & ((1u << c) - 1u));
-                                    penn[t] = Arith<T>::kpen(k[r]);
-                                    reinterpret_cast<uint4 *>(idxn)[t] = reinterpret_cast<const uint4 *>(idxc)[s];
-                                    reinterpret_cast<uint4 *>(bidxn)[t] = reinterpret_cast<const uint4 *>(bidxc)[s];
-                                    if (!dest) bidxn[t * 16 + j] = (uint8_t)t;
-                                    uint32_t word;
-                                    if (kind == OP_REP) {
-                                        word = ((flag != 0u) != (c == 1)) ? wmask : 0u;
-                                    } else {
-                                        const uint32_t dm = (kind == OP_R1) ? (uint32_t)c : (spc_tmask(c) ^ (flag ? 0u : 1u));
-                                        word = hd;
-#pragma unroll
-                                        for (int rr = 0; rr < 4; ++rr)
-                                            if ((dm >> rr) & 1u) word ^= 1u << ((mpos >> (4 * rr)) & 15u);
-                                    }
-                                    bout[t * ostride] = word;
-                                }
-                            }
-                        }
+                if (jc >= 5) {
+                    const int lw = jc - 5;
+                    const int total = La << lw;
+                    for (int t = tid; t < total; t += nthr) {
+                        const int p = t >> lw, w = t & (bwc - 1);
+                        const uint32_t l = blb[(int)bidxc[p * 16 + jc] * bwc + w];
+                        const uint32_t r = br[p * bwn + w];
+                        uint32_t *o2 = out + p * ostride;
+                        o2[w] = l ^ r;
+                        o2[w + bwc] = r;
                     }
                 } else {
-                    // ------- large leaf: the group, a warp per source path -------
-                    const int TS = 32;
-                    const int K = nv >> 5;
-                    const int rounds = (La + W - 1) / W;
-                    for (int r = 0; r < rounds; ++r) {
-                        const int s = r * W + wig;
-                        const bool act = s < La;
-                        T *row = stj + (j == n ? 0 : ((int)idxc[(act ? s : 0) * 16 + j] << j));
-                        const PT ps = act ? penc[s] : (PT)0;
-                        if (kind == OP_R0 || kind == OP_REP) {
-                            PT v0, v1;
-                            team_sums<T>(row, K, TS, lane, act, kind == OP_REP, v0, v1);
-                            if (act && lane == 0) {
-                                if (kind == OP_R0) {
-                                    penc[s] = ps + v0;
-                                } else {
-                                    const bool one = !(v0 <= v1);
-                                    keys[s * 2 + 0] = Arith<T>::mk(ps + (one ? v1 : v0), s * 2 + 0);
-                                    keys[s * 2 + 1] = Arith<T>::mk(ps + (one ? v0 : v1), s * 2 + 1);
-                                    cinfo[s] = make_uint4(0u, 0u, 0u, one ? 1u : 0u);
-                                }
-                            }
-                        } else {
-                            uint32_t hd = 0;
-                            if (K == 1) hd = __ballot_sync(FULL, act && (Arith<T>::val(row[lane]) < 0));
-                            uint64_t mk[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-                            if (kind == OP_R1) {
-                                team_lrb<T, 2>(row, K, TS, lane, act, mk);
-                                if (act && lane == 0) {
-                                    const PT a1 = Arith<T>::unabs((uint32_t)(mk[0] >> 32));
-                                    const PT a2 = Arith<T>::unabs((uint32_t)(mk[1] >> 32));
-                                    keys[s * 4 + 0] = Arith<T>::mk(ps, s * 4 + 0);
-                                    keys[s * 4 + 1] = Arith<T>::mk(ps + a1, s * 4 + 1);
-                                    keys[s * 4 + 2] = Arith<T>::mk(ps + a2, s * 4 + 2);
-                                    keys[s * 4 + 3] = Arith<T>::mk(ps + (a1 + a2), s * 4 + 3);
-                                    cinfo[s] = make_uint4((uint32_t)mk[0] | ((uint32_t)mk[1] << 16), 0u, hd, 0u);
-                                }
-                            } else {
-                                team_lrb<T, 4>(row, K, TS, lane, act, mk);
-                                int cnt = 0;
-                                if (act)
-                                    for (int kk = 0; kk < K; ++kk) cnt += Arith<T>::val(row[lane + kk * TS]) < 0 ? 1 : 0;
-                                for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(FULL, cnt, off);
-                                if (act && lane == 0) {
-                                    const uint32_t q = (cnt & 1) ? 0u : 1u;
-                                    PT ar[4];
-#pragma unroll
-                                    for (int rr = 0; rr < 4; ++rr) ar[rr] = Arith<T>::unabs((uint32_t)(mk[rr] >> 32));
-                                    for (int c = 0; c < C; ++c) {
-                                        const uint32_t dm = spc_tmask(c) ^ (q ? 0u : 1u);
-                                        PT inc = (PT)0;
-                                        bool first = true;
-#pragma unroll
-                                        for (int rr = 0; rr < 4; ++rr)
-                                            if ((dm >> rr) & 1u) { inc = first ? ar[rr] : inc + ar[rr]; first = false; }
-                                        keys[s * C + c] = Arith<T>::mk(ps + inc, s * C + c);
-                                    }
-                                    cinfo[s] = make_uint4((uint32_t)mk[0] | ((uint32_t)mk[1] << 16),
-                                                          (uint32_t)mk[2] | ((uint32_t)mk[3] << 16), hd, q);
-                                }
-                            }
-                        }
-                    }
-                    if (kind == OP_R0) {
-                        const int bw = beta_words(j);
-                        for (int t = gtid; t < La * bw; t += GT) {
-                            const int p = t / bw, w = t - p * bw;
-                            bout[p * ostride + w] = 0u;
-                        }
-                        if (!dest)
-                            for (int t = gtid; t < La; t += GT) bidxc[t * 16 + j] = (uint8_t)t;
-                    } else {
-                        gsync<W>(gidx);
-                        // selection by warp 0 (Algorithm 1)
-                        if (wig == 0) {
-                            const int s = lane;
-                            const bool act = s < La;
-                            KT k[8];
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) k[c] = (act && c < C) ? keys[s * C + c] : KINF;
-                            if (C == 8) sort8(k);
-                            const KT tau = (nc > L) ? warp_kth(k, C, L, lane) : KINF;
-                            uint32_t sm = 0;
-#pragma unroll
-                            for (int r = 0; r < 8; ++r)
-                                if (k[r] != KINF && k[r] <= tau) sm |= 1u << (Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
-                            const int base = warp_excl_scan(__popc(sm), lane);
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) {
-                                if (k[r] != KINF && k[r] <= tau) {
-                                    const int c = (int)(Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
-                                    const int t = base + __popc(sm & ((1u << c) - 1u));
-                                    survk[t] = k[r];
-                                    penn[t] = Arith<T>::kpen(k[r]);
-                                    reinterpret_cast<uint4 *>(idxn)[t] = reinterpret_cast<const uint4 *>(idxc)[s];
-                                    reinterpret_cast<uint4 *>(bidxn)[t] = reinterpret_cast<const uint4 *>(bidxc)[s];
-                                    if (!dest) bidxn[t * 16 + j] = (uint8_t)t;
-                                }
-                            }
-                        }
-                        gsync<W>(gidx);
-                        const int nn = nc < L ? nc : L;
-                        // candidate beta of every new slot (the group)
-                        const int bw = beta_words(j);
-                        if (kind == OP_REP) {
-                            for (int t = gtid; t < nn * bw; t += GT) {
-                                const int p = t / bw, w = t - p * bw;
-                                const uint32_t ci = Arith<T>::kidx(survk[p]);
-                                const int s = (int)(ci >> lc), c = (int)(ci & (uint32_t)(C - 1));
-                                bout[p * ostride + w] = ((cinfo[s].w != 0u) != (c == 1)) ? wmask : 0u;
-                            }
-                        } else {
-                            for (int q2 = wig; q2 < nn * bw; q2 += W) {
-                                const int p = q2 / bw, w = q2 - p * bw;
-                                const uint32_t ci = Arith<T>::kidx(survk[p]);
-                                const int s = (int)(ci >> lc), c = (int)(ci & (uint32_t)(C - 1));
-                                const T *row = stj + (j == n ? 0 : ((int)idxc[s * 16 + j] << j));
-                                const uint32_t bal = __ballot_sync(FULL, Arith<T>::val(row[(w << 5) + lane]) < 0);
-                                if (lane == 0) {
-                                    const uint4 ci4 = cinfo[s];
-                                    const uint32_t dm = (kind == OP_R1) ? (uint32_t)c : (spc_tmask(c) ^ (ci4.w ? 0u : 1u));
-                                    const uint32_t m[4] = {ci4.x & 0xFFFFu, ci4.x >> 16, ci4.y & 0xFFFFu, ci4.y >> 16};
-                                    uint32_t word = bal;
-#pragma unroll
-                                    for (int rr = 0; rr < 4; ++rr)
-                                        if (((dm >> rr) & 1u) && (int)(m[rr] >> 5) == w) word ^= 1u << (m[rr] & 31u);
-                                    bout[p * ostride + w] = word;
-                                }
-                            }
-                        }
+                    const int h = 1 << jc;
+                    const uint32_t m = (1u << h) - 1u;
+                    for (int t = tid; t < La; t += nthr) {
+                        const uint32_t l = blb[(int)bidxc[t * 16 + jc]];
+                        const uint32_t r = br[t * bwn];
+                        out[t * ostride] = ((l ^ r) & m) | ((r & m) << h);
                     }
                 }
-                if (kind != OP_R0) {
-                    La = nc < L ? nc : L;
-                    cur = nxt;
-                }
+                if (!dest)
+                    for (int t = tid; t < La; t += nthr) bidxc[t * 16 + j] = (uint8_t)t;
             }
-            if (op_sync(op)) gsync<W>(gidx);
-            else if (wig == 0) __syncwarp();
-            op = opn;
-        }
-        gsync<W>(gidx);
-
-        // ---------------- final pick (Sec. II-B) ----------------
-        PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
-        uint32_t *synb = reinterpret_cast<uint32_t *>(S + lay.cinfo);
-        if (cv.crc_len > 0) {
-            const int nbytes = N >> 3;
-            for (int p = wig; p < La; p += W) {
-                const uint8_t *xb = reinterpret_cast<const uint8_t *>(br + p * bwn);
-                uint32_t acc = 0;
-                for (int b = lane; b < nbytes; b += 32) acc ^= __ldg(cv.syn + ((b << 8) | xb[b]));
-                for (int off = 16; off >= 1; off >>= 1) acc ^= __shfl_xor_sync(FULL, acc, off);
-                if (lane == 0) synb[p] = acc;
+        } else if (kind == OP_SUB) {
+            // ---------------- a small subtree in registers (warp 0) ----------------
+            if (wig == 0) {
+                if (j == 4) run_sub<T, 4>(cv, S, Gs, op, La, cur, lane);
+                else run_sub<T, 3>(cv, S, Gs, op, La, cur, lane);
+            }
+            const int lm = op_sub_logmult(op);
+            La = (lm >= 6 || (La << lm) > L) ? L : (La << lm);
+            if (op_sub_fork(op)) cur ^= 1;
+        } else {
+            // ---------------- a leaf of more than 16 bits (warp 0) ----------------
+            if (wig == 0) big_leaf<T>(cv, S, Gs, kind, j, dest, La, cur, lane);
+            if (kind != OP_R0) {
+                const int C = kind == OP_R1 ? 4 : (kind == OP_REP ? 2 : (L == 2 ? 2 : 8));
+                La = La * C < L ? La * C : L;
+                cur ^= 1;
             }
         }
-        gsync<W>(gidx);
-        if (wig == 0) {
-            unsigned long long key = ~0ull;
-            if (lane < La) {
-                const bool okp = cv.crc_len == 0 || synb[lane] == 0u;
-                key = ((unsigned long long)(okp ? 0u : 1u) << 63) |
-                      ((unsigned long long)Arith<T>::pbits(penc[lane]) << 8) | (unsigned long long)lane;
-            }
-            for (int off = 16; off >= 1; off >>= 1) {
-                const unsigned long long o = __shfl_xor_sync(FULL, key, off);
-                key = o < key ? o : key;
-            }
-            const int win = (int)(key & 0xFFu);
-            const uint32_t okw = (uint32_t)(key >> 63) ^ 1u;
-            // u = x G_N for the winner (natural-order butterflies)
-            const uint32_t *xw = br + win * bwn;
-            const int R = bwn > 32 ? bwn >> 5 : 1;
-            uint32_t U[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int w = lane + 32 * r;
-                U[r] = (r < R && w < bwn) ? xw[w] : 0u;
-            }
-            const uint32_t M[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-#pragma unroll
-                for (int e = 0; e < 5; ++e) {
-                    const int hb = 1 << e;
-                    if (hb < N) U[r] ^= (U[r] >> hb) & M[e];
-                }
-            }
-            for (int d = 1; d < bwn; d <<= 1) {
-                if (d >= 32) {
-                    const int dr = d >> 5;
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        if (r < R && !(r & dr) && r + dr < 4) U[r] ^= U[r + dr];
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const uint32_t v = __shfl_down_sync(FULL, U[r], d);
-                        if (!(lane & d)) U[r] ^= v;
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int w = lane + 32 * r;
-                if (r < R && w < bwn) ubuf[w] = U[r];
-            }
-            if (lane == 0) {
-                *pm_out = Arith<T>::to_out(penc[win]);
-                if (ok_out) *ok_out = (uint8_t)okw;
-                if (slot_out) *slot_out = win;
-            }
-        }
-        gsync<W>(gidx);
-        for (int b = gtid; b < cv.kb; b += GT) {
-            uint32_t byte = 0;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int pos = 8 * b + t;
-                if (pos < cv.k) {
-                    const uint32_t u = __ldg(cv.info + pos);
-                    byte |= ((ubuf[u >> 5] >> (u & 31u)) & 1u) << t;
-                }
-            }
-            bits_row[b] = (uint8_t)byte;
-        }
-        gsync<W>(gidx);
+        if (op_sync(op)) gsync<W>(gidx);
+        else if (wig == 0) __syncwarp();
+        op = opn;
     }
+    gsync<W>(gidx);
+
+    // ---------------- final pick (Sec. II-B) ----------------
+    PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
+    uint32_t *synb = reinterpret_cast<uint32_t *>(S + lay.surv);
+    if (cv.crc_len > 0) {
+        const int nbytes = N >> 3;
+        for (int p = wig; p < La; p += W) {
+            const uint8_t *xb = reinterpret_cast<const uint8_t *>(br + p * bwn);
+            uint32_t acc = 0;
+            for (int b = lane; b < nbytes; b += 32) acc ^= __ldg(cv.syn + ((b << 8) | xb[b]));
+            for (int off = 16; off >= 1; off >>= 1) acc ^= __shfl_xor_sync(FULL, acc, off);
+            if (lane == 0) synb[p] = acc;
+        }
+    }
+    gsync<W>(gidx);
+    if (wig == 0) {
+        unsigned long long key = ~0ull;
+        if (lane < La) {
+            const bool okp = cv.crc_len == 0 || synb[lane] == 0u;
+            key = ((unsigned long long)(okp ? 0u : 1u) << 63) |
+                  ((unsigned long long)Arith<T>::pbits(penc[lane]) << 8) | (unsigned long long)lane;
+        }
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o2 = __shfl_xor_sync(FULL, key, off);
+            key = o2 < key ? o2 : key;
+        }
+        const int win = (int)(key & 0xFFu);
+        const uint32_t okw = (uint32_t)(key >> 63) ^ 1u;
+        // u = x G_N for the winner (natural-order butterflies)
+        const uint32_t *xw = br + win * bwn;
+        const int R = bwn > 32 ? bwn >> 5 : 1;
+        uint32_t U[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int w = lane + 32 * r;
+            U[r] = (r < R && w < bwn) ? xw[w] : 0u;
+        }
+        const uint32_t M[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int hb = 1 << e;
+                if (hb < N) U[r] ^= (U[r] >> hb) & M[e];
+            }
+        }
+        for (int d = 1; d < bwn; d <<= 1) {
+            if (d >= 32) {
+                const int dr = d >> 5;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r < R && !(r & dr) && r + dr < 4) U[r] ^= U[r + dr];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t v = __shfl_down_sync(FULL, U[r], d);
+                    if (!(lane & d)) U[r] ^= v;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int w = lane + 32 * r;
+            if (r < R && w < bwn) ubuf[w] = U[r];
+        }
+        if (lane == 0) {
+            *pm_out = Arith<T>::to_out(penc[win]);
+            if (ok_out) *ok_out = (uint8_t)okw;
+            if (slot_out) *slot_out = win;
+        }
+    }
+    gsync<W>(gidx);
+    for (int b = gtid; b < cv.kb; b += GT) {
+        uint32_t byte = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int pos = 8 * b + t;
+            if (pos < cv.k) {
+                const uint32_t u = __ldg(cv.info + pos);
+                byte |= ((ubuf[u >> 5] >> (u & 31u)) & 1u) << t;
+            }
+        }
+        bits_row[b] = (uint8_t)byte;
+    }
+    gsync<W>(gidx);
 }
 
 // Plain form: one code, frames f = group, group + n_groups, ...
