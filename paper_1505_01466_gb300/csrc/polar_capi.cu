@@ -516,7 +516,8 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    static const uint32_t budgets[] = {0xffffffffu, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u};
+    static const uint32_t budgets[] = {0xffffffffu, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u,
+                                       14000u, 10000u, 7000u};
     float best_ms = 1e30f;
     LaunchShape best;
     uint32_t best_w = 0, best_b = 0;
@@ -815,7 +816,8 @@ int polar_batch_autotune(polar_batch_t *b, const void *llr_dev, uint8_t *bits_de
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    static const uint32_t budgets[] = {0u, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u};
+    static const uint32_t budgets[] = {0u, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u, 14000u, 10000u,
+                                       7000u};
     float best = 1e30f;
     int bw = 0;
     uint32_t bb = 0;

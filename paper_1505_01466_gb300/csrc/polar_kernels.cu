@@ -324,7 +324,8 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
     int C, lc;
     const int s = lane;
     const P ps = st.pen;
-    if (type == OP_REP) {
+    // a leaf of one bit is Rate-0 or Rate-1; SPC needs at least four bits
+    if (J >= 1 && type == OP_REP) {
         // Repetition (Sec. III-E): the ML word listed first.
         C = 2;
         lc = 1;
@@ -356,16 +357,18 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
                 ce(lk[2], lk[3]); ce(lk[0], lk[2]); ce(lk[1], lk[3]); ce(lk[1], lk[2]);
             }
         } else {
-            const int R = (type == OP_R1) ? 2 : 4;
+            // R passes of a plain minimum over the keys not taken yet
+            const int R = (J < 2 || type == OP_R1) ? 2 : 4;
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                const unsigned long long prev = r > 0 ? lk[r - 1] : 0ull;
+                unsigned long long best = ~0ull;
 #pragma unroll
-            for (int i = 0; i < nv; ++i) {
-                unsigned long long v = ((unsigned long long)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
-                if (v < lk[R - 1]) {
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        if (r < R && v < lk[r]) { const unsigned long long t2 = lk[r]; lk[r] = v; v = t2; }
-                    }
+                for (int i = 0; i < nv; ++i) {
+                    const unsigned long long v = ((unsigned long long)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
+                    if ((r == 0 || v > prev) && v < best) best = v;
                 }
+                if (r == 0) lk[0] = best; else if (r == 1) lk[1] = best; else if (r == 2) lk[2] = best; else lk[3] = best;
             }
         }
         P ar[4];
@@ -376,7 +379,7 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
             m[r] = (uint32_t)(lk[r] & 15u);
         }
         mpos = m[0] | (m[1] << 4) | (m[2] << 8) | (m[3] << 12);
-        if (type == OP_R1) {
+        if (J < 2 || type == OP_R1) {
             // Rate-1 (Sec. III-C): HD, HD^m1, HD^m2, HD^m1^m2.
             C = nv == 1 ? 2 : 4;
             lc = nv == 1 ? 1 : 2;
@@ -427,10 +430,10 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
     st.orig = __shfl_sync(FULL, st.orig, src);
     if (act2) st.pen = Arith<T>::kpen(kt);
     uint32_t word;
-    if (type == OP_REP) {
+    if (J >= 1 && type == OP_REP) {
         word = ((fl_s != 0u) != (c == 1)) ? wmask : 0u;
     } else {
-        const uint32_t dm = (type == OP_R1) ? (uint32_t)c : (spc_tmask(c) ^ (fl_s ? 0u : 1u));
+        const uint32_t dm = (J < 2 || type == OP_R1) ? (uint32_t)c : (spc_tmask(c) ^ (fl_s ? 0u : 1u));
         word = hd_s;
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr)
