@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--pool-frames", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-rate", type=float, default=2e5, help="offered frames per second")
+    ap.add_argument("--skip-fer", action="store_true")
+    ap.add_argument("--fer-frames", type=int, default=1 << 17, help="frames per Eb/N0 point of the FER sweep")
+    ap.add_argument("--fer-points", default="3.5,4.0,4.5", help="Eb/N0 points (dB) of the FER sweep")
     return ap.parse_args()
 
 
@@ -66,10 +69,30 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(torch, x: float, dev) -> float:
+    """Max of a per-rank scalar over all ranks (identity on one rank)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank decodes its own frames (replicas; no data-path collective)."""
+    return 1000 + rank
+
+
+def job_gbps(k: int, frames_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job information throughput: payload bits of all ranks / slowest rank's time."""
+    return k * frames_per_rank * world / (ms_per_step * 1e-3) / 1e9
+
+
 def make_code_inputs(seed: int, n_unique: int):
     from paper_1505_01466_gb300 import inputs as I
     frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
-    fr = I.make_frames(frozen, CRC_LEN, I.CRC32_POLY, EBN0_DB, n_unique, seed=seed)
+    fr = I.make_frames_chunked(frozen, CRC_LEN, I.CRC32_POLY, EBN0_DB, n_unique, seed=seed)
     return I, frozen, fr
 
 
@@ -187,6 +210,97 @@ def config_dict(args, impl):
         "l2": "inputs larger than L2 (no flush needed)",
         "parallelism": "frames sharded across ranks (replicas)",
     }
+
+
+def clopper_pearson(x: int, n: int, conf: float = 0.99):
+    """Exact binomial confidence interval of x errors in n frames."""
+    from scipy.stats import beta
+    a = 1.0 - conf
+    lo = 0.0 if x == 0 else float(beta.ppf(a / 2, x, n - x + 1))
+    hi = 1.0 if x == n else float(beta.ppf(1 - a / 2, x + 1, n - x))
+    return lo, hi
+
+
+def paired_fer_test(err_a, err_b, conf: float = 0.99):
+    """Two decoders on the same frames: FERs with Clopper-Pearson intervals and
+    the exact McNemar test on the frames where exactly one of them failed."""
+    import numpy as np
+    from scipy.stats import binomtest
+    err_a, err_b = np.asarray(err_a, bool), np.asarray(err_b, bool)
+    n = err_a.size
+    xa, xb = int(err_a.sum()), int(err_b.sum())
+    only_a, only_b = int((err_a & ~err_b).sum()), int((err_b & ~err_a).sum())
+    p = 1.0 if only_a + only_b == 0 else float(binomtest(only_a, only_a + only_b, 0.5).pvalue)
+    ca, cb = clopper_pearson(xa, n, conf), clopper_pearson(xb, n, conf)
+    return {"frames": n, "errors": [xa, xb], "fer": [xa / n, xb / n], "ci": [ca, cb],
+            "only_first_failed": only_a, "only_second_failed": only_b, "mcnemar_p": p,
+            "match": bool(p >= 1.0 - conf and ca[0] <= cb[1] and cb[0] <= ca[1]),
+            "underpowered": min(xa, xb) < 100}
+
+
+def measure_fer(args, torch, dev, stream):
+    """FER of the fast decoder (Dec-SPC-4) against plain SC-list decoding
+    (length-one leaves, the same list size) on the same frames, and the
+    adaptive decoder (Fast-SSC, then the list decoder on CRC failures) with
+    its throughput, at each Eb/N0 point; float32 and int8 LLRs."""
+    import numpy as np
+    from paper_1505_01466_gb300 import inputs as I
+    from paper_1505_01466_gb300.polar import PolarCode, adaptive_decode
+    frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
+    k = K - CRC_LEN
+    fast = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L, mode=0)
+    scl = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L, mode=2)
+    sc1 = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 1, mode=0)
+    tuned = set()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    points = []
+    for ebn0 in [float(x) for x in args.fer_points.split(",") if x]:
+        fr = I.make_frames_chunked(frozen, CRC_LEN, I.CRC32_POLY, ebn0, args.fer_frames, seed=int(ebn0 * 1000))
+        for dt in ("f32", "i8"):
+            llr = torch.from_numpy(fr.llr_i8 if dt == "i8" else fr.llr_f32).to(dev)
+            if dt not in tuned:
+                for c in (fast, scl, sc1):
+                    c.autotune(llr[:16384], stream=stream)
+                tuned.add(dt)
+            errs, ms = {}, {}
+            for name, fn in (("fast", lambda: fast.decode(llr, stream=stream)),
+                             ("scl", lambda: scl.decode(llr, stream=stream)),
+                             ("adaptive", lambda: adaptive_decode(sc1, fast, llr, stream=stream))):
+                fn()                                     # warm-up
+                out, ms[name] = timed(fn)
+                got = I.unpack_bits_lsb(out[0].cpu().numpy(), k)
+                errs[name] = (got != fr.payload).any(axis=1)
+                if name == "adaptive":
+                    relisted = int(out[4].item())
+            t = paired_fer_test(errs["fast"], errs["scl"])
+            points.append({
+                "ebn0_db": ebn0, "dtype": dt, "frames": args.fer_frames,
+                "fer_fast": t["fer"][0], "ci99_fast": t["ci"][0], "fer_scl": t["fer"][1], "ci99_scl": t["ci"][1],
+                "errors_fast": t["errors"][0], "errors_scl": t["errors"][1],
+                "only_fast_failed": t["only_first_failed"], "only_scl_failed": t["only_second_failed"],
+                "mcnemar_p": t["mcnemar_p"], "fer_match": t["match"], "underpowered": t["underpowered"],
+                "fer_adaptive": float(errs["adaptive"].mean()),
+                "adaptive_relisted_frac": relisted / args.fer_frames,
+                "gbps_fast": k * args.fer_frames / ms["fast"] / 1e6,
+                "gbps_scl": k * args.fer_frames / ms["scl"] / 1e6,
+                "gbps_adaptive": k * args.fer_frames / ms["adaptive"] / 1e6,
+            })
+            del llr
+    for c in (fast, scl, sc1):
+        c.close()
+    return {"code": f"({N},{K}) CRC-32 L={L}, GA {DESIGN_DB} dB", "fast": "Dec-SPC-4",
+            "plain": "SC-list with length-one leaves (bit-exact with the oracle's SC-list)",
+            "adaptive": f"Fast-SSC (L=1) then L={L} on CRC failures", "test": "exact McNemar + Clopper-Pearson 99%",
+            "points": points}
 
 
 def measure_batched(args, torch, dev, stream, barrier):
@@ -353,7 +467,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1505_01466_gb300.polar import PolarCode
 
-    I, frozen, fr = make_code_inputs(seed=1000 + rank, n_unique=min(UNIQUE, args.frames))
+    I, frozen, fr = make_code_inputs(seed=rank_seed(rank), n_unique=min(UNIQUE, args.frames))
     llr_np = fr.llr_i8 if args.dtype == "i8" else fr.llr_f32
     reps = (args.frames + llr_np.shape[0] - 1) // llr_np.shape[0]
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -393,13 +507,9 @@ def run_ours(args):
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = reduce_max(torch, sum(step_ms), dev)
     ms_per_step = tot_ms / args.steps
-    value = k * args.frames * world / (ms_per_step * 1e-3) / 1e9
+    value = job_gbps(k, args.frames, world, ms_per_step)
 
     # sanity: a noisy 4 dB workload must decode with a low frame-error rate
     with torch.cuda.stream(stream):
@@ -432,12 +542,8 @@ def run_ours(args):
             hok.copy_(ok, non_blocking=True)
         e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = k * args.frames * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = reduce_max(torch, e0.elapsed_time(e1) / e2e_steps, dev)
+    e2e_val = job_gbps(k, args.frames, world, e2e_ms)
     h2d = llr.numel() * llr.element_size()
     d2h = bits.numel() + pm.numel() * 4 + ok.numel()
 
@@ -478,15 +584,19 @@ def run_ours(args):
                 code.decode_into(ollr, bits, pm, ok, None, stream=stream)
             b.record(stream)
         barrier()
-        oms = a.elapsed_time(b) / args.steps
+        oms = reduce_max(torch, a.elapsed_time(b) / args.steps, dev)
         oinfo = code.info()
         di = 1 if odt == "i8" else 0
-        other = {"dtype": odt, "value": k * args.frames * world / (oms * 1e-3) / 1e9, "unit": UNIT,
+        other = {"dtype": odt, "value": job_gbps(k, args.frames, world, oms), "unit": UNIT,
                  "ms_per_step": oms, "launch": {"warps_per_frame": oinfo["warps_per_frame"][di],
                                                 "frames_per_cta": oinfo["frames_per_cta"][di],
                                                 "smem_per_frame": oinfo["smem_per_frame"][di],
                                                 "spill_mask": oinfo["spill_mask"][di]}}
         del ollr
+
+    fer_sweep = None
+    if rank == 0 and not args.skip_fer:
+        fer_sweep = measure_fer(args, torch, dev, stream)
 
     batched = None
     if not args.skip_batched:
@@ -516,6 +626,7 @@ def run_ours(args):
             "other_dtype": other,
             "batched": batched,
             "serving": serving,
+            "fer": fer_sweep,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

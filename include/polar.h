@@ -163,6 +163,22 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                           uint32_t smem_budget);
 
+/* Adaptive decoding (Sec. V): every frame is first decoded with `fast`
+ * (normally the same code with L = 1, i.e. Fast-SSC decoding); the frames
+ * whose CRC fails are then decoded again with `list` (the target L_max) and
+ * their outputs replaced. Both codes must be the same code (N, K, frozen set,
+ * CRC) created on the current device, and the code must have a CRC. Outputs
+ * as polar_list_decode; crc_ok_dev is required (it drives the switch).
+ * n_relisted_dev (device, one uint32, may be NULL) receives the number of
+ * frames handed to the list decoder. Everything is enqueued on `stream`;
+ * the second decode reads the failure count from device memory, so no host
+ * synchronisation happens. Errors: POLAR_EINVAL (different codes, no CRC,
+ * NULL pointers), POLAR_ENOMEM, POLAR_ECUDA. */
+POLAR_API int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, const void *llr_dev,
+                                    int llr_dtype, uint32_t n_frames, uint8_t *info_bits_dev, float *path_metric_dev,
+                                    uint8_t *crc_ok_dev, int32_t *winner_slot_dev, uint32_t *n_relisted_dev,
+                                    polar_stream_t stream);
+
 /* Autotune the launch shape of one dtype on real frames: times every
  * distinct (warps per frame, shared-memory budget) shape on n_frames frames of
  * llr_dev (device, [n_frames][N]) on `stream`, installs the fastest and

@@ -95,6 +95,21 @@ def decode(frozen, L, llr, crc_len=0, crc_poly=0, mode=SPC4, n_threads=1):
     return bits, pm, ok, slot
 
 
+def adaptive_decode(frozen, L_max, llr, crc_len, crc_poly, mode=SPC4, n_threads=1):
+    """Adaptive decoding of Sec. V: Fast-SSC (the list decoder with one path)
+    on every frame, then the list decoder with ``L_max`` on the frames whose
+    CRC failed. Returns decode()'s four arrays plus the re-decoded count."""
+    llr = np.asarray(llr)
+    N = np.asarray(frozen).size
+    flat = llr.reshape(-1, N)
+    bits, pm, ok, slot = decode(frozen, 1, flat, crc_len, crc_poly, mode, n_threads)
+    bad = np.flatnonzero(ok == 0)
+    if bad.size:
+        b2, p2, o2, s2 = decode(frozen, L_max, flat[bad], crc_len, crc_poly, mode, n_threads)
+        bits[bad], pm[bad], ok[bad], slot[bad] = b2, p2, o2, s2
+    return bits, pm, ok, slot, int(bad.size)
+
+
 def decode_list(frozen, L, llr_frame, mode=SPC4):
     """Final list of one frame: (codewords uint8 [n, N], penalties float32 [n])."""
     lib = _load()

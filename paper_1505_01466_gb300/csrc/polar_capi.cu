@@ -335,7 +335,8 @@ CodeView make_view(const polar_code *code, const LaunchShape &sh) {
 
 // Launch a decode of n_frames with an explicit shape.
 int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const void *llr, uint32_t n_frames,
-                 uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot, cudaStream_t st) {
+                 uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot, cudaStream_t st,
+                 const uint32_t *frame_idx = nullptr, const uint32_t *frame_cnt = nullptr) {
     int occ = occupancy(dtype, sh);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
@@ -351,6 +352,8 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
     p.slot = slot;
     p.n_frames = n_frames;
     p.groups_per_cta = sh.groups_per_cta;
+    p.frame_idx = frame_idx;
+    p.frame_cnt = frame_cnt;
     void *scratch = nullptr;
     if (sh.lay.gbytes > 0) {
         const size_t bytes = (size_t)grid * sh.groups_per_cta * sh.lay.gbytes;
@@ -498,6 +501,40 @@ int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dty
     if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
     return decode_shape(code, llr_dtype, code->shape[llr_dtype], llr_dev, n_frames, info_bits_dev, path_metric_dev,
                         crc_ok_dev, winner_slot_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, const void *llr_dev, int llr_dtype,
+                          uint32_t n_frames, uint8_t *info_bits_dev, float *path_metric_dev, uint8_t *crc_ok_dev,
+                          int32_t *winner_slot_dev, uint32_t *n_relisted_dev, polar_stream_t stream) {
+    if (!fast || !list || fast->host_only || list->host_only) return POLAR_EINVAL;
+    if (fast->N != list->N || fast->K != list->K || fast->crc_len != list->crc_len ||
+        fast->crc_poly != list->crc_poly || fast->frozen != list->frozen || fast->device != list->device)
+        return POLAR_EINVAL;
+    if (fast->crc_len == 0) return POLAR_EINVAL;   // the switch is driven by the CRC
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!llr_dev || !path_metric_dev || !crc_ok_dev || (!info_bits_dev && fast->k > 0)) return POLAR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = decode_shape(fast, llr_dtype, fast->shape[llr_dtype], llr_dev, n_frames, info_bits_dev,
+                          path_metric_dev, crc_ok_dev, winner_slot_dev, st);
+    if (rc != POLAR_OK) return rc;
+    void *tmp = nullptr;
+    if (cudaMallocAsync(&tmp, sizeof(uint32_t) * ((size_t)n_frames + 1), st) != cudaSuccess) return POLAR_ENOMEM;
+    uint32_t *cnt = (uint32_t *)tmp;
+    uint32_t *idx = cnt + 1;
+    if (launch_crc_failures(crc_ok_dev, n_frames, idx, cnt, st) != cudaSuccess) {
+        cudaFreeAsync(tmp, st);
+        return POLAR_ECUDA;
+    }
+    if (n_relisted_dev && cudaMemcpyAsync(n_relisted_dev, cnt, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) !=
+                              cudaSuccess) {
+        cudaFreeAsync(tmp, st);
+        return POLAR_ECUDA;
+    }
+    rc = decode_shape(list, llr_dtype, list->shape[llr_dtype], llr_dev, n_frames, info_bits_dev, path_metric_dev,
+                      crc_ok_dev, winner_slot_dev, st, idx, cnt);
+    cudaFreeAsync(tmp, st);
+    return rc;
 }
 
 int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,

@@ -101,6 +101,8 @@ struct Params {                    // plain form: one code
     uint32_t n_frames;
     uint8_t *scratch;              // global scratch (spilled stages), lay.gbytes per group
     int groups_per_cta;
+    const uint32_t *frame_idx;     // optional: decode only frames frame_idx[0 .. *frame_cnt)
+    const uint32_t *frame_cnt;
 };
 
 struct BatchItem {                 // one frame of a batched launch
@@ -141,6 +143,9 @@ cudaError_t launch_decode(int dtype, const LaunchShape &shape, const Params &p, 
                           cudaStream_t stream);
 // Resident CTAs per SM for a shape (0 if it cannot launch).
 int occupancy(int dtype, const LaunchShape &shape);
+// Indices of the frames whose CRC flag is 0 (order unspecified) and their count.
+cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n_frames, uint32_t *idx, uint32_t *cnt,
+                                cudaStream_t stream);
 // Batched form: 128-thread CTAs of `warps`-warp groups with `smem` bytes each.
 cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, cudaStream_t stream);
 int occupancy_batch(int dtype, int warps, uint32_t smem);

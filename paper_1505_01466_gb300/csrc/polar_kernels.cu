@@ -33,6 +33,8 @@
 // right in rank order; every new penalty is parent + increment. int8 LLRs
 // use saturated G and exact integer penalties.
 
+#include <algorithm>
+
 #include "polar_internal.h"
 
 namespace polar {
@@ -1150,10 +1152,29 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
     const int ngroups = gridDim.x * P.groups_per_cta;
     uint8_t *Gs = P.scratch ? P.scratch + (size_t)ggid * P.cv.lay.gbytes : nullptr;
     const size_t nbytes = (size_t)P.cv.N * sizeof(T);
-    for (uint32_t f = ggid; f < P.n_frames; f += ngroups) {
+    const uint32_t nf = P.frame_idx ? *P.frame_cnt : P.n_frames;
+    for (uint32_t i = ggid; i < nf; i += ngroups) {
+        const uint32_t f = P.frame_idx ? P.frame_idx[i] : i;
         decode_frame<T, W>(P.cv, S, Gs, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
                            P.bits + (size_t)f * P.cv.kb, P.pm + f, P.ok ? P.ok + f : nullptr,
                            P.slot ? P.slot + f : nullptr, gidx, gtid);
+    }
+}
+
+// Compaction for the adaptive decoder (Sec. V): indices of frames whose CRC
+// failed. One warp-aggregated atomic per warp; the order is unspecified.
+__global__ void crc_failures_kernel(const uint8_t *ok, uint32_t n, uint32_t *idx, uint32_t *cnt) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n;
+         base += gridDim.x * blockDim.x) {
+        const uint32_t f = base + lane;
+        const bool bad = f < n && ok[f] == 0;
+        const uint32_t m = __ballot_sync(FULL, bad);
+        if (!m) continue;
+        uint32_t off = 0;
+        if (lane == 0) off = atomicAdd(cnt, (uint32_t)__popc(m));
+        off = __shfl_sync(FULL, off, 0);
+        if (bad) idx[off + __popc(m & ((1u << lane) - 1u))] = f;
     }
 }
 
@@ -1230,6 +1251,14 @@ int occ_batch_one(uint32_t smem) {
 }
 
 }  // namespace
+
+cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n, uint32_t *idx, uint32_t *cnt, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess || n == 0) return e;
+    const int blocks = (int)std::min<uint32_t>((n + 255) / 256, 4096u);
+    crc_failures_kernel<<<blocks, 256, 0, st>>>(ok, n, idx, cnt);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, cudaStream_t st) {
     if (dtype == 0) {

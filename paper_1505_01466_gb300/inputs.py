@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import functools
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -259,6 +260,27 @@ def make_frames(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: f
     llr = 2.0 * y / (sig * sig)
     return Frames(payload=payload, codeword=x, llr_f32=llr.astype(np.float32),
                   llr_i8=quantize_i8(llr), sigma=sig)
+
+
+def make_frames_chunked(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: float,
+                        n_frames: int, seed: int, chunk: int = 8192, threads: int | None = None) -> Frames:
+    """make_frames over chunks of ``chunk`` frames generated on host threads.
+
+    Chunk c is ``make_frames(..., chunk, seed=(seed << 20) + c)``; the result is
+    their concatenation, so it does not depend on the thread count.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+    if n_frames == 0:
+        return make_frames(frozen_mask, crc_len, crc_poly, ebn0_db, 0, seed)
+    sizes = [min(chunk, n_frames - s) for s in range(0, n_frames, chunk)]
+    threads = threads or min(len(sizes), os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda c: make_frames(frozen_mask, crc_len, crc_poly, ebn0_db, sizes[c],
+                                                  seed=(seed << 20) + c), range(len(sizes))))
+    return Frames(payload=np.concatenate([p.payload for p in parts]),
+                  codeword=np.concatenate([p.codeword for p in parts]),
+                  llr_f32=np.concatenate([p.llr_f32 for p in parts]),
+                  llr_i8=np.concatenate([p.llr_i8 for p in parts]), sigma=parts[0].sigma)
 
 
 # --------------------------------------------------------------------------

@@ -28,7 +28,7 @@ EXPORTED = [
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
     "polar_server_create", "polar_server_destroy", "polar_server_submit", "polar_server_poll", "polar_server_wait",
-    "polar_server_pause", "polar_server_stats",
+    "polar_server_pause", "polar_server_stats", "polar_adaptive_decode",
 ]
 
 
@@ -47,6 +47,26 @@ class CodeInfo(ctypes.Structure):
         ("frames_per_cta", ctypes.c_uint32 * 2), ("smem_per_frame", ctypes.c_uint32 * 2),
         ("scratch_per_frame", ctypes.c_uint64 * 2), ("spill_mask", ctypes.c_uint32 * 2),
     ]
+
+
+def adaptive_decode(fast, list_code, llr, stream=None):
+    """Sec. V adaptive decoding: ``fast`` (L = 1) first, CRC failures again with
+    ``list_code``. Returns (bits, penalty, crc_ok, slot, n_relisted tensor)."""
+    import torch
+    dt = LLR_I8 if llr.dtype == torch.int8 else LLR_F32
+    F = llr.numel() // fast.N
+    dev = llr.device
+    bits = torch.empty((F, (fast.k + 7) // 8), dtype=torch.uint8, device=dev)
+    pm = torch.empty(F, dtype=torch.float32, device=dev)
+    ok = torch.empty(F, dtype=torch.uint8, device=dev)
+    slot = torch.empty(F, dtype=torch.int32, device=dev)
+    nrel = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(_lib().polar_adaptive_decode(fast.handle, list_code.handle, ctypes.c_void_p(llr.data_ptr()), dt, F,
+                                        ctypes.c_void_p(bits.data_ptr()), ctypes.c_void_p(pm.data_ptr()),
+                                        ctypes.c_void_p(ok.data_ptr()), ctypes.c_void_p(slot.data_ptr()),
+                                        ctypes.c_void_p(nrel.data_ptr()), _stream_handle(stream)),
+           "polar_adaptive_decode")
+    return bits, pm, ok, slot, nrel
 
 
 class BatchInfo(ctypes.Structure):
@@ -105,6 +125,7 @@ def _lib():
         lib.polar_server_wait.argtypes = [vp, u64, u32]
         lib.polar_server_pause.argtypes = [vp, i32]
         lib.polar_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats), i32]
+        lib.polar_adaptive_decode.argtypes = [vp, vp, vp, i32, u32, vp, vp, vp, vp, vp, vp]
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32

@@ -123,3 +123,17 @@ def test_code_info_and_op_count(polar):
     assert code.info()["spill_mask"][1] != 0
     with pytest.raises(polar.PolarError):
         code.set_launch(1, 3, 0)
+
+
+def test_fer_statistics_helpers():
+    import bench
+    lo, hi = bench.clopper_pearson(0, 100)
+    assert lo == 0.0 and hi == pytest.approx(1 - 0.005 ** (1 / 100))   # closed form at x = 0
+    lo, hi = bench.clopper_pearson(50, 100)
+    assert lo < 0.5 < hi and lo == pytest.approx(1 - hi)               # symmetric at x = n/2
+    a = np.zeros(1000, bool); a[:120] = True
+    b = a.copy(); b[0] = False; b[500] = True
+    t = bench.paired_fer_test(a, b)
+    assert t["errors"] == [120, 120] and t["only_first_failed"] == 1 and t["match"] and not t["underpowered"]
+    c = np.zeros(1000, bool); c[:10] = True
+    assert not bench.paired_fer_test(a, c)["match"]

@@ -133,3 +133,12 @@ def test_batch_zipf_mix_counts():
     assert counts.max() / counts.min() > 100          # uneven (Zipf s = 1.2)
     fc = I.frame_order(counts, seed=1)
     assert np.array_equal(np.bincount(fc, minlength=125), counts)
+
+
+def test_chunked_frames_are_the_concatenated_chunks():
+    fr = I.ga_frozen_mask(128, 70, 2.0, 62 / 128)
+    full = I.make_frames_chunked(fr, 8, I.CRC8_POLY, 2.0, 50, seed=3, chunk=16, threads=3)
+    one = I.make_frames_chunked(fr, 8, I.CRC8_POLY, 2.0, 50, seed=3, chunk=16, threads=1)
+    assert np.array_equal(full.llr_f32, one.llr_f32) and full.payload.shape == (50, 62)
+    c2 = I.make_frames(fr, 8, I.CRC8_POLY, 2.0, 16, seed=(3 << 20) + 2)
+    assert np.array_equal(full.llr_i8[32:48], c2.llr_i8) and np.array_equal(full.payload[32:48], c2.payload)

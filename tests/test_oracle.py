@@ -296,3 +296,22 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
     spec.loader.exec_module(mod)
     mod.build(force=True)
     assert not _pins_pass(mod), f"mutation '{name}' was not detected"
+
+
+def test_adaptive_decoder_properties(oracle_mod):
+    # Sec. V: Fast-SSC first, the list decoder only where the CRC failed.
+    fr = I.ga_frozen_mask(256, 128, 2.0, 120 / 256)
+    clean = I.make_frames(fr, 8, I.CRC8_POLY, 2.0, 16, seed=3, noiseless=True)
+    b, pm, ok, slot, n = oracle_mod.adaptive_decode(fr, 8, clean.llr_f32, 8, I.CRC8_POLY)
+    assert n == 0 and ok.all() and np.array_equal(I.unpack_bits_lsb(b, 120), clean.payload)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 1.5, 400, seed=4)
+    b, pm, ok, slot, n = oracle_mod.adaptive_decode(fr, 8, f.llr_f32, 8, I.CRC8_POLY)
+    _, _, ok1, _ = oracle_mod.decode(fr, 1, f.llr_f32, 8, I.CRC8_POLY)
+    _, _, ok8, _ = oracle_mod.decode(fr, 8, f.llr_f32, 8, I.CRC8_POLY)
+    assert 0 < n == int((ok1 == 0).sum()) < 400          # both branches taken
+    assert np.array_equal(ok, ok1 | ok8)                  # the switch only ever helps
+    # a frame whose payload the list decoder gets right is right after the switch too
+    right8 = (I.unpack_bits_lsb(oracle_mod.decode(fr, 8, f.llr_f32, 8, I.CRC8_POLY)[0], 120) ==
+              f.payload).all(axis=1)
+    right = (I.unpack_bits_lsb(b, 120) == f.payload).all(axis=1)
+    assert (right | ~right8 | (ok1 == 1)).all()
