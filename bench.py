@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--pool-frames", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-rate", type=float, default=2e5, help="offered frames per second")
+    ap.add_argument("--launch", default=None,
+                    help="WARPS,SMEM_BUDGET[,CTA_THREADS]: fixed launch shape instead of autotuning")
     ap.add_argument("--skip-fer", action="store_true")
     ap.add_argument("--fer-frames", type=int, default=1 << 17, help="frames per Eb/N0 point of the FER sweep")
     ap.add_argument("--fer-points", default="3.5,4.0,4.5", help="Eb/N0 points (dB) of the FER sweep")
@@ -476,7 +478,12 @@ def run_ours(args):
     del uniq
     code = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L)
     # untimed: pick the launch shape (warps per frame, shared-memory budget) by measurement
-    tuned = code.autotune(llr[: min(args.frames, 16384)])
+    di = 1 if args.dtype == "i8" else 0
+    if args.launch:
+        tuned = tuple(int(v) for v in args.launch.split(","))
+        code.set_launch(di, *tuned)
+    else:
+        tuned = code.autotune(llr[: min(args.frames, 16384)])
     k = K - CRC_LEN
     kb = (k + 7) // 8
     bits = torch.empty((args.frames, kb), dtype=torch.uint8, device=dev)
@@ -548,10 +555,11 @@ def run_ours(args):
     d2h = bits.numel() + pm.numel() * 4 + ok.numel()
 
     info = code.info()
-    di = 1 if args.dtype == "i8" else 0
     launch_info = {"warps_per_frame": info["warps_per_frame"][di], "frames_per_cta": info["frames_per_cta"][di],
                    "smem_per_frame": info["smem_per_frame"][di], "scratch_per_frame": info["scratch_per_frame"][di],
-                   "spill_mask": info["spill_mask"][di], "autotuned": {"warps": tuned[0], "smem_budget": tuned[1]}}
+                   "spill_mask": info["spill_mask"][di],
+                   "autotuned": {"warps": tuned[0], "smem_budget": tuned[1],
+                                 "cta_threads": tuned[2] if len(tuned) > 2 else 0}}
 
     # ---- roofline: counted min/add/compare/select/xor ops vs the scalar ALU peak ----
     pk, src = peaks()

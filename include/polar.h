@@ -159,9 +159,11 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
 /* Override the launch shape chosen at create time for one dtype (for the
  * autotuner and tests). warps_per_frame in {1,2,4}; smem_budget caps the
  * shared memory of one frame (0 = default), larger alpha stages move to
- * global scratch to meet it. POLAR_EINVAL if the shape cannot hold the code. */
+ * global scratch to meet it; cta_threads (a multiple of 32 * warps_per_frame,
+ * at most 512; 0 = 128) sets how many frame groups share a CTA and run the
+ * schedule in lockstep. POLAR_EINVAL if the shape cannot hold the code. */
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
-                          uint32_t smem_budget);
+                                    uint32_t smem_budget, uint32_t cta_threads);
 
 /* Adaptive decoding (Sec. V): every frame is first decoded with `fast`
  * (normally the same code with L = 1, i.e. Fast-SSC decoding); the frames
@@ -180,14 +182,15 @@ POLAR_API int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t
                                     polar_stream_t stream);
 
 /* Autotune the launch shape of one dtype on real frames: times every
- * distinct (warps per frame, shared-memory budget) shape on n_frames frames of
- * llr_dev (device, [n_frames][N]) on `stream`, installs the fastest and
- * reports it (either out pointer may be NULL; *budget_out = 0 means no cap).
+ * distinct (warps per frame, CTA size, shared-memory budget) shape on n_frames
+ * frames of llr_dev (device, [n_frames][N]) on `stream`, installs the fastest
+ * and reports it (any out pointer may be NULL; *budget_out = 0 means no cap).
  * Blocks until the timing runs finish. Results of later decodes do not depend
  * on the shape (only speed does). Errors: POLAR_EINVAL, POLAR_ENOMEM,
  * POLAR_ECUDA. */
 POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
-                                  polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out);
+                                  polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out,
+                                  uint32_t *cta_threads_out);
 
 /* ---- Batched form --------------------------------------------------------
  * Frames of several codes (mixed N, rate and L) decoded by one persistent

@@ -7,6 +7,7 @@
 // sit in shared memory and which spill to global scratch).
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -247,14 +248,18 @@ std::vector<uint32_t> flag_ops(const std::vector<uint32_t> &ops, uint32_t warps)
     return out;
 }
 
-bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget, LaunchShape &sh) {
+bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget, LaunchShape &sh,
+                uint32_t cta_threads = 0) {
     if (warps != 1 && warps != 2 && warps != 4) return false;
+    if (cta_threads == 0) cta_threads = 128;
+    if (cta_threads % (32u * warps) != 0 || cta_threads > (uint32_t)kMaxCtaThreads) return false;
     const uint32_t es = dtype == POLAR_LLR_I8 ? 1u : 4u;
-    const uint32_t gpc = 4u / warps;
+    const uint32_t gpc = cta_threads / (32u * warps);
     if (budget == 0) {
-        // Default: 4 frames per SM with 4 warps each, 6 with 2, 8 with 1.
+        // Default: 4 frames per SM with 4 warps each, 6 with 2, 8 with 1, and
+        // never more than one CTA's share of the shared memory.
         const uint32_t groups_per_sm = warps == 4 ? 4u : (warps == 2 ? 6u : 8u);
-        budget = (kMaxSmemPerCta / groups_per_sm) & ~15u;
+        budget = (kMaxSmemPerCta / std::max(groups_per_sm, gpc)) & ~15u;
     }
     budget = std::min(budget, kMaxSmemPerCta / gpc);
     Layout lay;
@@ -262,7 +267,7 @@ bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget,
     sh.d_ops = nullptr;
     sh.warps = (int)warps;
     sh.groups_per_cta = (int)gpc;
-    sh.threads = 128;
+    sh.threads = (int)cta_threads;
     sh.smem = lay.bytes * gpc;
     sh.lay = lay;
     return sh.smem <= kMaxSmemPerCta;
@@ -538,7 +543,7 @@ int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, co
 }
 
 int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
-                        polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out) {
+                        polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out, uint32_t *cta_out) {
     if (!code || code->host_only || !llr_dev || n_frames == 0) return POLAR_EINVAL;
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -557,17 +562,18 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
                                        14000u, 10000u, 7000u};
     float best_ms = 1e30f;
     LaunchShape best;
-    uint32_t best_w = 0, best_b = 0;
-    std::vector<std::pair<uint32_t, uint32_t>> seen;   // (warps, spill mask) already timed
+    uint32_t best_w = 0, best_b = 0, best_t = 0;
+    std::vector<std::array<uint32_t, 3>> seen;   // (warps, CTA threads, spill mask) already timed
     int status = POLAR_OK;
     for (uint32_t w : {4u, 2u, 1u}) {
+      for (uint32_t t : {128u, 256u, 512u}) {
         for (uint32_t b : budgets) {
             LaunchShape sh;
-            if (!make_shape(code, llr_dtype, w, b, sh)) continue;
+            if (!make_shape(code, llr_dtype, w, b, sh, t)) continue;
             bool dup = false;
-            for (auto &pr : seen) dup |= pr.first == w && pr.second == sh.lay.spill_mask;
+            for (auto &pr : seen) dup |= pr[0] == w && pr[1] == t && pr[2] == sh.lay.spill_mask;
             if (dup) continue;
-            seen.push_back({w, sh.lay.spill_mask});
+            seen.push_back({w, t, sh.lay.spill_mask});
             std::vector<uint32_t> fl = flag_ops(code->ops, w);
             if (upload(&sh.d_ops, fl) != cudaSuccess) { status = POLAR_ECUDA; break; }
             float ms = 0.f;
@@ -582,9 +588,11 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
             cudaFree(sh.d_ops);
             sh.d_ops = nullptr;
             if (rc != POLAR_OK) continue;
-            if (ms < best_ms) { best_ms = ms; best = sh; best_w = w; best_b = b; }
+            if (ms < best_ms) { best_ms = ms; best = sh; best_w = w; best_b = b; best_t = t; }
         }
         if (status != POLAR_OK) break;
+      }
+      if (status != POLAR_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -594,6 +602,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     if (best_w == 0) return POLAR_ECUDA;
     if (warps_out) *warps_out = best_w;
     if (budget_out) *budget_out = best_b == 0xffffffffu ? 0u : best_b;
+    if (cta_out) *cta_out = best_t;
     return install_shape(code, llr_dtype, best);
 }
 
@@ -980,10 +989,11 @@ int polar_code_op_count(const polar_code_t *c, uint64_t *ops_per_frame) {
     return POLAR_OK;
 }
 
-int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_frame, uint32_t smem_budget) {
+int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_frame, uint32_t smem_budget,
+                          uint32_t cta_threads) {
     if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
     LaunchShape sh;
-    if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh)) return POLAR_EINVAL;
+    if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh, cta_threads)) return POLAR_EINVAL;
     return install_shape(c, llr_dtype, sh);
 }
 

@@ -129,6 +129,10 @@ struct BatchParams {               // batched form: frames of several codes
     int groups_per_cta;
 };
 
+// Plain-form CTAs hold up to this many threads (frame groups of 1, 2 or 4
+// warps); the groups of one CTA decode the same code in lockstep.
+constexpr int kMaxCtaThreads = 512;
+
 struct LaunchShape {
     int warps;                     // warps per frame group (1, 2, 4)
     uint32_t *d_ops;               // schedule with this shape's solo / sync flags (device)

@@ -859,7 +859,7 @@ __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t
 template <typename T, int W>
 __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uint8_t *Gs, const uint8_t *src,
                                              uint8_t *bits_row, float *pm_out, uint8_t *ok_out, int32_t *slot_out,
-                                             int gidx, int gtid) {
+                                             int gidx, int gtid, bool lockstep) {
     typedef typename Arith<T>::P PT;
     constexpr int GT = W * 32;
     const Layout &lay = cv.lay;
@@ -1050,6 +1050,9 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
         }
         if (op_sync(op)) gsync<W>(gidx);
         else if (wig == 0) __syncwarp();
+        // Every group of the CTA runs the same schedule: a CTA barrier per op
+        // keeps them on the same code, so they share instruction fetches.
+        if (lockstep) asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
         op = opn;
     }
     gsync<W>(gidx);
@@ -1142,7 +1145,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
 
 // Plain form: one code, frames f = group, group + n_groups, ...
 template <typename T, int W>
-__global__ void __launch_bounds__(128) decode_kernel(const Params P) {
+__global__ void __launch_bounds__(kMaxCtaThreads) decode_kernel(const Params P) {
     constexpr int GT = W * 32;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int gidx = threadIdx.x / GT;
@@ -1155,9 +1158,12 @@ __global__ void __launch_bounds__(128) decode_kernel(const Params P) {
     const uint32_t nf = P.frame_idx ? *P.frame_cnt : P.n_frames;
     for (uint32_t i = ggid; i < nf; i += ngroups) {
         const uint32_t f = P.frame_idx ? P.frame_idx[i] : i;
+        // lockstep only in rounds where every group of the CTA has a frame, so
+        // that all warps reach each per-op barrier the same number of times
+        const bool full = P.groups_per_cta > 1 && (i - (uint32_t)gidx) + (uint32_t)P.groups_per_cta <= nf;
         decode_frame<T, W>(P.cv, S, Gs, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
                            P.bits + (size_t)f * P.cv.kb, P.pm + f, P.ok ? P.ok + f : nullptr,
-                           P.slot ? P.slot + f : nullptr, gidx, gtid);
+                           P.slot ? P.slot + f : nullptr, gidx, gtid, full);
     }
 }
 
@@ -1209,7 +1215,8 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchParams B) {
             gsync<W>(gidx);
         }
         decode_frame<T, W>(*cvs, S, Gs, B.llr + item.llr_off, B.bits + item.bits_off, B.pm + item.frame,
-                           B.ok ? B.ok + item.frame : nullptr, B.slot ? B.slot + item.frame : nullptr, gidx, gtid);
+                           B.ok ? B.ok + item.frame : nullptr, B.slot ? B.slot + item.frame : nullptr, gidx, gtid,
+                           false);
     }
 }
 

@@ -105,8 +105,9 @@ def _lib():
         lib.polar_code_get_info.argtypes = [vp, ctypes.POINTER(CodeInfo)]
         lib.polar_code_schedule.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
         lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
-        lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32]
-        lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32, u32]
+        lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32),
+                                             ctypes.POINTER(u32)]
         lib.polar_list_decode_noalloc.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
         lib.polar_noalloc_scratch_bytes.argtypes = []
         lib.polar_batch_plan.argtypes = [ctypes.POINTER(vp), vp, u32, vp, u32, i32, u32]
@@ -212,18 +213,19 @@ class PolarCode:
         _check(_lib().polar_code_op_count(self._h, ctypes.byref(v)), "polar_code_op_count")
         return int(v.value)
 
-    def set_launch(self, dtype: int, warps_per_frame: int, smem_budget: int = 0):
-        _check(_lib().polar_code_set_launch(self._h, dtype, warps_per_frame, smem_budget), "polar_code_set_launch")
+    def set_launch(self, dtype: int, warps_per_frame: int, smem_budget: int = 0, cta_threads: int = 0):
+        _check(_lib().polar_code_set_launch(self._h, dtype, warps_per_frame, smem_budget, cta_threads),
+               "polar_code_set_launch")
 
     def autotune(self, llr, stream=None):
         """Time the launch shapes on ``llr`` ([F, N] CUDA tensor) and keep the fastest."""
         import torch
         dt = LLR_I8 if llr.dtype == torch.int8 else LLR_F32
-        w, b = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        w, b, t = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
         _check(_lib().polar_code_autotune(self._h, dt, ctypes.c_void_p(llr.data_ptr()), llr.numel() // self.N,
-                                          _stream_handle(stream), ctypes.byref(w), ctypes.byref(b)),
+                                          _stream_handle(stream), ctypes.byref(w), ctypes.byref(b), ctypes.byref(t)),
                "polar_code_autotune")
-        return int(w.value), int(b.value)
+        return int(w.value), int(b.value), int(t.value)
 
     def decode_into(self, llr, bits, pm, ok=None, slot=None, stream=None):
         """Enqueue a decode of ``llr`` ([F, N] float32 or int8 CUDA tensor)."""

@@ -114,13 +114,14 @@ def test_launch_shapes_and_spills_agree(torch_cuda, oracle_mod, dtype):
     from paper_1505_01466_gb300.polar import PolarCode
     for warps in (1, 2, 4):
         for budget in (0, 60000, 20000):
-            code = PolarCode(fr, 32, I.CRC32_POLY, 16)
-            try:
-                code.set_launch(1 if dtype == "i8" else 0, warps, budget)
-            except Exception:
-                continue
-            g = gpu_decode(torch_cuda, code, llr)
-            assert_parity(g, o, dtype, f"warps={warps} budget={budget} info={code.info()}")
+            for cta in (128, 512):
+                code = PolarCode(fr, 32, I.CRC32_POLY, 16)
+                try:
+                    code.set_launch(1 if dtype == "i8" else 0, warps, budget, cta)
+                except Exception:
+                    continue
+                g = gpu_decode(torch_cuda, code, llr)
+                assert_parity(g, o, dtype, f"warps={warps} budget={budget} cta={cta} info={code.info()}")
 
 
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
@@ -183,8 +184,8 @@ def test_autotune_keeps_results(torch_cuda, oracle_mod):
         code = PolarCode(fr, 32, I.CRC32_POLY, 8)
         llr = torch_cuda.from_numpy(llr_np).cuda()
         before = code.decode(llr)
-        w, b = code.autotune(llr)
-        assert w in (1, 2, 4)
+        w, b, t = code.autotune(llr)
+        assert w in (1, 2, 4) and t in (128, 256, 512)
         after = code.decode(llr)
         torch_cuda.cuda.synchronize()
         for x, y in zip(before, after):
