@@ -1206,10 +1206,12 @@ int srv_launch(polar_server *s, int i) {
             return POLAR_ENOMEM;
         s->items_cap[i] = cap;
     }
-    // items: larger codes first
+    // items: larger codes first, each code's frames adjacent (lockstep units)
     std::vector<SrvReq *> ord = take;
-    std::stable_sort(ord.begin(), ord.end(), [](SrvReq *a, SrvReq *b) {
-        return (uint64_t)a->code->N * a->code->L > (uint64_t)b->code->N * b->code->L;
+    std::stable_sort(ord.begin(), ord.end(), [s](SrvReq *a, SrvReq *b) {
+        const uint64_t ca = (uint64_t)a->code->N * a->code->L, cb = (uint64_t)b->code->N * b->code->L;
+        if (ca != cb) return ca > cb;
+        return s->code_idx.at(a->code) < s->code_idx.at(b->code);
     });
     const uint64_t es = d == POLAR_LLR_I8 ? 1 : 4;
     uint64_t t = 0;

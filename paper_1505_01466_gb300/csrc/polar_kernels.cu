@@ -1184,9 +1184,11 @@ __global__ void crc_failures_kernel(const uint8_t *ok, uint32_t n, uint32_t *idx
     }
 }
 
-// Batched form: frames of several codes in one persistent launch. Groups take
-// work items (ordered by decreasing cost) from a device counter; the code of
-// an item is copied into the group's shared memory when it changes.
+// Batched form: frames of several codes in one persistent launch. A CTA takes
+// one work item per group (items ordered by decreasing cost, each class's
+// items contiguous) from a device counter; the code of an item is copied into
+// the group's shared memory when it changes. When all groups of the CTA got a
+// frame of the same code they run it in lockstep, as in the plain form.
 template <typename T, int W>
 __global__ void __launch_bounds__(128) batch_kernel(const BatchParams B) {
     constexpr int GT = W * 32;
@@ -1199,13 +1201,22 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchParams B) {
     uint8_t *S = region + B.view_bytes;
     const int ggid = blockIdx.x * B.groups_per_cta + gidx;
     uint8_t *Gs = B.scratch ? B.scratch + (size_t)ggid * B.gbytes : nullptr;
+    // the CTA's work slot is group 0's
+    uint32_t *cta_slot = reinterpret_cast<uint32_t *>(smem_raw + sizeof(CodeView));
     uint32_t loaded = 0xffffffffu;
+    (void)slot_word;
     for (;;) {
-        if (gtid == 0) *slot_word = atomicAdd(B.counter, 1u);
-        gsync<W>(gidx);
-        const uint32_t it = *slot_word;
-        gsync<W>(gidx);
-        if (it >= B.n_items) break;
+        if (threadIdx.x == 0) *cta_slot = atomicAdd(B.counter, (uint32_t)B.groups_per_cta);
+        __syncthreads();
+        const uint32_t base = *cta_slot;
+        const uint32_t it = base + (uint32_t)gidx;
+        const bool have = it < B.n_items;
+        const uint32_t cls = have ? B.items[it].cls : 0xffffffffu;
+        const uint32_t cls0 = base < B.n_items ? B.items[base].cls : 0xfffffffeu;
+        // also orders the read of the slot above before its next write
+        const bool lock = __syncthreads_and(have && cls == cls0) && B.groups_per_cta > 1;
+        if (base >= B.n_items) break;
+        if (!have) continue;
         const BatchItem item = B.items[it];
         if (item.cls != loaded) {
             const uint32_t *srcw = reinterpret_cast<const uint32_t *>(B.classes + item.cls);
@@ -1216,7 +1227,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchParams B) {
         }
         decode_frame<T, W>(*cvs, S, Gs, B.llr + item.llr_off, B.bits + item.bits_off, B.pm + item.frame,
                            B.ok ? B.ok + item.frame : nullptr, B.slot ? B.slot + item.frame : nullptr, gidx, gtid,
-                           false);
+                           lock);
     }
 }
 
