@@ -525,34 +525,30 @@ def run_ours(args):
     got = I.unpack_bits_lsb(bits[: min(UNIQUE, args.frames)].cpu().numpy(), k)
     fer = float((got != fr.payload[: got.shape[0]]).any(axis=1).mean())
 
-    # ---- end to end through the C ABI with host buffers ----
+    # ---- end to end through the C ABI with host buffers (polar_list_decode_host:
+    # pinned host LLRs in, pinned host payload / penalty / CRC flag out; the call
+    # pipelines copies and decodes in chunks and returns when the outputs are on
+    # the host, so wall-clock time brackets the whole step) ----
     host_llr = torch.empty_like(llr, device="cpu").pin_memory()
     host_llr.copy_(llr.cpu())
     hbits = torch.empty((args.frames, kb), dtype=torch.uint8).pin_memory()
     hpm = torch.empty(args.frames, dtype=torch.float32).pin_memory()
     hok = torch.empty(args.frames, dtype=torch.uint8).pin_memory()
-    dllr = torch.empty_like(llr)
     e2e_steps = max(1, min(args.steps, 3))
-    with torch.cuda.stream(stream):
-        dllr.copy_(host_llr, non_blocking=True)
-        code.decode_into(dllr, bits, pm, ok, None, stream=stream)
+    code.decode_host(host_llr, hbits, hpm, hok, stream=stream)
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        code.decode_host(host_llr, hbits, hpm, hok, stream=stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     barrier()
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            dllr.copy_(host_llr, non_blocking=True)
-            code.decode_into(dllr, bits, pm, ok, None, stream=stream)
-            hbits.copy_(bits, non_blocking=True)
-            hpm.copy_(pm, non_blocking=True)
-            hok.copy_(ok, non_blocking=True)
-        e1.record(stream)
-    barrier()
-    e2e_ms = reduce_max(torch, e0.elapsed_time(e1) / e2e_steps, dev)
+    e2e_ms = reduce_max(torch, e2e_ms, dev)
     e2e_val = job_gbps(k, args.frames, world, e2e_ms)
+    if not torch.equal(hbits[:UNIQUE].to(dev), bits[:UNIQUE]):
+        raise RuntimeError("host-buffer decode differs from the device decode")
     h2d = llr.numel() * llr.element_size()
-    d2h = bits.numel() + pm.numel() * 4 + ok.numel()
+    d2h = hbits.numel() + hpm.numel() * 4 + hok.numel()
+    del host_llr
 
     info = code.info()
     launch_info = {"warps_per_frame": info["warps_per_frame"][di], "frames_per_cta": info["frames_per_cta"][di],

@@ -165,6 +165,19 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                                     uint32_t smem_budget, uint32_t cta_threads);
 
+/* polar_list_decode on HOST buffers (same layouts, host pointers): the frames
+ * go through the device in chunks, the copy in of one chunk and the copy out
+ * of another overlapping the decode of a third (two device staging buffers,
+ * two internal streams; the decodes run on `stream`). Pinned host memory
+ * (cudaHostAlloc / cudaHostRegister) is needed for the copies to overlap;
+ * pageable memory works but serialises them. Blocks until every output is in
+ * host memory. Allocates its staging buffers with cudaMalloc and frees them
+ * before returning. Errors as polar_list_decode; POLAR_EINVAL also when the
+ * current device is not the code's. */
+POLAR_API int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int llr_dtype, uint32_t n_frames,
+                                     uint8_t *info_bits_host, float *path_metric_host, uint8_t *crc_ok_host,
+                                     int32_t *winner_slot_host, polar_stream_t stream);
+
 /* Adaptive decoding (Sec. V): every frame is first decoded with `fast`
  * (normally the same code with L = 1, i.e. Fast-SSC decoding); the frames
  * whose CRC fails are then decoded again with `list` (the target L_max) and

@@ -508,6 +508,92 @@ int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dty
                         crc_ok_dev, winner_slot_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int llr_dtype, uint32_t n_frames,
+                           uint8_t *info_bits_host, float *path_metric_host, uint8_t *crc_ok_host,
+                           int32_t *winner_slot_host, polar_stream_t stream) {
+    if (!code || code->host_only) return POLAR_EINVAL;
+    if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    if (n_frames == 0) return POLAR_OK;
+    if (!llr_host || !path_metric_host || (!info_bits_host && code->k > 0)) return POLAR_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
+    if (dev != code->device) return POLAR_EINVAL;
+    const uint64_t row = (uint64_t)code->N * (llr_dtype == POLAR_LLR_I8 ? 1u : 4u);
+    const uint64_t kb = (code->k + 7) / 8;
+    // chunks of frames in a two-buffer ring: the copy in of chunk c + 1 and the
+    // copy out of chunk c - 1 overlap the decode of chunk c
+    const uint32_t chunk = std::min<uint32_t>(n_frames, std::max<uint32_t>(4096u, std::min<uint32_t>(131072u, n_frames / 8)));
+    const uint32_t n_chunks = (n_frames + chunk - 1) / chunk;
+    const uint64_t out_row = kb + 4 + 1 + 4;
+    const uint64_t buf_bytes = (uint64_t)chunk * (row + out_row) + 64;
+    cudaStream_t dec = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_dec[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    uint8_t *buf[2] = {nullptr, nullptr};
+    int rc = POLAR_OK;
+    bool ok = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; ok && b < 2; ++b)
+        ok = cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ev_dec[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) rc = POLAR_ECUDA;
+    for (int b = 0; rc == POLAR_OK && b < 2 && b < (int)n_chunks; ++b)
+        if (cudaMalloc(&buf[b], buf_bytes) != cudaSuccess) rc = POLAR_ENOMEM;
+    // the caller's stream may have pending work on the host buffers' producers
+    if (rc == POLAR_OK && cudaEventRecord(ev_dec[0], dec) != cudaSuccess) rc = POLAR_ECUDA;
+    if (rc == POLAR_OK && cudaStreamWaitEvent(cin, ev_dec[0], 0) != cudaSuccess) rc = POLAR_ECUDA;
+    for (uint32_t c = 0; rc == POLAR_OK && c < n_chunks; ++c) {
+        const int b = (int)(c & 1u);
+        const uint64_t f0 = (uint64_t)c * chunk;
+        const uint32_t nf = (uint32_t)std::min<uint64_t>(chunk, n_frames - f0);
+        uint8_t *d_llr = buf[b];
+        uint8_t *d_bits = d_llr + (uint64_t)chunk * row;
+        float *d_pm = reinterpret_cast<float *>(((uintptr_t)(d_bits + (uint64_t)chunk * kb) + 15) & ~(uintptr_t)15);
+        int32_t *d_slot = reinterpret_cast<int32_t *>(d_pm + chunk);
+        uint8_t *d_ok = reinterpret_cast<uint8_t *>(d_slot + chunk);
+        // buffer b is free once the copy out of chunk c - 2 finished
+        if (c >= 2 && cudaStreamWaitEvent(cin, ev_out[b], 0) != cudaSuccess) { rc = POLAR_ECUDA; break; }
+        if (cudaMemcpyAsync(d_llr, static_cast<const uint8_t *>(llr_host) + f0 * row, (size_t)nf * row,
+                            cudaMemcpyHostToDevice, cin) != cudaSuccess ||
+            cudaEventRecord(ev_in[b], cin) != cudaSuccess || cudaStreamWaitEvent(dec, ev_in[b], 0) != cudaSuccess) {
+            rc = POLAR_ECUDA;
+            break;
+        }
+        rc = decode_shape(code, llr_dtype, code->shape[llr_dtype], d_llr, nf, d_bits, d_pm, d_ok, d_slot, dec);
+        if (rc != POLAR_OK) break;
+        if (cudaEventRecord(ev_dec[b], dec) != cudaSuccess || cudaStreamWaitEvent(cout, ev_dec[b], 0) != cudaSuccess) {
+            rc = POLAR_ECUDA;
+            break;
+        }
+        bool cp = true;
+        if (code->k > 0)
+            cp = cudaMemcpyAsync(info_bits_host + f0 * kb, d_bits, (size_t)nf * kb, cudaMemcpyDeviceToHost, cout) ==
+                 cudaSuccess;
+        cp = cp && cudaMemcpyAsync(path_metric_host + f0, d_pm, (size_t)nf * 4, cudaMemcpyDeviceToHost, cout) ==
+                       cudaSuccess;
+        if (crc_ok_host)
+            cp = cp && cudaMemcpyAsync(crc_ok_host + f0, d_ok, nf, cudaMemcpyDeviceToHost, cout) == cudaSuccess;
+        if (winner_slot_host)
+            cp = cp && cudaMemcpyAsync(winner_slot_host + f0, d_slot, (size_t)nf * 4, cudaMemcpyDeviceToHost, cout) ==
+                           cudaSuccess;
+        if (!cp || cudaEventRecord(ev_out[b], cout) != cudaSuccess) { rc = POLAR_ECUDA; break; }
+    }
+    // drain everything that was enqueued, also after an error
+    if (cin && cudaStreamSynchronize(cin) != cudaSuccess) rc = POLAR_ECUDA;
+    if (cudaStreamSynchronize(dec) != cudaSuccess) rc = POLAR_ECUDA;
+    if (cout && cudaStreamSynchronize(cout) != cudaSuccess) rc = POLAR_ECUDA;
+    for (int b = 0; b < 2; ++b) {
+        if (buf[b]) cudaFree(buf[b]);
+        if (ev_in[b]) cudaEventDestroy(ev_in[b]);
+        if (ev_dec[b]) cudaEventDestroy(ev_dec[b]);
+        if (ev_out[b]) cudaEventDestroy(ev_out[b]);
+    }
+    if (cin) cudaStreamDestroy(cin);
+    if (cout) cudaStreamDestroy(cout);
+    return rc;
+}
+
 int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, const void *llr_dev, int llr_dtype,
                           uint32_t n_frames, uint8_t *info_bits_dev, float *path_metric_dev, uint8_t *crc_ok_dev,
                           int32_t *winner_slot_dev, uint32_t *n_relisted_dev, polar_stream_t stream) {

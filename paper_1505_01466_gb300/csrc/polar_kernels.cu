@@ -146,9 +146,9 @@ template <typename K> __device__ __forceinline__ K kmax(K a, K b) { return a < b
 
 template <typename K>
 __device__ __forceinline__ K bsort32(K x, int lane) {   // ascending across the warp
-#pragma unroll 1
+#pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll 1
+#pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             const K o = __shfl_xor_sync(FULL, x, j);
             const bool up = (lane & k) == 0;
@@ -161,7 +161,7 @@ __device__ __forceinline__ K bsort32(K x, int lane) {   // ascending across the 
 
 template <typename K>
 __device__ __forceinline__ K bmerge32(K x, int lane) {  // bitonic -> ascending
-#pragma unroll 1
+#pragma unroll
     for (int j = 16; j > 0; j >>= 1) {
         const K o = __shfl_xor_sync(FULL, x, j);
         x = ((lane & j) == 0) ? kmin(x, o) : kmax(x, o);
@@ -186,11 +186,51 @@ __device__ __forceinline__ void sort8(K (&k)[8]) {   // Batcher odd-even merge n
     ce(k[1], k[2]); ce(k[3], k[4]); ce(k[5], k[6]);
 }
 
-// The L-th smallest key of the warp, lane s holding its keys sorted in k[].
-// Column r (every lane's r-th key) can change the result only while its
-// minimum is below the current L-th key; each lane's columns only grow.
+__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += o;
+    }
+    return x - v;
+}
+
+// The L-th smallest key of the warp, lane s holding its keys sorted in k[]
+// (lanes >= La hold none). `tmp` is warp scratch in shared memory for at least
+// L keys.
 template <typename K>
-__device__ __forceinline__ K warp_kth(const K (&k)[8], int C, int L, int lane) {
+__device__ __forceinline__ K warp_kth(const K (&k)[8], int C, int L, int La, int lane, K *tmp) {
+    if (C >= 4 && La == L) {
+        // With a full list, the L sources' best keys are L keys no larger than
+        // t0 (the largest of them), so the result is at most t0: only the few
+        // later candidates below t0 can still displace a best key.
+        K t0 = lane < La ? k[0] : (K)0;
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) t0 = kmax(t0, __shfl_xor_sync(FULL, t0, m));
+        int t = 0;
+#pragma unroll
+        for (int r = 1; r < 8; ++r) t += k[r] < t0 ? 1 : 0;
+        const int base = warp_excl_scan(t, lane);
+        const int tot = __shfl_sync(FULL, base + t, 31);
+        if (tot == 0) return t0;
+        if (tot <= L) {
+#pragma unroll
+            for (int r = 1; r < 8; ++r)
+                if (r <= t) tmp[base + r - 1] = k[r];
+            __syncwarp();
+            K y = lane < tot ? tmp[lane] : ~(K)0;
+            __syncwarp();
+            K B = bsort32(k[0], lane);
+            y = bsort32(y, lane);
+            y = __shfl_sync(FULL, y, 31 - lane);      // descending
+            B = bmerge32(kmin(B, y), lane);
+            return __shfl_sync(FULL, B, L - 1);
+        }
+    }
+    // General case: column r (every lane's r-th key) can change the result
+    // only while its minimum is below the current L-th key; each lane's
+    // columns only grow.
     K B = bsort32(k[0], lane);
     K tau = __shfl_sync(FULL, B, L - 1);
     // later columns, one per iteration (kept rolled: the body is large)
@@ -212,16 +252,6 @@ __device__ __forceinline__ K warp_kth(const K (&k)[8], int C, int L, int lane) {
         tau = __shfl_sync(FULL, B, L - 1);
     }
     return tau;
-}
-
-__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
-    int x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(FULL, x, d);
-        if (lane >= d) x += o;
-    }
-    return x - v;
 }
 
 // ---- register-resident subtrees (OP_SUB) ----------------------------------
@@ -276,7 +306,7 @@ __device__ __noinline__ KT select_keys(KT k0, KT k1, KT k2, KT k3, KT k4, KT k5,
                                        int lane, KT *tab) {
     const KT KINF = (KT)~(KT)0;
     KT k[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
-    const KT tau = (nc > L) ? warp_kth(k, C, L, lane) : KINF;
+    const KT tau = (nc > L) ? warp_kth(k, C, L, nc / C, lane, tab) : KINF;
     const uint32_t cm = (uint32_t)(C - 1);
     uint32_t sm = 0;
 #pragma unroll
@@ -800,13 +830,13 @@ __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t
     }
     // selection (Algorithm 1)
     const int nc = La * C;
-    const KT tau = (nc > L) ? warp_kth(k, C, L, lane) : KINF;
+    KT *tab = reinterpret_cast<KT *>(S + lay.surv);
+    const KT tau = (nc > L) ? warp_kth(k, C, L, La, lane, tab) : KINF;
     uint32_t sm = 0;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
         if (k[r] != KINF && k[r] <= tau) sm |= 1u << (Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
     const int base = warp_excl_scan(__popc(sm), lane);
-    KT *tab = reinterpret_cast<KT *>(S + lay.surv);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         if (k[r] != KINF && k[r] <= tau) {

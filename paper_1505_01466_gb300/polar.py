@@ -28,7 +28,7 @@ EXPORTED = [
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
     "polar_server_create", "polar_server_destroy", "polar_server_submit", "polar_server_poll", "polar_server_wait",
-    "polar_server_pause", "polar_server_stats", "polar_adaptive_decode",
+    "polar_server_pause", "polar_server_stats", "polar_adaptive_decode", "polar_list_decode_host",
 ]
 
 
@@ -127,6 +127,7 @@ def _lib():
         lib.polar_server_pause.argtypes = [vp, i32]
         lib.polar_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats), i32]
         lib.polar_adaptive_decode.argtypes = [vp, vp, vp, i32, u32, vp, vp, vp, vp, vp, vp]
+        lib.polar_list_decode_host.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32
@@ -245,6 +246,21 @@ class PolarCode:
             ctypes.c_void_p(ok.data_ptr() if ok is not None else 0),
             ctypes.c_void_p(slot.data_ptr() if slot is not None else 0), _stream_handle(stream))
         _check(st, "polar_list_decode")
+
+    def decode_host(self, llr, bits, pm, ok=None, slot=None, stream=None):
+        """polar_list_decode_host: ``llr`` and the outputs are CPU tensors (pinned
+        for overlapped copies); blocks until the outputs are written."""
+        import torch
+        dt = LLR_I8 if llr.dtype == torch.int8 else LLR_F32
+        for t in (llr, bits, pm) + tuple(x for x in (ok, slot) if x is not None):
+            if t.is_cuda or not t.is_contiguous():
+                raise PolarError("decode_host takes contiguous host tensors")
+        F = llr.numel() // self.N
+        _check(_lib().polar_list_decode_host(self._h, ctypes.c_void_p(llr.data_ptr()), dt, F,
+                                             ctypes.c_void_p(bits.data_ptr()), ctypes.c_void_p(pm.data_ptr()),
+                                             ctypes.c_void_p(ok.data_ptr() if ok is not None else 0),
+                                             ctypes.c_void_p(slot.data_ptr() if slot is not None else 0),
+                                             _stream_handle(stream)), "polar_list_decode_host")
 
     def decode(self, llr, stream=None):
         """Decode; returns (payload bits [F, ceil(k/8)] uint8, penalty [F], crc_ok [F], slot [F])."""

@@ -192,3 +192,29 @@ def test_autotune_keeps_results(torch_cuda, oracle_mod):
             assert torch_cuda.equal(x, y)
         o = oracle_mod.decode(fr, 8, llr_np[:64], 32, I.CRC32_POLY, 0, n_threads=NT)
         assert_parity(tuple(t[:64].cpu().numpy() for t in after), o, "i8" if llr_np.dtype == np.int8 else "f32")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_host_buffer_decode_matches_device_decode(torch_cuda, oracle_mod, dtype):
+    # polar_list_decode_host: chunked copy in / decode / copy out, ragged last chunk
+    from paper_1505_01466_gb300.polar import PolarCode
+    torch = torch_cuda
+    fr = I.ga_frozen_mask(512, 300, 3.0, 268 / 512)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 2.5, 10001, seed=12)
+    x = f.llr_i8 if dtype == "i8" else f.llr_f32
+    code = PolarCode(fr, 32, I.CRC32_POLY, 8)
+    ref = [t.cpu() for t in code.decode(torch.from_numpy(x).cuda())]
+    for pinned in (True, False):
+        hl = torch.from_numpy(x).clone()
+        if pinned:
+            hl = hl.pin_memory()
+        bits = torch.full_like(ref[0], 0xAA)
+        pm = torch.full_like(ref[1], -1.0)
+        ok = torch.full_like(ref[2], 7)
+        slot = torch.full_like(ref[3], -1)
+        code.decode_host(hl, bits, pm, ok, slot)
+        for a, b in zip((bits, pm, ok, slot), ref):
+            assert torch.equal(a, b)
+    o = oracle_mod.decode(fr, 8, x[-40:], 32, I.CRC32_POLY, 0, n_threads=NT)
+    assert_parity(tuple(t[-40:].numpy() for t in ref), o, dtype, "host decode tail")
+    code.close()
