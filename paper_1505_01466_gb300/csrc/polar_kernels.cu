@@ -959,12 +959,12 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                 if (sizeof(T) == 4) {
                     const int lv = jo - 2;             // h >= 16 here: float4 items
                     const int total = La << lv;
-                    for (int t0 = tid; t0 < total; t0 += 2 * nthr) {
-                        float4 a[2], b[2];
-                        uint32_t nb[2] = {0u, 0u};
-                        int pp[2], vv[2];
+                    for (int t0 = tid; t0 < total; t0 += 4 * nthr) {
+                        float4 a[4], b[4];
+                        uint32_t nb[4] = {0u, 0u, 0u, 0u};
+                        int pp[4], vv[4];
 #pragma unroll
-                        for (int u = 0; u < 2; ++u) {
+                        for (int u = 0; u < 4; ++u) {
                             const int t = t0 + u * nthr;
                             pp[u] = t < total ? t >> lv : 0;
                             vv[u] = t < total ? t & ((1 << lv) - 1) : 0;
@@ -978,7 +978,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < 2; ++u) {
+                        for (int u = 0; u < 4; ++u) {
                             if (t0 + u * nthr >= total) break;
                             float4 r;
                             if (isG) {
