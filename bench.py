@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--launch", default=None,
                     help="WARPS,SMEM_BUDGET[,CTA_THREADS]: fixed launch shape instead of autotuning")
     ap.add_argument("--skip-fer", action="store_true")
+    ap.add_argument("--skip-ablation", action="store_true")
+    ap.add_argument("--ablation-frames", type=int, default=1 << 17)
     ap.add_argument("--fer-frames", type=int, default=1 << 17, help="frames per Eb/N0 point of the FER sweep")
     ap.add_argument("--fer-points", default="3.5,4.0,4.5", help="Eb/N0 points (dB) of the FER sweep")
     return ap.parse_args()
@@ -253,6 +255,7 @@ def measure_fer(args, torch, dev, stream):
     fast = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L, mode=0)
     scl = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L, mode=2)
     sc1 = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 1, mode=0)
+    fast8 = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 8, mode=0)
     tuned = set()
 
     def timed(fn):
@@ -270,18 +273,19 @@ def measure_fer(args, torch, dev, stream):
         for dt in ("f32", "i8"):
             llr = torch.from_numpy(fr.llr_i8 if dt == "i8" else fr.llr_f32).to(dev)
             if dt not in tuned:
-                for c in (fast, scl, sc1):
+                for c in (fast, scl, sc1, fast8):
                     c.autotune(llr[:16384], stream=stream)
                 tuned.add(dt)
             errs, ms = {}, {}
             for name, fn in (("fast", lambda: fast.decode(llr, stream=stream)),
                              ("scl", lambda: scl.decode(llr, stream=stream)),
-                             ("adaptive", lambda: adaptive_decode(sc1, fast, llr, stream=stream))):
+                             ("adaptive", lambda: adaptive_decode(sc1, fast, llr, stream=stream)),
+                             ("adaptive8", lambda: adaptive_decode(sc1, fast8, llr, stream=stream))):
                 fn()                                     # warm-up
                 out, ms[name] = timed(fn)
                 got = I.unpack_bits_lsb(out[0].cpu().numpy(), k)
                 errs[name] = (got != fr.payload).any(axis=1)
-                if name == "adaptive":
+                if name.startswith("adaptive"):
                     relisted = int(out[4].item())
             t = paired_fer_test(errs["fast"], errs["scl"])
             points.append({
@@ -295,14 +299,60 @@ def measure_fer(args, torch, dev, stream):
                 "gbps_fast": k * args.fer_frames / ms["fast"] / 1e6,
                 "gbps_scl": k * args.fer_frames / ms["scl"] / 1e6,
                 "gbps_adaptive": k * args.fer_frames / ms["adaptive"] / 1e6,
+                "fer_adaptive_L8": float(errs["adaptive8"].mean()),
+                "gbps_adaptive_L8": k * args.fer_frames / ms["adaptive8"] / 1e6,
             })
             del llr
-    for c in (fast, scl, sc1):
+    for c in (fast, scl, sc1, fast8):
         c.close()
     return {"code": f"({N},{K}) CRC-32 L={L}, GA {DESIGN_DB} dB", "fast": "Dec-SPC-4",
             "plain": "SC-list with length-one leaves (bit-exact with the oracle's SC-list)",
             "adaptive": f"Fast-SSC (L=1) then L={L} on CRC failures", "test": "exact McNemar + Clopper-Pearson 99%",
             "points": points}
+
+
+def measure_ablation(args, torch, dev, stream):
+    """Node-set ablation in the shape of the paper's Table I: (2048,1723) at
+    L = 2, 8, 32 with plain SC-list leaves, Dec-SPC-4 and Dec-SPC-4+ (L <= 8).
+    Throughput over a full batch and the latency of one frame decoded alone."""
+    from paper_1505_01466_gb300 import inputs as I
+    from paper_1505_01466_gb300.polar import PolarCode
+    frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
+    fr = I.make_frames_chunked(frozen, CRC_LEN, I.CRC32_POLY, EBN0_DB, min(args.ablation_frames, 16384), seed=77)
+    x = torch.from_numpy(fr.llr_f32).to(dev)
+    reps = (args.ablation_frames + x.shape[0] - 1) // x.shape[0]
+    llr = x.repeat(reps, 1)[: args.ablation_frames].contiguous()
+    k = K - CRC_LEN
+    rows = []
+    for Ls in (2, 8, 32):
+        for mode, name in ((2, "SC-list (length-one leaves)"), (0, "Dec-SPC-4"), (1, "Dec-SPC-4+")):
+            if mode == 1 and Ls > 8:
+                continue
+            code = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, Ls, mode=mode)
+            code.autotune(llr[:16384], stream=stream)
+            bits = torch.empty((llr.shape[0], (k + 7) // 8), dtype=torch.uint8, device=dev)
+            pm = torch.empty(llr.shape[0], dtype=torch.float32, device=dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                code.decode_into(llr, bits, pm, None, None, stream=stream)
+                a.record(stream)
+                code.decode_into(llr, bits, pm, None, None, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            lat = []
+            for _ in range(7):
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    code.decode_into(llr[:1], bits[:1], pm[:1], None, None, stream=stream)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                lat.append(a.elapsed_time(b) * 1e3)
+            rows.append({"L": Ls, "decoder": name, "gbps": k * llr.shape[0] / ms / 1e6,
+                         "frames_per_s": llr.shape[0] / ms * 1e3, "one_frame_latency_us": statistics.median(lat[2:])})
+            code.close()
+    return {"code": f"({N},{K}) CRC-32, f32 LLRs at {EBN0_DB} dB, {args.ablation_frames} frames per batch",
+            "rows": rows}
 
 
 def measure_batched(args, torch, dev, stream, barrier):
@@ -389,7 +439,7 @@ def measure_batched(args, torch, dev, stream, barrier):
         "graph_replay": True, "results_equal_plain": same,
         "launch": {"warps_per_frame": binfo["warps_per_frame"], "frames_per_cta": binfo["frames_per_cta"],
                    "smem_per_frame": binfo["smem_per_frame"], "grid": binfo["grid"],
-                   "autotuned": {"warps": tuned[0], "smem_budget": tuned[1]}},
+                   "autotuned": {"warps": tuned[0], "smem_budget": tuned[1], "cta_threads": tuned[2]}},
     }
 
 
@@ -601,6 +651,9 @@ def run_ours(args):
     fer_sweep = None
     if rank == 0 and not args.skip_fer:
         fer_sweep = measure_fer(args, torch, dev, stream)
+    ablation = None
+    if rank == 0 and not args.skip_ablation:
+        ablation = measure_ablation(args, torch, dev, stream)
 
     batched = None
     if not args.skip_batched:
@@ -631,6 +684,7 @@ def run_ours(args):
             "batched": batched,
             "serving": serving,
             "fer": fer_sweep,
+            "ablation": ablation,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

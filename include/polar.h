@@ -76,9 +76,13 @@ enum polar_flags {
                                        bits ("Dec-SPC-4+", Sec. III-D, VI) */
     POLAR_NO_SPECIAL_NODES = 2,     /* length-one leaves only: unrolled SC-list
                                        (Table I, "Unrolled SC-list") */
-    POLAR_HOST_ONLY = 0x100         /* build the schedule and tables on the host
+    POLAR_HOST_ONLY = 0x100,        /* build the schedule and tables on the host
                                        only: no CUDA call, cannot decode (for
                                        inspecting schedules without a GPU) */
+    POLAR_SYSTEMATIC = 0x200        /* systematic code (the encoder cited in
+                                       Sec. I): payload and CRC are read from the
+                                       decoded codeword x at the information
+                                       positions instead of from u = x G_N */
 };
 
 /* Create a code object.
@@ -90,7 +94,8 @@ enum polar_flags {
  *   crc_poly     generator polynomial without the x^crc_len term.
  *   L            list size, a power of two, 1 <= L <= 32 (L = 1 is Fast-SSC
  *                decoding, Sec. V).
- *   flags        one node-set value, optionally | POLAR_HOST_ONLY.
+ *   flags        one node-set value, optionally | POLAR_HOST_ONLY and/or
+ *                POLAR_SYSTEMATIC.
  * Builds the decoding tree (Sec. II-D: the largest Rate-0 / Rate-1 /
  * repetition / SPC sub-tree from the root down), the unrolled operation list
  * (Listing 2) and the CRC tables, and copies them to the current device.
@@ -245,14 +250,19 @@ POLAR_API int polar_batch_layout(const polar_batch_t *batch, uint64_t *llr_bytes
  * (they share the plan's work counter and scratch). */
 POLAR_API int polar_batch_run(polar_batch_t *batch, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
                               uint8_t *ok_dev, int32_t *slot_dev, polar_stream_t stream);
-/* Choose warps per frame and the shared-memory budget per frame (larger
- * alpha stages go to the plan's global scratch). */
-POLAR_API int polar_batch_set_launch(polar_batch_t *batch, uint32_t warps_per_frame, uint32_t smem_budget);
-/* Autotuner: times every (warps per frame, budget) shape on the plan's own
- * frames (llr_dev as for polar_batch_run; bits_dev / pm_dev are scratch
- * outputs), keeps the fastest, reports it. Blocks until done. */
+/* Choose warps per frame, the shared-memory budget per frame (larger alpha
+ * stages go to the plan's global scratch) and the CTA size (a multiple of
+ * 32 * warps_per_frame, at most 512; 0 = 128). A CTA takes one frame per group
+ * at a time; groups holding frames of the same code run in lockstep. */
+POLAR_API int polar_batch_set_launch(polar_batch_t *batch, uint32_t warps_per_frame, uint32_t smem_budget,
+                                     uint32_t cta_threads);
+/* Autotuner: times (warps per frame in {1,2}, CTA size, budget) shapes on the
+ * plan's own frames (llr_dev as for polar_batch_run; bits_dev / pm_dev are
+ * scratch outputs), keeps the fastest, reports it (out pointers may be NULL).
+ * Blocks until done. */
 POLAR_API int polar_batch_autotune(polar_batch_t *batch, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
-                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out);
+                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out,
+                                   uint32_t *cta_threads_out);
 /* Capture one run (counter reset + persistent launch) into a CUDA graph owned
  * by the plan, for the given buffers; `stream` must not be the legacy default
  * stream. polar_batch_replay launches that graph on any stream. A later

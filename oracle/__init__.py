@@ -7,7 +7,8 @@ tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
 use it; the product decoder never does.
 
 Modes: ``BITWISE`` (SC-list, length-one leaves), ``SPC4`` (the paper's
-"Dec-SPC-4"), ``SPC_ANY`` ("Dec-SPC-4+").
+"Dec-SPC-4"), ``SPC_ANY`` ("Dec-SPC-4+"); any of them | ``SYSTEMATIC`` for a
+systematic code.
 """
 
 from __future__ import annotations
@@ -19,6 +20,7 @@ import subprocess
 import numpy as np
 
 SPC4, SPC_ANY, BITWISE = 0, 1, 2
+SYSTEMATIC = 0x100   # or-ed into a mode: payload and CRC read from x, not u = x G_N
 F32, I8 = 0, 1
 OP_F, OP_G, OP_COMBINE = 0, 1, 2
 LEAF_RATE0, LEAF_RATE1, LEAF_REP, LEAF_SPC = 11, 12, 13, 14

@@ -19,6 +19,10 @@
  *                       length <= 4 ("Dec-SPC-4", Sec. II-D, III, VI);
  *   mode OR_SPC_ANY  -- the same with SPC nodes of any length ("Dec-SPC-4+").
  *
+ * Any mode may be or-ed with OR_SYSTEMATIC: the code is systematic (the
+ * encoder cited in Sec. I puts payload and CRC in the codeword x itself), so
+ * the final pick reads the information bits from x instead of u = x G_N.
+ *
  * Inner nodes apply F (Eq. (1), min-sum), G (Eq. (2)) and Combine (Eq. (3))
  * to every path independently (Sec. III). Leaves generate candidates from
  * the codeword metric of Eq. (9) (Sec. III-A) with the node rules of
@@ -83,6 +87,7 @@
 #define OR_SPC4 0
 #define OR_SPC_ANY 1
 #define OR_BITWISE 2
+#define OR_SYSTEMATIC 0x100
 
 #define NODE_INNER 0
 #define NODE_RATE0 1
@@ -91,7 +96,7 @@
 #define NODE_SPC 4
 
 typedef struct {
-    int N, n, K, L, dtype, crc_len, mode;
+    int N, n, K, L, dtype, crc_len, mode, systematic, bad_flags;
     uint64_t crc_poly;
     const uint8_t *frozen; /* N bytes, 1 = frozen */
 } ocode_t;
@@ -420,7 +425,8 @@ static void list_free(olist_t *ls, const ocode_t *c) {
     free(ls->spare);
 }
 
-/* Final pick (Sec. II-B, R10, R11). Writes the payload bits of the winner. */
+/* Final pick (Sec. II-B, R10, R11). Writes the payload bits of the winner.
+ * The information bits are those of u = x G_N, or of x for a systematic code. */
 static opick_t final_pick(const olist_t *ls, const ocode_t *c, uint8_t *payload_bits) {
     int N = c->N, k = c->K - c->crc_len;
     uint8_t *u = (uint8_t *)malloc((size_t)N);
@@ -428,7 +434,7 @@ static opick_t final_pick(const olist_t *ls, const ocode_t *c, uint8_t *payload_
     opick_t best = {0.0f, 0, -1};
     for (int p = 0; p < ls->na; ++p) {
         memcpy(u, ls->paths[p].beta, (size_t)N);
-        oracle_polar_transform(u, N);
+        if (!c->systematic) oracle_polar_transform(u, N);
         int t = 0;
         for (int i = 0; i < N; ++i) if (!c->frozen[i]) info[t++] = u[i];
         int ok = 1;
@@ -445,7 +451,7 @@ static opick_t final_pick(const olist_t *ls, const ocode_t *c, uint8_t *payload_
         if (better) { best.pen = pen; best.ok = ok; best.slot = p; }
     }
     memcpy(u, ls->paths[best.slot].beta, (size_t)N);
-    oracle_polar_transform(u, N);
+    if (!c->systematic) oracle_polar_transform(u, N);
     int t = 0;
     for (int i = 0; i < N && t < k; ++i) if (!c->frozen[i]) payload_bits[t++] = u[i];
     free(u);
@@ -458,7 +464,7 @@ static int check_code(const ocode_t *c) {
     if (c->L < 1 || c->L > 1024) return -1;
     if (c->crc_len < 0 || c->crc_len > 63 || c->crc_len > c->K) return -1;
     if (c->dtype != OR_F32 && c->dtype != OR_I8) return -1;
-    if (c->mode < 0 || c->mode > 2) return -1;
+    if (c->mode < 0 || c->mode > 2 || c->bad_flags) return -1;
     return 0;
 }
 
@@ -473,7 +479,9 @@ static void fill_code(ocode_t *c, int N, int K, const uint8_t *frozen, int L, in
     c->dtype = dtype;
     c->crc_len = crc_len;
     c->crc_poly = crc_poly;
-    c->mode = mode;
+    c->mode = mode & 0xFF;
+    c->systematic = (mode & OR_SYSTEMATIC) ? 1 : 0;
+    c->bad_flags = (mode & ~(0xFF | OR_SYSTEMATIC)) != 0;
 }
 
 /* ---------------- exported entry points ---------------- */

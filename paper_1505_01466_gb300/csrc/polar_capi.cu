@@ -155,7 +155,9 @@ struct TreeBuilder {
 // (payload then CRC, MSB first, start 0) is zero iff the CRC matches, and it is
 // linear in x. Column t is the register for the unit vector at information
 // index t; codeword bit i contributes the columns of every information
-// position p of row i of G_N, i.e. every p with (p & ~i) == 0.
+// position p of row i of G_N, i.e. every p with (p & ~i) == 0. A systematic
+// code reads its information bits from x itself: bit i contributes only its
+// own column when i is an information position.
 void build_syndrome(polar_code *c) {
     const uint32_t K = c->K, N = c->N, cl = c->crc_len;
     const uint32_t mask = cl >= 32 ? 0xffffffffu : ((1u << cl) - 1u);
@@ -168,10 +170,11 @@ void build_syndrome(polar_code *c) {
         reg = ((reg << 1) & mask) ^ (top ? poly : 0u);
     }
     std::vector<uint32_t> T(N, 0u);
+    const bool sys = (c->flags & POLAR_SYSTEMATIC) != 0;
     for (uint32_t i = 0; i < N; ++i) {
         uint32_t s = 0;
         for (uint32_t t = 0; t < K; ++t)
-            if ((c->info[t] & ~i) == 0) s ^= col[t];
+            if (sys ? c->info[t] == i : (c->info[t] & ~i) == 0) s ^= col[t];
         T[i] = s;
     }
     c->syn.assign((size_t)(N / 8) * 256, 0u);
@@ -334,6 +337,7 @@ CodeView make_view(const polar_code *code, const LaunchShape &sh) {
     v.k = (int)code->k;
     v.kb = (int)((code->k + 7) / 8);
     v.crc_len = (int)code->crc_len;
+    v.systematic = (code->flags & POLAR_SYSTEMATIC) ? 1 : 0;
     v.lay = sh.lay;
     return v;
 }
@@ -424,7 +428,7 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     if (!frozen_mask) return POLAR_EINVAL;
     if (N < 8 || N > 4096 || (N & (N - 1))) return POLAR_EINVAL;
     if (K > N || crc_len > 32 || (crc_len > 0 && crc_len >= K) || (crc_len == 0 && K == 0)) return POLAR_EINVAL;
-    if ((flags & ~0x1FFu) != 0 || (flags & 0xFFu) > POLAR_NO_SPECIAL_NODES) return POLAR_EINVAL;
+    if ((flags & ~0x3FFu) != 0 || (flags & 0xFFu) > POLAR_NO_SPECIAL_NODES) return POLAR_EINVAL;
     if (L < 1 || L > (uint32_t)kMaxL || (L & (L - 1))) return POLAR_EUNSUPPORTED;
     uint32_t nf = 0;
     for (uint32_t i = 0; i < N; ++i) nf += frozen_mask[i] ? 1u : 0u;
@@ -749,6 +753,7 @@ struct polar_batch {
     // current launch shape
     int warps = 4;
     uint32_t budget = 0;
+    int threads = 128;
     int groups_per_cta = 1;
     uint32_t group_bytes = 0, view_bytes = 0, cta_smem = 0;
     uint64_t gbytes = 0;
@@ -779,9 +784,11 @@ void batch_free_shape(polar_batch *b) {
 
 // Lay out every class for `warps` warps per frame and a shared-memory budget
 // per frame, upload the class table and size the global scratch.
-int batch_shape(polar_batch *b, int warps, uint32_t budget) {
+int batch_shape(polar_batch *b, int warps, uint32_t budget, uint32_t cta_threads = 0) {
     if (warps != 1 && warps != 2 && warps != 4) return POLAR_EINVAL;
-    const int gpc = 4 / warps;
+    if (cta_threads == 0) cta_threads = 128;
+    if (cta_threads % (32u * (uint32_t)warps) != 0 || cta_threads > (uint32_t)kMaxCtaThreads) return POLAR_EINVAL;
+    const int gpc = (int)cta_threads / (32 * warps);
     const uint32_t view_bytes = al16((uint32_t)sizeof(CodeView) + 16u);
     if (budget == 0) budget = (kMaxSmemPerCta / (warps == 4 ? 4u : (warps == 2 ? 6u : 8u))) & ~15u;
     budget = std::min<uint32_t>(budget, kMaxSmemPerCta / gpc - view_bytes);
@@ -802,7 +809,7 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget) {
     const uint32_t group_bytes = view_bytes + gb;
     const uint32_t cta_smem = group_bytes * (uint32_t)gpc;
     if (cta_smem > kMaxSmemPerCta) return POLAR_EINVAL;
-    const int occ = occupancy_batch(b->dtype, warps, cta_smem);
+    const int occ = occupancy_batch(b->dtype, warps, cta_smem, (int)cta_threads);
     if (occ <= 0) return POLAR_ECUDA;
     batch_free_shape(b);
     for (size_t c = 0; c < b->codes.size(); ++c) {
@@ -822,6 +829,7 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget) {
     }
     b->warps = warps;
     b->budget = budget;
+    b->threads = (int)cta_threads;
     b->groups_per_cta = gpc;
     b->group_bytes = group_bytes;
     b->view_bytes = view_bytes;
@@ -850,7 +858,8 @@ int batch_launch(polar_batch *b, const void *llr, uint8_t *bits, float *pm, uint
     p.group_bytes = b->group_bytes;
     p.view_bytes = b->view_bytes;
     p.groups_per_cta = b->groups_per_cta;
-    return launch_batch(b->dtype, b->warps, p, b->grid, b->cta_smem, st) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+    return launch_batch(b->dtype, b->warps, p, b->grid, b->cta_smem, b->threads, st) == cudaSuccess ? POLAR_OK
+                                                                                                 : POLAR_ECUDA;
 }
 
 }  // namespace
@@ -935,27 +944,28 @@ int polar_batch_run(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, fl
     return batch_launch(b, llr_dev, bits_dev, pm_dev, ok_dev, slot_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
-int polar_batch_set_launch(polar_batch_t *b, uint32_t warps_per_frame, uint32_t smem_budget) {
+int polar_batch_set_launch(polar_batch_t *b, uint32_t warps_per_frame, uint32_t smem_budget, uint32_t cta_threads) {
     if (!b) return POLAR_EINVAL;
-    return batch_shape(b, (int)warps_per_frame, smem_budget);
+    return batch_shape(b, (int)warps_per_frame, smem_budget, cta_threads);
 }
 
 int polar_batch_autotune(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, float *pm_dev,
-                         polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out) {
+                         polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out, uint32_t *cta_out) {
     if (!b || !llr_dev || !bits_dev || !pm_dev) return POLAR_EINVAL;
     if (b->n_frames == 0) return POLAR_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    static const uint32_t budgets[] = {0u, 110000u, 75000u, 56000u, 44000u, 36000u, 28000u, 20000u, 14000u, 10000u,
-                                       7000u};
+    // a coarser grid than the plain form's: every timing runs the whole plan
+    static const uint32_t budgets[] = {0u, 28000u, 14000u, 7000u};
     float best = 1e30f;
     int bw = 0;
-    uint32_t bb = 0;
-    for (int w : {4, 2, 1}) {
+    uint32_t bb = 0, bt = 0;
+    for (int w : {2, 1}) {
+      for (uint32_t t : {128u, 256u, 512u}) {
         for (uint32_t bud : budgets) {
-            if (batch_shape(b, w, bud) != POLAR_OK) continue;
+            if (batch_shape(b, w, bud, t) != POLAR_OK) continue;
             if (batch_launch(b, llr_dev, bits_dev, pm_dev, nullptr, nullptr, st) != POLAR_OK) continue;
             cudaEventRecord(e0, st);
             const int rc = batch_launch(b, llr_dev, bits_dev, pm_dev, nullptr, nullptr, st);
@@ -963,15 +973,17 @@ int polar_batch_autotune(polar_batch_t *b, const void *llr_dev, uint8_t *bits_de
             float ms = 0.f;
             if (cudaEventSynchronize(e1) != cudaSuccess || rc != POLAR_OK) continue;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; bw = w; bb = bud; }
+            if (ms < best) { best = ms; bw = w; bb = bud; bt = t; }
         }
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (bw == 0) return POLAR_ECUDA;
     if (warps_out) *warps_out = (uint32_t)bw;
     if (budget_out) *budget_out = bb;
-    return batch_shape(b, bw, bb);
+    if (cta_out) *cta_out = bt;
+    return batch_shape(b, bw, bb, bt);
 }
 
 int polar_batch_capture(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, float *pm_dev, uint8_t *ok_dev,
@@ -1313,7 +1325,7 @@ int srv_launch(polar_server *s, int i) {
     uint32_t group_bytes, cta_smem;
     int gpc;
     srv_shape(s, d, group_bytes, cta_smem, gpc);
-    const int occ = occupancy_batch(d, s->warps, cta_smem);
+    const int occ = occupancy_batch(d, s->warps, cta_smem, 128);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * s->sm_count;
     const uint64_t need = (n_items + gpc - 1) / gpc;
@@ -1342,7 +1354,7 @@ int srv_launch(polar_server *s, int i) {
     p.group_bytes = group_bytes;
     p.view_bytes = srv_view_bytes();
     p.groups_per_cta = gpc;
-    okc &= launch_batch(d, s->warps, p, (int)grid, cta_smem, st) == cudaSuccess;
+    okc &= launch_batch(d, s->warps, p, (int)grid, cta_smem, 128, st) == cudaSuccess;
     for (SrvReq *r : take) {
         const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
         okc &= cudaMemcpyAsync(s->h_arena + bits_base, s->d_arena + bits_base, r->bits_sz, cudaMemcpyDeviceToHost,

@@ -88,6 +88,7 @@ struct CodeView {
     const unsigned long long *desc;// subtree descriptors, two words each
     int n_ops;
     int N, n, L, K, k, kb, crc_len;
+    int systematic;                // payload read from x, not from u = x G_N
     Layout lay;
 };
 
@@ -150,7 +151,9 @@ int occupancy(int dtype, const LaunchShape &shape);
 // Indices of the frames whose CRC flag is 0 (order unspecified) and their count.
 cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n_frames, uint32_t *idx, uint32_t *cnt,
                                 cudaStream_t stream);
-// Batched form: 128-thread CTAs of `warps`-warp groups with `smem` bytes each.
-cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, cudaStream_t stream);
-int occupancy_batch(int dtype, int warps, uint32_t smem);
+// Batched form: CTAs of `threads` threads (groups of `warps` warps) with
+// `smem` bytes of shared memory.
+cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
+                         cudaStream_t stream);
+int occupancy_batch(int dtype, int warps, uint32_t smem, int threads);
 }  // namespace polar

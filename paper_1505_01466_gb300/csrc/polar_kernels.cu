@@ -1114,7 +1114,8 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
         }
         const int win = (int)(key & 0xFFu);
         const uint32_t okw = (uint32_t)(key >> 63) ^ 1u;
-        // u = x G_N for the winner (natural-order butterflies)
+        // u = x G_N for the winner (natural-order butterflies); a systematic
+        // code keeps x, whose information positions carry payload and CRC
         const uint32_t *xw = br + win * bwn;
         const int R = bwn > 32 ? bwn >> 5 : 1;
         uint32_t U[4];
@@ -1123,26 +1124,28 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
             const int w = lane + 32 * r;
             U[r] = (r < R && w < bwn) ? xw[w] : 0u;
         }
-        const uint32_t M[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+        if (!cv.systematic) {
+            const uint32_t M[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < 4; ++r) {
 #pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                const int hb = 1 << e;
-                if (hb < N) U[r] ^= (U[r] >> hb) & M[e];
+                for (int e = 0; e < 5; ++e) {
+                    const int hb = 1 << e;
+                    if (hb < N) U[r] ^= (U[r] >> hb) & M[e];
+                }
             }
-        }
-        for (int d = 1; d < bwn; d <<= 1) {
-            if (d >= 32) {
-                const int dr = d >> 5;
+            for (int d = 1; d < bwn; d <<= 1) {
+                if (d >= 32) {
+                    const int dr = d >> 5;
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (r < R && !(r & dr) && r + dr < 4) U[r] ^= U[r + dr];
-            } else {
+                    for (int r = 0; r < 4; ++r)
+                        if (r < R && !(r & dr) && r + dr < 4) U[r] ^= U[r + dr];
+                } else {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const uint32_t v = __shfl_down_sync(FULL, U[r], d);
-                    if (!(lane & d)) U[r] ^= v;
+                    for (int r = 0; r < 4; ++r) {
+                        const uint32_t v = __shfl_down_sync(FULL, U[r], d);
+                        if (!(lane & d)) U[r] ^= v;
+                    }
                 }
             }
         }
@@ -1220,7 +1223,7 @@ __global__ void crc_failures_kernel(const uint8_t *ok, uint32_t n, uint32_t *idx
 // the group's shared memory when it changes. When all groups of the CTA got a
 // frame of the same code they run it in lockstep, as in the plain form.
 template <typename T, int W>
-__global__ void __launch_bounds__(128) batch_kernel(const BatchParams B) {
+__global__ void __launch_bounds__(kMaxCtaThreads) batch_kernel(const BatchParams B) {
     constexpr int GT = W * 32;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int gidx = threadIdx.x / GT;
@@ -1282,19 +1285,19 @@ int occ_one(const LaunchShape &sh) {
 }
 
 template <typename T, int W>
-cudaError_t launch_batch_one(const BatchParams &b, int grid, uint32_t smem, cudaStream_t st) {
+cudaError_t launch_batch_one(const BatchParams &b, int grid, uint32_t smem, int threads, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    batch_kernel<T, W><<<grid, 128, smem, st>>>(b);
+    batch_kernel<T, W><<<grid, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
 template <typename T, int W>
-int occ_batch_one(uint32_t smem) {
+int occ_batch_one(uint32_t smem, int threads) {
     if (cudaFuncSetAttribute(batch_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T, W>, 128, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T, W>, threads, smem) != cudaSuccess) return 0;
     return nb;
 }
 
@@ -1308,28 +1311,29 @@ cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n, uint32_t *idx, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, cudaStream_t st) {
+cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
+                         cudaStream_t st) {
     if (dtype == 0) {
-        if (warps == 1) return launch_batch_one<float, 1>(b, grid, smem, st);
-        if (warps == 2) return launch_batch_one<float, 2>(b, grid, smem, st);
-        if (warps == 4) return launch_batch_one<float, 4>(b, grid, smem, st);
+        if (warps == 1) return launch_batch_one<float, 1>(b, grid, smem, threads, st);
+        if (warps == 2) return launch_batch_one<float, 2>(b, grid, smem, threads, st);
+        if (warps == 4) return launch_batch_one<float, 4>(b, grid, smem, threads, st);
     } else {
-        if (warps == 1) return launch_batch_one<int8_t, 1>(b, grid, smem, st);
-        if (warps == 2) return launch_batch_one<int8_t, 2>(b, grid, smem, st);
-        if (warps == 4) return launch_batch_one<int8_t, 4>(b, grid, smem, st);
+        if (warps == 1) return launch_batch_one<int8_t, 1>(b, grid, smem, threads, st);
+        if (warps == 2) return launch_batch_one<int8_t, 2>(b, grid, smem, threads, st);
+        if (warps == 4) return launch_batch_one<int8_t, 4>(b, grid, smem, threads, st);
     }
     return cudaErrorInvalidValue;
 }
 
-int occupancy_batch(int dtype, int warps, uint32_t smem) {
+int occupancy_batch(int dtype, int warps, uint32_t smem, int threads) {
     if (dtype == 0) {
-        if (warps == 1) return occ_batch_one<float, 1>(smem);
-        if (warps == 2) return occ_batch_one<float, 2>(smem);
-        if (warps == 4) return occ_batch_one<float, 4>(smem);
+        if (warps == 1) return occ_batch_one<float, 1>(smem, threads);
+        if (warps == 2) return occ_batch_one<float, 2>(smem, threads);
+        if (warps == 4) return occ_batch_one<float, 4>(smem, threads);
     } else {
-        if (warps == 1) return occ_batch_one<int8_t, 1>(smem);
-        if (warps == 2) return occ_batch_one<int8_t, 2>(smem);
-        if (warps == 4) return occ_batch_one<int8_t, 4>(smem);
+        if (warps == 1) return occ_batch_one<int8_t, 1>(smem, threads);
+        if (warps == 2) return occ_batch_one<int8_t, 2>(smem, threads);
+        if (warps == 4) return occ_batch_one<int8_t, 4>(smem, threads);
     }
     return 0;
 }

@@ -231,12 +231,24 @@ def quantize_i8(llr: np.ndarray, scale: float = 4.0) -> np.ndarray:
     return np.clip(q, -127, 127).astype(np.int8)
 
 
+def systematic_encode(v: np.ndarray, frozen_mask: np.ndarray) -> np.ndarray:
+    """Systematic polar encoding: v holds the information bits at the
+    information positions (zeros elsewhere); x = ((v G_N) with the frozen
+    positions cleared) G_N. For information sets closed under the polar
+    order (those of density evolution are) x equals v at every information
+    position."""
+    w = polar_transform(v)
+    w[..., np.asarray(frozen_mask) == 1] = 0
+    return polar_transform(w)
+
+
 def make_frames(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: float,
-                n_frames: int, seed: int, noiseless: bool = False) -> Frames:
+                n_frames: int, seed: int, noiseless: bool = False, systematic: bool = False) -> Frames:
     """Random codewords of the polar-CRC code sent over BPSK-AWGN.
 
     Uses numpy's counter-based Philox generator keyed by ``seed``. With
-    ``noiseless`` the channel output is exactly +-1 (LLR = +-2/sigma^2).
+    ``noiseless`` the channel output is exactly +-1 (LLR = +-2/sigma^2). With
+    ``systematic`` the payload and CRC are placed in the codeword itself.
     """
     frozen_mask = np.asarray(frozen_mask, dtype=np.uint8)
     N = frozen_mask.size
@@ -251,7 +263,7 @@ def make_frames(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: f
     u = np.zeros((n_frames, N), dtype=np.uint8)
     u[:, info[:k]] = payload
     u[:, info[k:]] = crc
-    x = polar_transform(u)
+    x = systematic_encode(u, frozen_mask) if systematic else polar_transform(u)
     rate = k / N if k > 0 else K / N if K > 0 else 1.0 / N
     sig = sigma_for(ebn0_db, rate)
     y = 1.0 - 2.0 * x.astype(np.float64)
@@ -263,7 +275,8 @@ def make_frames(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: f
 
 
 def make_frames_chunked(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: float,
-                        n_frames: int, seed: int, chunk: int = 8192, threads: int | None = None) -> Frames:
+                        n_frames: int, seed: int, chunk: int = 8192, threads: int | None = None,
+                        systematic: bool = False) -> Frames:
     """make_frames over chunks of ``chunk`` frames generated on host threads.
 
     Chunk c is ``make_frames(..., chunk, seed=(seed << 20) + c)``; the result is
@@ -276,7 +289,8 @@ def make_frames_chunked(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, eb
     threads = threads or min(len(sizes), os.cpu_count() or 1)
     with ThreadPoolExecutor(max_workers=threads) as ex:
         parts = list(ex.map(lambda c: make_frames(frozen_mask, crc_len, crc_poly, ebn0_db, sizes[c],
-                                                  seed=(seed << 20) + c), range(len(sizes))))
+                                                  seed=(seed << 20) + c, systematic=systematic),
+                            range(len(sizes))))
     return Frames(payload=np.concatenate([p.payload for p in parts]),
                   codeword=np.concatenate([p.codeword for p in parts]),
                   llr_f32=np.concatenate([p.llr_f32 for p in parts]),

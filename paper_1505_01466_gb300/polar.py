@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpolar_gb300.so")
 POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
 POLAR_EUNSUPPORTED, POLAR_ETIMEDOUT, POLAR_EBUSY = -4, -5, -6
 LLR_F32, LLR_I8 = 0, 1
-SPC_MAX_4, SPC_ANY, NO_SPECIAL_NODES, HOST_ONLY = 0, 1, 2, 0x100
+SPC_MAX_4, SPC_ANY, NO_SPECIAL_NODES, HOST_ONLY, SYSTEMATIC = 0, 1, 2, 0x100, 0x200
 
 # Every symbol include/polar.h declares.
 EXPORTED = [
@@ -114,8 +114,9 @@ def _lib():
         lib.polar_batch_destroy.argtypes = [vp]
         lib.polar_batch_layout.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), vp, vp]
         lib.polar_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
-        lib.polar_batch_set_launch.argtypes = [vp, u32, u32]
-        lib.polar_batch_autotune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        lib.polar_batch_set_launch.argtypes = [vp, u32, u32, u32]
+        lib.polar_batch_autotune.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(u32), ctypes.POINTER(u32),
+                                             ctypes.POINTER(u32)]
         lib.polar_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.polar_batch_replay.argtypes = [vp, vp]
         lib.polar_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
@@ -158,11 +159,12 @@ class PolarCode:
 
     frozen_mask: N bytes, nonzero = frozen. crc_len / crc_poly: the outer
     CRC (MSB-first, register starts at 0). L: list size (power of two <= 32).
-    mode: SPC_MAX_4 (default), SPC_ANY or NO_SPECIAL_NODES.
+    mode: SPC_MAX_4 (default), SPC_ANY or NO_SPECIAL_NODES. systematic: the
+    payload and CRC sit in the codeword x (read from x, not from u = x G_N).
     """
 
     def __init__(self, frozen_mask, crc_len: int = 0, crc_poly: int = 0, L: int = 8,
-                 mode: int = SPC_MAX_4, host_only: bool = False):
+                 mode: int = SPC_MAX_4, host_only: bool = False, systematic: bool = False):
         mask = np.ascontiguousarray(np.asarray(frozen_mask).astype(np.uint8) != 0, dtype=np.uint8)
         self.N = int(mask.size)
         self.K = int((mask == 0).sum())
@@ -170,7 +172,7 @@ class PolarCode:
         self.k = self.K - self.crc_len
         self.L = int(L)
         self.frozen = mask
-        flags = int(mode) | (HOST_ONLY if host_only else 0)
+        flags = int(mode) | (HOST_ONLY if host_only else 0) | (SYSTEMATIC if systematic else 0)
         h = ctypes.c_void_p()
         st = _lib().polar_code_create(ctypes.byref(h), self.N, self.K, mask.ctypes.data_as(ctypes.c_void_p),
                                       self.crc_len, int(crc_poly), self.L, flags)
@@ -325,18 +327,20 @@ class PolarBatch:
         _check(_lib().polar_batch_get_info(self._h, ctypes.byref(bi)), "polar_batch_get_info")
         return {name: int(getattr(bi, name)) for name, _ in BatchInfo._fields_}
 
-    def set_launch(self, warps_per_frame: int, smem_budget: int = 0):
-        _check(_lib().polar_batch_set_launch(self._h, warps_per_frame, smem_budget), "polar_batch_set_launch")
+    def set_launch(self, warps_per_frame: int, smem_budget: int = 0, cta_threads: int = 0):
+        _check(_lib().polar_batch_set_launch(self._h, warps_per_frame, smem_budget, cta_threads),
+               "polar_batch_set_launch")
 
     def run(self, llr, bits, pm, ok=None, slot=None, stream=None):
         _check(_lib().polar_batch_run(self._h, _ptr(llr), _ptr(bits), _ptr(pm), _ptr(ok), _ptr(slot),
                                       _stream_handle(stream)), "polar_batch_run")
 
     def autotune(self, llr, bits, pm, stream=None):
-        w, b = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        w, b, t = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
         _check(_lib().polar_batch_autotune(self._h, _ptr(llr), _ptr(bits), _ptr(pm), _stream_handle(stream),
-                                           ctypes.byref(w), ctypes.byref(b)), "polar_batch_autotune")
-        return int(w.value), int(b.value)
+                                           ctypes.byref(w), ctypes.byref(b), ctypes.byref(t)),
+               "polar_batch_autotune")
+        return int(w.value), int(b.value), int(t.value)
 
     def capture(self, llr, bits, pm, ok=None, slot=None, stream=None):
         _check(_lib().polar_batch_capture(self._h, _ptr(llr), _ptr(bits), _ptr(pm), _ptr(ok), _ptr(slot),

@@ -48,7 +48,7 @@ def _mixed(polar, dtype, n_frames, seed):
     return codes, frozen, fc, rows
 
 
-def _run_batch(torch, polar, codes, fc, rows, dtype, graph=False, tune=False):
+def _run_batch(torch, polar, codes, fc, rows, dtype, graph=False, tune=False, launch=None):
     dt = polar.LLR_I8 if dtype == "i8" else polar.LLR_F32
     b = polar.PolarBatch(codes, fc, dt)
     llr_bytes, bits_bytes, lo, bo = b.layout()
@@ -60,6 +60,8 @@ def _run_batch(torch, polar, codes, fc, rows, dtype, graph=False, tune=False):
     pm = torch.zeros(F, dtype=torch.float32, device="cuda")
     ok = torch.zeros(F, dtype=torch.uint8, device="cuda")
     slot = torch.zeros(F, dtype=torch.int32, device="cuda")
+    if launch is not None:
+        b.set_launch(*launch)
     if tune:
         b.autotune(llr, bits, pm)
     if graph:
@@ -120,3 +122,15 @@ def test_batch_graph_replay_and_autotune(env):
         out = _run_batch(torch, polar, codes, fc, rows, "i8", graph=graph, tune=tune)
         for a, b in zip(out, ref):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("launch", [(1, 7000, 512), (1, 0, 256), (2, 20000, 256), (4, 0, 512)])
+def test_batch_cta_sizes_and_lockstep_units(env, launch):
+    # CTAs of several groups: units whose frames share a code run in lockstep,
+    # mixed units (class boundaries, the ragged end) run without it
+    torch, polar = env
+    codes, frozen, fc, rows = _mixed(polar, "i8", 613, seed=6)
+    ref = _run_batch(torch, polar, codes, fc, rows, "i8")
+    out = _run_batch(torch, polar, codes, fc, rows, "i8", launch=launch)
+    for a, b in zip(out, ref):
+        assert np.array_equal(a, b)

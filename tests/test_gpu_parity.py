@@ -218,3 +218,23 @@ def test_host_buffer_decode_matches_device_decode(torch_cuda, oracle_mod, dtype)
     o = oracle_mod.decode(fr, 8, x[-40:], 32, I.CRC32_POLY, 0, n_threads=NT)
     assert_parity(tuple(t[-40:].numpy() for t in ref), o, dtype, "host decode tail")
     code.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("case", [(256, 128, 8, 4, 2.0, 2.0), (1024, 860, 32, 8, 4.0, 3.25), (2048, 1723, 32, 32, 4.0, 3.5)])
+def test_systematic_codes(torch_cuda, oracle_mod, dtype, case):
+    from paper_1505_01466_gb300.polar import PolarCode
+    N, K, crc, L, design, snr = case
+    poly = I.CRC8_POLY if crc == 8 else I.CRC32_POLY
+    fr = I.ga_frozen_mask(N, K, design, (K - crc) / N)
+    f = I.make_frames(fr, crc, poly, snr, 200 if N < 2048 else 64, seed=N + L, systematic=True)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    for mode in (0, 2):
+        code = PolarCode(fr, crc, poly, L, mode=mode, systematic=True)
+        g = gpu_decode(torch_cuda, code, llr)
+        code.close()
+        o = oracle_mod.decode(fr, L, llr, crc, poly, mode | oracle_mod.SYSTEMATIC, n_threads=NT)
+        assert_parity(g, o, dtype, f"systematic ({N},{K}) L={L} mode={mode}")
+        # most frames decode to their payload
+        got = I.unpack_bits_lsb(g[0], K - crc)
+        assert (got == f.payload).all(axis=1).mean() > 0.5

@@ -142,3 +142,17 @@ def test_chunked_frames_are_the_concatenated_chunks():
     assert np.array_equal(full.llr_f32, one.llr_f32) and full.payload.shape == (50, 62)
     c2 = I.make_frames(fr, 8, I.CRC8_POLY, 2.0, 16, seed=(3 << 20) + 2)
     assert np.array_equal(full.llr_i8[32:48], c2.llr_i8) and np.array_equal(full.payload[32:48], c2.payload)
+
+
+def test_systematic_encoder_places_data_in_the_codeword():
+    for N, K, db in ((64, 40, 3.0), (1024, 860, 4.0), (2048, 1723, 4.0)):
+        fr = I.ga_frozen_mask(N, K, db)
+        f = I.make_frames(fr, 32, I.CRC32_POLY, db, 20, seed=N, noiseless=True, systematic=True)
+        info = I.info_positions(fr)
+        x = f.codeword
+        assert np.array_equal(x[:, info[: K - 32]], f.payload)          # payload in x itself
+        assert not I.crc_bits(x[:, info], 32, I.CRC32_POLY).any()        # CRC in x too
+        assert not I.polar_transform(x)[:, fr == 1].any()                # still a codeword of the code
+        # the non-systematic encoding of the same data differs (but is also a codeword)
+        g = I.make_frames(fr, 32, I.CRC32_POLY, db, 20, seed=N, noiseless=True)
+        assert np.array_equal(g.payload, f.payload) and not np.array_equal(g.codeword, f.codeword)

@@ -315,3 +315,24 @@ def test_adaptive_decoder_properties(oracle_mod):
               f.payload).all(axis=1)
     right = (I.unpack_bits_lsb(b, 120) == f.payload).all(axis=1)
     assert (right | ~right8 | (ok1 == 1)).all()
+
+
+@pytest.mark.parametrize("mode", ["SPC4", "BITWISE"])
+def test_systematic_mode(oracle_mod, mode):
+    # noiseless systematic frames decode to their payload; a non-systematic
+    # decoder of the same frames finds the same codeword, whose u is not the payload
+    fr = I.ga_frozen_mask(256, 128, 2.0, 96 / 256)
+    m = getattr(oracle_mod, mode)
+    clean = I.make_frames(fr, 32, I.CRC32_POLY, 2.0, 8, seed=2, noiseless=True, systematic=True)
+    b, pm, ok, _ = oracle_mod.decode(fr, 4, clean.llr_f32, 32, I.CRC32_POLY, m | oracle_mod.SYSTEMATIC)
+    assert ok.all() and (pm == 0).all() and np.array_equal(I.unpack_bits_lsb(b, 96), clean.payload)
+    b2, _, ok2, _ = oracle_mod.decode(fr, 4, clean.llr_f32, 32, I.CRC32_POLY, m)
+    info = I.info_positions(fr)
+    u = I.polar_transform(clean.codeword)
+    assert np.array_equal(I.unpack_bits_lsb(b2, 96), u[:, info[:96]])
+    # noisy frames: the systematic payload is x at the information positions of
+    # the word the decoder returns, and errors are no more frequent than u-errors
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 2.0, 300, seed=3, systematic=True)
+    b, _, ok, _ = oracle_mod.decode(fr, 8, f.llr_f32, 32, I.CRC32_POLY, m | oracle_mod.SYSTEMATIC)
+    err = (I.unpack_bits_lsb(b, 96) != f.payload).any(axis=1)
+    assert err.mean() < 0.5 and (ok[~err] == 1).all()
