@@ -34,6 +34,7 @@
 // use saturated G and exact integer penalties.
 
 #include <algorithm>
+#include <type_traits>
 
 #include "polar_internal.h"
 
@@ -378,12 +379,13 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
         k[0] = Arith<T>::mk(ps + (flag ? x1[0] : x0[0]), s * 2 + 0);
         k[1] = Arith<T>::mk(ps + (flag ? x0[0] : x1[0]), s * 2 + 1);
     } else {
-        // least reliable positions by (|a|, index): keys |a| << 4 | i
-        unsigned long long lk[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+        // least reliable positions by (|a|, index): keys |a| << 4 | i (32 bits hold them for int8)
+        typedef typename std::conditional<sizeof(T) == 1, uint32_t, unsigned long long>::type LKT;
+        LKT lk[4] = {~(LKT)0, ~(LKT)0, ~(LKT)0, ~(LKT)0};
         if (nv <= 4) {
             // a sorting network over the (at most four) keys
 #pragma unroll
-            for (int i = 0; i < nv; ++i) lk[i] = ((unsigned long long)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
+            for (int i = 0; i < nv; ++i) lk[i] = ((LKT)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
             if (nv >= 2) ce(lk[0], lk[1]);
             if (nv == 4) {
                 ce(lk[2], lk[3]); ce(lk[0], lk[2]); ce(lk[1], lk[3]); ce(lk[1], lk[2]);
@@ -393,11 +395,11 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
             const int R = (J < 2 || type == OP_R1) ? 2 : 4;
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
-                const unsigned long long prev = r > 0 ? lk[r - 1] : 0ull;
-                unsigned long long best = ~0ull;
+                const LKT prev = r > 0 ? lk[r - 1] : (LKT)0;
+                LKT best = ~(LKT)0;
 #pragma unroll
                 for (int i = 0; i < nv; ++i) {
-                    const unsigned long long v = ((unsigned long long)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
+                    const LKT v = ((LKT)Arith<T>::absbits(st.a[o + i]) << 4) | (unsigned)i;
                     if ((r == 0 || v > prev) && v < best) best = v;
                 }
                 if (r == 0) lk[0] = best; else if (r == 1) lk[1] = best; else if (r == 2) lk[2] = best; else lk[3] = best;
