@@ -36,6 +36,11 @@ DESIGN_DB, EBN0_DB = 4.0, 4.0
 FRAMES = 1 << 20
 UNIQUE = 1 << 16
 METRIC = "info Gbps at (2048,1723) L=32 on 1 GB300, batched vs plain; FER match; p99 lat"
+# DRAM bytes per frame of decode_kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture over 32768 frames of this workload, 1 warp per frame, 7000-byte budget; the
+# capture is summarised in profiles/decode_kernel_2048_1723_L32.md). Valid only for the
+# kernel source with this sha1; any other source reports traffic null.
+NCU_TRAFFIC = {"kernel_sha1": "2480a4675ef7fa94ab61ecaa39914e06378548e7", "f32": 1713090, "i8": 181301}
 UNIT = "Gbps"
 
 
@@ -614,11 +619,17 @@ def run_ours(args):
     achieved = ops_frame * args.frames / kernel_s / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1505_01466_gb300", "csrc", "polar_kernels.cu"), "rb") as fh:
+        ksha = hashlib.sha1(fh.read()).hexdigest()
+    traffic = NCU_TRAFFIC[args.dtype] * args.frames if ksha == NCU_TRAFFIC["kernel_sha1"] else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic,
                 "note": f"ops counted per frame along the schedule ({ops_frame}); peak = {sms} SMs x 128 lanes x "
                         f"{pk.get('sm_max_mhz', 2070.0)} MHz ({src} clock); HBM side: "
-                        f"{N * llr.element_size() * args.frames / kernel_s / 1e9:.1f} GB/s of {pk.get('hbm_gbs')}"}
+                        f"{N * llr.element_size() * args.frames / kernel_s / 1e9:.1f} GB/s of {pk.get('hbm_gbs')}; "
+                        f"traffic = ncu DRAM bytes per frame (32768-frame capture) x frames per launch, "
+                        f"{(traffic or 0) / kernel_s / 1e9:.0f} GB/s implied"}
 
     # the other LLR type on the same frames (device-resident timing only)
     other = {}

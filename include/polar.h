@@ -92,15 +92,21 @@ enum polar_flags {
  *                Read during the call only.
  *   crc_len      0 (no CRC: the best path wins) or 1..32.
  *   crc_poly     generator polynomial without the x^crc_len term.
- *   L            list size, a power of two, 1 <= L <= 32 (L = 1 is Fast-SSC
- *                decoding, Sec. V).
+ *   L            list size, a power of two, 1 <= L <= 128 (L = 1 is Fast-SSC
+ *                decoding, Sec. V). L <= 32 runs the warp-per-frame kernels;
+ *                L = 64 and 128 (the paper's Fig. 3 uses L = 128) run one CTA
+ *                of L threads per frame over the fully unrolled schedule, with
+ *                every stage in global scratch. Wide codes decode through
+ *                polar_list_decode, polar_list_decode_host and
+ *                polar_adaptive_decode; set_launch, the allocation-free entry,
+ *                batch plans and servers return POLAR_EUNSUPPORTED for them.
  *   flags        one node-set value, optionally | POLAR_HOST_ONLY and/or
  *                POLAR_SYSTEMATIC.
  * Builds the decoding tree (Sec. II-D: the largest Rate-0 / Rate-1 /
  * repetition / SPC sub-tree from the root down), the unrolled operation list
  * (Listing 2) and the CRC tables, and copies them to the current device.
  * Errors: POLAR_EINVAL (bad N, K, mask, crc_len, flags, NULL out),
- * POLAR_EUNSUPPORTED (L not a power of two in 1..32), POLAR_ENOMEM,
+ * POLAR_EUNSUPPORTED (L not a power of two in 1..128), POLAR_ENOMEM,
  * POLAR_ECUDA. On error *out is set to NULL. */
 POLAR_API int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t *frozen_mask,
                       uint32_t crc_len, uint64_t crc_poly, uint32_t L, uint32_t flags);

@@ -1,6 +1,6 @@
 """Build ``libpolar_gb300.so`` in-tree with nvcc for sm_103a.
 
-The two translation units (host runtime, kernels) compile in parallel and
+The three translation units (host runtime, narrow and wide kernels) compile in parallel and
 are linked into one shared library next to this file. No CMake, no torch
 extension machinery: the library has a plain C ABI (include/polar.h).
 """
@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpolar_gb300.so")
-SOURCES = ["polar_capi.cu", "polar_kernels.cu"]
+SOURCES = ["polar_capi.cu", "polar_kernels.cu", "polar_wide.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -45,6 +45,10 @@ struct polar_code {
     uint16_t *d_info = nullptr;
     unsigned long long *d_desc = nullptr;
     LaunchShape shape[2];
+    // L = 64 / 128: the wide kernel over the fully unrolled schedule
+    bool wide = false;
+    uint32_t *d_xops = nullptr;
+    uint64_t wide_gbytes[2] = {0, 0};
 };
 
 namespace {
@@ -291,6 +295,8 @@ void free_device(polar_code *c) {
     if (c->d_syn) cudaFree(c->d_syn);
     if (c->d_info) cudaFree(c->d_info);
     if (c->d_desc) cudaFree(c->d_desc);
+    if (c->d_xops) cudaFree(c->d_xops);
+    c->d_xops = nullptr;
     c->d_syn = nullptr;
     c->d_info = nullptr;
     c->d_desc = nullptr;
@@ -374,6 +380,70 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
+// ---- wide lists ---------------------------------------------------------------
+// Every stage of every path in the CTA's global scratch: alpha stages 0..n-1
+// (L rows of 2^j elements), left betas 0..n-1, the right/root beta, the channel.
+WideView &wide_view(const polar_code *c, int dtype, WideView &v) {
+    std::memset(&v, 0, sizeof(v));
+    const uint64_t es = dtype == POLAR_LLR_I8 ? 1 : 4;
+    uint64_t off = 0;
+    for (uint32_t j = 0; j < c->n; ++j) { v.galpha[j] = off; off = al256(off + (uint64_t)c->L * (1u << j) * es); }
+    for (uint32_t j = 0; j < c->n; ++j) {
+        v.gbl[j] = off;
+        off = al256(off + (uint64_t)c->L * 4u * (uint64_t)beta_words((int)j));
+    }
+    v.gbr = off; off = al256(off + (uint64_t)c->L * 4u * (uint64_t)beta_words((int)c->n));
+    v.gchan = off; off = al256(off + (uint64_t)c->N * es);
+    v.gbytes = off;
+    v.xops = c->d_xops;
+    v.syn = c->d_syn;
+    v.info = c->d_info;
+    v.n_xops = (int)c->xops.size();
+    v.N = (int)c->N;
+    v.n = (int)c->n;
+    v.L = (int)c->L;
+    v.K = (int)c->K;
+    v.k = (int)c->k;
+    v.kb = (int)((c->k + 7) / 8);
+    v.crc_len = (int)c->crc_len;
+    v.systematic = (c->flags & POLAR_SYSTEMATIC) ? 1 : 0;
+    return v;
+}
+
+int decode_wide(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
+                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx, const uint32_t *frame_cnt) {
+    WideParams p;
+    std::memset(&p, 0, sizeof(p));
+    wide_view(code, dtype, p.v);
+    const int occ = occupancy_wide(dtype, (int)code->L, (int)code->n);
+    if (occ <= 0) return POLAR_ECUDA;
+    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
+    if (grid > n_frames) grid = n_frames;
+    p.llr = llr;
+    p.bits = bits;
+    p.pm = pm;
+    p.ok = ok;
+    p.slot = slot;
+    p.n_frames = n_frames;
+    p.frame_idx = frame_idx;
+    p.frame_cnt = frame_cnt;
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, (size_t)(grid * p.v.gbytes), st) != cudaSuccess) return POLAR_ENOMEM;
+    p.scratch = (uint8_t *)scratch;
+    cudaError_t e = launch_wide(dtype, p, (int)grid, st);
+    cudaFreeAsync(scratch, st);
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+// The installed shape of the narrow kernels, or the wide kernel.
+int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
+               uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx = nullptr,
+               const uint32_t *frame_cnt = nullptr) {
+    if (code->wide) return decode_wide(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
+    return decode_shape(code, dtype, code->shape[dtype], llr, n_frames, bits, pm, ok, slot, st, frame_idx,
+                        frame_cnt);
+}
+
 // ---- allocation-free decoding ----------------------------------------------
 // Some callers cannot allocate device memory while they decode: code running
 // inside a captured CUDA graph that must not contain allocation nodes, real-
@@ -429,7 +499,7 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     if (N < 8 || N > 4096 || (N & (N - 1))) return POLAR_EINVAL;
     if (K > N || crc_len > 32 || (crc_len > 0 && crc_len >= K) || (crc_len == 0 && K == 0)) return POLAR_EINVAL;
     if ((flags & ~0x3FFu) != 0 || (flags & 0xFFu) > POLAR_NO_SPECIAL_NODES) return POLAR_EINVAL;
-    if (L < 1 || L > (uint32_t)kMaxL || (L & (L - 1))) return POLAR_EUNSUPPORTED;
+    if (L < 1 || L > (uint32_t)kMaxWideL || (L & (L - 1))) return POLAR_EUNSUPPORTED;
     uint32_t nf = 0;
     for (uint32_t i = 0; i < N; ++i) nf += frozen_mask[i] ? 1u : 0u;
     if (nf != N - K) return POLAR_EINVAL;
@@ -475,11 +545,21 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
         cudaError_t e = upload(&c->d_info, c->info);
         if (e == cudaSuccess) e = upload(&c->d_syn, c->syn);
         if (e == cudaSuccess) e = upload(&c->d_desc, c->desc);
+        if (e == cudaSuccess && L > (uint32_t)kMaxL) e = upload(&c->d_xops, c->xops);
         if (e != cudaSuccess) {
             free_device(c);
             delete c;
             return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
         }
+    }
+    if (L > (uint32_t)kMaxL) {
+        c->wide = true;
+        for (int d = 0; d < 2; ++d) {
+            WideView v;
+            c->wide_gbytes[d] = wide_view(c, d, v).gbytes;
+        }
+        *out = c;
+        return POLAR_OK;
     }
     for (int d = 0; d < 2; ++d) {
         LaunchShape sh;
@@ -508,8 +588,8 @@ int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dty
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     if (n_frames == 0) return POLAR_OK;
     if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
-    return decode_shape(code, llr_dtype, code->shape[llr_dtype], llr_dev, n_frames, info_bits_dev, path_metric_dev,
-                        crc_ok_dev, winner_slot_dev, reinterpret_cast<cudaStream_t>(stream));
+    return decode_any(code, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev, winner_slot_dev,
+                      reinterpret_cast<cudaStream_t>(stream));
 }
 
 int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int llr_dtype, uint32_t n_frames,
@@ -564,7 +644,7 @@ int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int l
             rc = POLAR_ECUDA;
             break;
         }
-        rc = decode_shape(code, llr_dtype, code->shape[llr_dtype], d_llr, nf, d_bits, d_pm, d_ok, d_slot, dec);
+        rc = decode_any(code, llr_dtype, d_llr, nf, d_bits, d_pm, d_ok, d_slot, dec);
         if (rc != POLAR_OK) break;
         if (cudaEventRecord(ev_dec[b], dec) != cudaSuccess || cudaStreamWaitEvent(cout, ev_dec[b], 0) != cudaSuccess) {
             rc = POLAR_ECUDA;
@@ -610,8 +690,8 @@ int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, co
     if (n_frames == 0) return POLAR_OK;
     if (!llr_dev || !path_metric_dev || !crc_ok_dev || (!info_bits_dev && fast->k > 0)) return POLAR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    int rc = decode_shape(fast, llr_dtype, fast->shape[llr_dtype], llr_dev, n_frames, info_bits_dev,
-                          path_metric_dev, crc_ok_dev, winner_slot_dev, st);
+    int rc = decode_any(fast, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev,
+                        winner_slot_dev, st);
     if (rc != POLAR_OK) return rc;
     void *tmp = nullptr;
     if (cudaMallocAsync(&tmp, sizeof(uint32_t) * ((size_t)n_frames + 1), st) != cudaSuccess) return POLAR_ENOMEM;
@@ -626,8 +706,8 @@ int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, co
         cudaFreeAsync(tmp, st);
         return POLAR_ECUDA;
     }
-    rc = decode_shape(list, llr_dtype, list->shape[llr_dtype], llr_dev, n_frames, info_bits_dev, path_metric_dev,
-                      crc_ok_dev, winner_slot_dev, st, idx, cnt);
+    rc = decode_any(list, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev, winner_slot_dev,
+                    st, idx, cnt);
     cudaFreeAsync(tmp, st);
     return rc;
 }
@@ -636,6 +716,12 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
                         polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out, uint32_t *cta_out) {
     if (!code || code->host_only || !llr_dev || n_frames == 0) return POLAR_EINVAL;
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
+    if (code->wide) {   // one shape only: a CTA of L threads per frame
+        if (warps_out) *warps_out = code->L / 32;
+        if (budget_out) *budget_out = 0;
+        if (cta_out) *cta_out = code->L;
+        return POLAR_OK;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t kb = (code->k + 7) / 8;
     uint8_t *bits = nullptr;
@@ -700,6 +786,7 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
                               uint8_t *info_bits_dev, float *path_metric_dev, uint8_t *crc_ok_dev,
                               int32_t *winner_slot_dev, polar_stream_t stream) {
     if (!code || code->host_only) return POLAR_EINVAL;
+    if (code->wide) return POLAR_EUNSUPPORTED;
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     if (n_frames == 0) return POLAR_OK;
     if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
@@ -874,6 +961,8 @@ int polar_batch_plan(polar_batch_t **out, polar_code_t *const *codes, uint32_t n
     if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
     for (uint32_t c = 0; c < n_codes; ++c)
         if (!codes[c] || codes[c]->host_only || codes[c]->device != dev) return POLAR_EINVAL;
+    for (uint32_t c = 0; c < n_codes; ++c)
+        if (codes[c]->wide) return POLAR_EUNSUPPORTED;
     for (uint32_t f = 0; f < n_frames; ++f)
         if (frame_code[f] >= n_codes) return POLAR_EINVAL;
     polar_batch *b = new (std::nothrow) polar_batch();
@@ -1040,6 +1129,14 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
     info->n_rep = c->n_rep;
     info->n_spc = c->n_spc;
     for (int d = 0; d < 2; ++d) {
+        if (c->wide) {
+            info->warps_per_frame[d] = c->L / 32;
+            info->frames_per_cta[d] = 1;
+            info->smem_per_frame[d] = wide_smem_bytes((int)c->L, (int)c->n);
+            info->scratch_per_frame[d] = c->wide_gbytes[d];
+            info->spill_mask[d] = (1u << c->n) - 1u;
+            continue;
+        }
         info->warps_per_frame[d] = (uint32_t)c->shape[d].warps;
         info->frames_per_cta[d] = (uint32_t)c->shape[d].groups_per_cta;
         info->smem_per_frame[d] = c->shape[d].lay.bytes;
@@ -1090,6 +1187,7 @@ int polar_code_op_count(const polar_code_t *c, uint64_t *ops_per_frame) {
 int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_frame, uint32_t smem_budget,
                           uint32_t cta_threads) {
     if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
+    if (c->wide) return POLAR_EUNSUPPORTED;
     LaunchShape sh;
     if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh, cta_threads)) return POLAR_EINVAL;
     return install_shape(c, llr_dtype, sh);
@@ -1209,7 +1307,7 @@ namespace {
 int srv_register(polar_server *s, const polar_code *c, uint32_t &idx) {
     auto it = s->code_idx.find(c);
     if (it != s->code_idx.end()) { idx = it->second; return POLAR_OK; }
-    if (s->codes.size() >= kSrvMaxCodes) return POLAR_EUNSUPPORTED;
+    if (s->codes.size() >= kSrvMaxCodes || c->wide) return POLAR_EUNSUPPORTED;
     uint32_t *ops = nullptr;
     if (upload(&ops, flag_ops(c->ops, (uint32_t)s->warps)) != cudaSuccess) return POLAR_ECUDA;
     idx = (uint32_t)s->codes.size();

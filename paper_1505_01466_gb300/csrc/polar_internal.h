@@ -8,7 +8,8 @@
 namespace polar {
 
 constexpr int kMaxLogN = 12;   // N <= 4096
-constexpr int kMaxL = 32;      // one warp lane per path in the final pick
+constexpr int kMaxL = 32;      // narrow kernels: one warp lane per path
+constexpr int kMaxWideL = 128; // wide kernel: one CTA thread per path
 
 // Operation kinds of the unrolled schedule (Listing 2 of the paper).
 enum OpKind : uint32_t {
@@ -156,4 +157,35 @@ cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n_frames, uint32_t *
 cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
                          cudaStream_t stream);
 int occupancy_batch(int dtype, int warps, uint32_t smem, int threads);
+// Wide lists (L = 64, 128): one CTA of L threads per frame over the fully
+// unrolled schedule; every stage in the CTA's global scratch region.
+struct WideView {
+    const uint32_t *xops;          // fully unrolled schedule (F, G, Combine, leaves)
+    const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
+    const uint16_t *info;          // [K] information positions
+    int n_xops;
+    int N, n, L, K, k, kb, crc_len, systematic;
+    uint64_t galpha[kMaxLogN];     // stage j: L rows of 2^j elements
+    uint64_t gbl[kMaxLogN];        // left beta of stage j: L rows of beta_words(j) words
+    uint64_t gbr, gchan;           // right/root beta, channel row
+    uint64_t gbytes;               // global scratch per CTA
+};
+
+struct WideParams {
+    WideView v;
+    const void *llr;
+    uint8_t *bits;
+    float *pm;
+    uint8_t *ok;
+    int32_t *slot;
+    uint32_t n_frames;
+    uint8_t *scratch;              // v.gbytes per CTA
+    const uint32_t *frame_idx;     // optional indirection, as in Params
+    const uint32_t *frame_cnt;
+};
+
+uint32_t wide_smem_bytes(int L, int n);
+int occupancy_wide(int dtype, int L, int n);
+cudaError_t launch_wide(int dtype, const WideParams &p, int grid, cudaStream_t stream);
+
 }  // namespace polar

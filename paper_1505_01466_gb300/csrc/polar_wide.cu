@@ -1,0 +1,494 @@
+// polar_wide.cu -- list decoding with L = 64 or 128 paths.
+//
+// The narrow kernels (polar_kernels.cu) map one path to one lane of one warp.
+// Wider lists (the paper uses L = 128 to study the CRC length, Sec. VI,
+// Fig. 3) need more lanes than a warp has, so they run here: one CTA of L
+// threads per frame, thread p owning path p for leaves, all threads sharing
+// the element-wise F / G / Combine work. The schedule is the fully unrolled
+// one (every F, G, Combine and leaf of the decoding tree, Sec. II-D,
+// Listing 2); every stage lives in the CTA's global scratch behind per-path
+// stage-index rows (the lazy copy of Sec. IV-A/B). Selection (Algorithm 1)
+// sorts all candidate keys of the CTA in shared memory and keeps the L
+// smallest; survivors take slots in (source, candidate) order.
+//
+// The arithmetic is the narrow decoder's, element by element: min-sum F
+// (Eq. (1)), G (Eq. (2), saturating for int8), Combine (Eq. (3)), the node
+// rules of Sec. III-B..E with pairwise-tree sums, least reliable bits ranked
+// by (|a|, index), penalties parent + increment, keys (penalty, source slot,
+// candidate index), and the final CRC pick of Sec. II-B.
+
+#include "polar_internal.h"
+
+namespace polar {
+namespace {
+
+constexpr unsigned FULLW = 0xffffffffu;
+constexpr unsigned long long KINF64 = ~0ull;
+
+template <typename T> struct WA;
+template <> struct WA<float> {
+    typedef float P;
+    static __device__ __forceinline__ float negp(float a) { return a < 0.f ? -a : 0.f; }
+    static __device__ __forceinline__ float posp(float a) { return a > 0.f ? a : 0.f; }
+    static __device__ __forceinline__ uint32_t absbits(float a) { return __float_as_uint(fabsf(a)); }
+    static __device__ __forceinline__ float unabs(uint32_t b) { return __uint_as_float(b); }
+    static __device__ __forceinline__ uint32_t pbits(float p) { return __float_as_uint(p); }
+    static __device__ __forceinline__ float frombits(uint32_t b) { return __uint_as_float(b); }
+    static __device__ __forceinline__ float f(float a, float b) {
+        const float m = fminf(fabsf(a), fabsf(b));
+        return __uint_as_float(__float_as_uint(m) | ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u));
+    }
+    static __device__ __forceinline__ float g(float a, float b, uint32_t beta) {
+        return b + __uint_as_float(__float_as_uint(a) ^ (beta << 31));
+    }
+};
+template <> struct WA<int8_t> {
+    typedef int P;
+    static __device__ __forceinline__ int negp(int8_t a) { return a < 0 ? -(int)a : 0; }
+    static __device__ __forceinline__ int posp(int8_t a) { return a > 0 ? (int)a : 0; }
+    static __device__ __forceinline__ uint32_t absbits(int8_t a) { return (uint32_t)(a < 0 ? -(int)a : (int)a); }
+    static __device__ __forceinline__ int unabs(uint32_t b) { return (int)b; }
+    static __device__ __forceinline__ uint32_t pbits(int p) { return (uint32_t)p; }
+    static __device__ __forceinline__ int frombits(uint32_t b) { return (int)b; }
+    static __device__ __forceinline__ int8_t f(int8_t a, int8_t b) {
+        const int x = a, y = b;
+        const int m = min(abs(x), abs(y));
+        return (int8_t)(((x ^ y) < 0) ? -m : m);
+    }
+    static __device__ __forceinline__ int8_t g(int8_t a, int8_t b, uint32_t beta) {
+        const int r = beta ? (int)b - (int)a : (int)b + (int)a;
+        return (int8_t)max(-127, min(127, r));
+    }
+};
+
+__device__ __forceinline__ uint32_t spc_mask(int c) { return (0xFCA69530u >> (4 * c)) & 0xFu; }
+
+// Shared memory of one CTA (one frame at a time).
+struct WideSmem {
+    uint8_t *idx[2], *bidx[2];     // [L][16] stage -> physical row
+    uint32_t *pen[2];              // penalty bits per slot
+    unsigned long long *keys;      // [L * 8] candidate keys in (source, candidate) order
+    unsigned long long *sortb;     // [pow2 >= L * 8] sort buffer
+    uint32_t *flag, *mpos;         // per source: SPC parity / repetition ML flag, [L][4] positions
+    int *nsrc;                     // per new slot: index into keys[]
+    int *scan;                     // [L] per-thread counts
+    uint32_t *ubuf;                // winner's u words
+    unsigned long long *red;       // [L / 32] reduction scratch
+};
+
+__device__ __forceinline__ WideSmem carve(uint8_t *base, int L, int nbw) {
+    WideSmem s;
+    uint8_t *p = base;
+    for (int b = 0; b < 2; ++b) { s.idx[b] = p; p += L * 16; }
+    for (int b = 0; b < 2; ++b) { s.bidx[b] = p; p += L * 16; }
+    for (int b = 0; b < 2; ++b) { s.pen[b] = reinterpret_cast<uint32_t *>(p); p += L * 4; }
+    s.keys = reinterpret_cast<unsigned long long *>(p); p += L * 8 * 8;
+    s.sortb = reinterpret_cast<unsigned long long *>(p); p += L * 8 * 8;
+    s.flag = reinterpret_cast<uint32_t *>(p); p += L * 4;
+    s.mpos = reinterpret_cast<uint32_t *>(p); p += L * 16;
+    s.nsrc = reinterpret_cast<int *>(p); p += L * 4;
+    s.scan = reinterpret_cast<int *>(p); p += L * 4;
+    s.ubuf = reinterpret_cast<uint32_t *>(p); p += nbw * 4;
+    p = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    s.red = reinterpret_cast<unsigned long long *>(p);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T *wrow(const WideView &v, uint8_t *G, const WideSmem &s, int cur, int p, int j) {
+    if (j == v.n) return reinterpret_cast<T *>(G + v.gchan);
+    return reinterpret_cast<T *>(G + v.galpha[j]) + ((size_t)s.idx[cur][p * 16 + j] << j);
+}
+
+// CTA-wide exclusive scan of one int per thread; returns the prefix, *total the sum.
+__device__ __forceinline__ int cta_excl_scan(int x, int *scan, int *total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    int v = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULLW, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) scan[w] = v;
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int i = 0; i < nw; ++i) {
+        if (i < w) base += scan[i];
+        tot += scan[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return base + v - x;
+}
+
+// Exact L-th smallest of keys[0, M) (M > L): bitonic sort of a padded copy.
+__device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, int L) {
+    int P = 1;
+    while (P < M) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) s.sortb[i] = i < M ? s.keys[i] : KINF64;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int o = i ^ j;
+                if (o > i) {
+                    const unsigned long long a = s.sortb[i], b = s.sortb[o];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { s.sortb[i] = b; s.sortb[o] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return s.sortb[L - 1];
+}
+
+// Canonical sums of |min(a,0)| and |max(a,0)| over nv elements (in place on
+// the path's own row, which the leaf does not need afterwards).
+template <typename T>
+__device__ __forceinline__ void wide_sums(T *row, int nv, bool want1, typename WA<T>::P &v0, typename WA<T>::P &v1) {
+    typedef typename WA<T>::P P;
+    if (sizeof(T) == 1) {
+        int s0 = 0, s1 = 0;
+        for (int i = 0; i < nv; ++i) {
+            s0 += WA<T>::negp(row[i]);
+            s1 += WA<T>::posp(row[i]);
+        }
+        v0 = (P)s0;
+        v1 = (P)s1;
+        return;
+    }
+    float *x = reinterpret_cast<float *>(row);
+    if (nv == 1) {
+        v0 = (P)WA<float>::negp(x[0]);
+        v1 = (P)WA<float>::posp(x[0]);
+        return;
+    }
+    const int h = nv >> 1;
+    for (int i = 0; i < h; ++i) {
+        const float a = x[i], b = x[i + h];
+        x[i] = WA<float>::negp(a) + WA<float>::negp(b);
+        x[i + h] = WA<float>::posp(a) + WA<float>::posp(b);
+    }
+    for (int hh = h >> 1; hh >= 1; hh >>= 1) {
+        for (int i = 0; i < hh; ++i) {
+            x[i] = x[i] + x[i + hh];
+            x[h + i] = x[h + i] + x[h + i + hh];
+        }
+    }
+    v0 = (P)x[0];
+    v1 = want1 ? (P)x[h] : (P)0;
+}
+
+template <typename T>
+__device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, const uint8_t *src, uint8_t *bits_row,
+                           float *pm_out, uint8_t *ok_out, int32_t *slot_out) {
+    typedef typename WA<T>::P P;
+    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
+    const int n = v.n, N = v.N, L = v.L;
+    const int nbw = beta_words(n);
+    T *chan = reinterpret_cast<T *>(G + v.gchan);
+    uint32_t *br = reinterpret_cast<uint32_t *>(G + v.gbr);
+
+    for (int i = t; i < N; i += nt) {
+        T x = reinterpret_cast<const T *>(src)[i];
+        if (sizeof(T) == 1 && (int)x < -127) x = (T)-127;   // -128 reads as -127
+        chan[i] = x;
+    }
+    for (int i = t; i < L * 16; i += nt) {
+        s.idx[0][i] = 0; s.idx[1][i] = 0; s.bidx[0][i] = 0; s.bidx[1][i] = 0;
+    }
+    if (t == 0) s.pen[0][0] = 0u;
+    __syncthreads();
+    int La = 1, cur = 0;
+
+    for (int o = 0; o < v.n_xops; ++o) {
+        const uint32_t op = __ldg(v.xops + o);
+        const uint32_t kind = op_kind(op);
+        const int j = op_stage(op);
+        const int dest = op_dest(op);
+        if (kind == OP_F || kind == OP_G) {
+            const int jo = j - 1, h = 1 << jo;
+            const int bwc = beta_words(jo);
+            const uint32_t *blb = reinterpret_cast<const uint32_t *>(G + v.gbl[jo]);
+            T *outb = reinterpret_cast<T *>(G + v.galpha[jo]);
+            for (int e = t; e < (La << jo); e += nt) {
+                const int p = e >> jo, i = e & (h - 1);
+                const T *in = wrow<T>(v, G, s, cur, p, j);
+                T r;
+                if (kind == OP_F) {
+                    r = WA<T>::f(in[i], in[i + h]);
+                } else {
+                    const uint32_t bit = (blb[(int)s.bidx[cur][p * 16 + jo] * bwc + (i >> 5)] >> (i & 31)) & 1u;
+                    r = WA<T>::g(in[i], in[i + h], bit);
+                }
+                outb[((size_t)p << jo) + i] = r;
+            }
+            // this op reads only the stage-j entries of the index rows
+            if (t < La) s.idx[cur][t * 16 + jo] = (uint8_t)t;
+            __syncthreads();
+        } else if (kind == OP_COMB) {
+            const int jc = j - 1, bwc = beta_words(jc);
+            const uint32_t *blb = reinterpret_cast<const uint32_t *>(G + v.gbl[jc]);
+            uint32_t *out = dest ? br : reinterpret_cast<uint32_t *>(G + v.gbl[j]);
+            const int ostride = dest ? nbw : beta_words(j);
+            if (jc >= 5) {
+                for (int e = t; e < La * bwc; e += nt) {
+                    const int p = e / bwc, w = e - p * bwc;
+                    const uint32_t l = blb[(int)s.bidx[cur][p * 16 + jc] * bwc + w];
+                    const uint32_t r = br[p * nbw + w];
+                    out[p * ostride + w] = l ^ r;
+                    out[p * ostride + w + bwc] = r;
+                }
+            } else {
+                const int hb = 1 << jc;
+                const uint32_t m = (1u << hb) - 1u;
+                if (t < La) {
+                    const uint32_t l = blb[(int)s.bidx[cur][t * 16 + jc]];
+                    const uint32_t r = br[t * nbw];
+                    out[t * ostride] = ((l ^ r) & m) | ((r & m) << hb);
+                }
+            }
+            // this op reads only the stage-jc entries of the left-beta rows
+            if (!dest && t < La) s.bidx[cur][t * 16 + j] = (uint8_t)t;
+            __syncthreads();
+        } else {
+            // ---------------- leaf of 2^j bits: thread p = path p ----------------
+            const int nv = 1 << j;
+            const int bw = beta_words(j);
+            uint32_t *bout = dest ? br : reinterpret_cast<uint32_t *>(G + v.gbl[j]);
+            const int ostride = dest ? nbw : bw;
+            const uint32_t wmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+            const bool act = t < La;
+            if (kind == OP_R0) {
+                // Rate-0 (Sec. III-B): penalty += sum |min(a, 0)|, beta = 0, no fork.
+                if (act) {
+                    T *row = wrow<T>(v, G, s, cur, t, j);
+                    P v0, v1;
+                    wide_sums<T>(row, nv, false, v0, v1);
+                    s.pen[cur][t] = WA<T>::pbits(WA<T>::frombits(s.pen[cur][t]) + v0);
+                    for (int w = 0; w < bw; ++w) bout[t * ostride + w] = 0u;
+                    if (!dest) s.bidx[cur][t * 16 + j] = (uint8_t)t;
+                }
+                __syncthreads();
+                continue;
+            }
+            int C = 2;
+            if (kind == OP_R1) C = nv == 1 ? 2 : 4;
+            else if (kind == OP_SPC) C = L == 2 ? 2 : 8;
+            if (act) {
+                T *row = wrow<T>(v, G, s, cur, t, j);
+                const P ps = WA<T>::frombits(s.pen[cur][t]);
+                unsigned long long *kk = s.keys + t * C;
+                if (kind == OP_REP) {
+                    // Repetition (Sec. III-E): the ML word listed first.
+                    P x0, x1;
+                    wide_sums<T>(row, nv, true, x0, x1);
+                    const uint32_t fl = (x0 <= x1) ? 0u : 1u;
+                    s.flag[t] = fl;
+                    kk[0] = ((unsigned long long)WA<T>::pbits(ps + (fl ? x1 : x0)) << 32) | (unsigned)(t * C);
+                    kk[1] = ((unsigned long long)WA<T>::pbits(ps + (fl ? x0 : x1)) << 32) | (unsigned)(t * C + 1);
+                } else {
+                    // least reliable positions by (|a|, index), and the parity of the hard decision
+                    const int R = kind == OP_R1 ? 2 : 4;
+                    unsigned long long top[4] = {KINF64, KINF64, KINF64, KINF64};
+                    int neg = 0;
+                    for (int i = 0; i < nv; ++i) {
+                        const T a = row[i];
+                        neg += a < (T)0 ? 1 : 0;
+                        unsigned long long key = ((unsigned long long)WA<T>::absbits(a) << 16) | (unsigned)i;
+                        if (key < top[R - 1]) {
+                            for (int r = 0; r < R; ++r)
+                                if (key < top[r]) { const unsigned long long x = top[r]; top[r] = key; key = x; }
+                        }
+                    }
+                    P ar[4];
+                    for (int r = 0; r < 4; ++r) {
+                        ar[r] = WA<T>::unabs((uint32_t)(top[r] >> 16));
+                        s.mpos[t * 4 + r] = (uint32_t)(top[r] & 0xFFFFu);
+                    }
+                    if (kind == OP_R1) {
+                        // Rate-1 (Sec. III-C): HD, HD^m1, HD^m2, HD^m1^m2.
+                        kk[0] = ((unsigned long long)WA<T>::pbits(ps) << 32) | (unsigned)(t * C);
+                        kk[1] = ((unsigned long long)WA<T>::pbits(ps + ar[0]) << 32) | (unsigned)(t * C + 1);
+                        if (C == 4) {
+                            kk[2] = ((unsigned long long)WA<T>::pbits(ps + ar[1]) << 32) | (unsigned)(t * C + 2);
+                            kk[3] = ((unsigned long long)WA<T>::pbits(ps + (ar[0] + ar[1])) << 32) | (unsigned)(t * C + 3);
+                        }
+                    } else {
+                        // SPC (Sec. III-D): ML = HD or HD^m1 by the parity q; ML ^ T, penalty Eq. (9).
+                        const uint32_t fl = (neg & 1) ? 0u : 1u;
+                        s.flag[t] = fl;
+                        for (int c = 0; c < C; ++c) {
+                            const uint32_t dm = spc_mask(c) ^ (fl ? 0u : 1u);
+                            P inc = (P)0;
+                            bool first = true;
+                            for (int r = 0; r < 4; ++r)
+                                if ((dm >> r) & 1u) { inc = first ? ar[r] : inc + ar[r]; first = false; }
+                            kk[c] = ((unsigned long long)WA<T>::pbits(ps + inc) << 32) | (unsigned)(t * C + c);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // ---------------- selection (Algorithm 1) ----------------
+            const int M = La * C;
+            const int keep = M < L ? M : L;
+            const unsigned long long tau = M > L ? cta_kth(s, M, L) : KINF64;
+            // survivors in (source, candidate) order: thread t scans items [t*q, t*q + q)
+            const int q = (M + nt - 1) / nt;
+            int cnt = 0;
+            for (int i = t * q; i < M && i < t * q + q; ++i) cnt += s.keys[i] <= tau ? 1 : 0;
+            int tot = 0;
+            int off = cta_excl_scan(cnt, s.scan, &tot);
+            for (int i = t * q; i < M && i < t * q + q; ++i)
+                if (s.keys[i] <= tau) s.nsrc[off++] = i;
+            __syncthreads();
+            // ---------------- commit: slot t takes its source's rows and its word ----------------
+            const int nxt = cur ^ 1;
+            if (t < keep) {
+                const int ki = s.nsrc[t];
+                const int sp = ki / C, c = ki - sp * C;
+                const unsigned long long key = s.keys[ki];
+                s.pen[nxt][t] = (uint32_t)(key >> 32);
+                for (int b = 0; b < 16; ++b) {
+                    s.idx[nxt][t * 16 + b] = s.idx[cur][sp * 16 + b];
+                    s.bidx[nxt][t * 16 + b] = s.bidx[cur][sp * 16 + b];
+                }
+                if (!dest) s.bidx[nxt][t * 16 + j] = (uint8_t)t;
+                uint32_t *ob = bout + t * ostride;
+                if (kind == OP_REP) {
+                    const uint32_t word = ((s.flag[sp] != 0u) != (c == 1)) ? wmask : 0u;
+                    for (int w = 0; w < bw; ++w) ob[w] = word;
+                } else {
+                    const uint32_t dm = kind == OP_R1 ? (uint32_t)c : (spc_mask(c) ^ (s.flag[sp] ? 0u : 1u));
+                    const T *srow = wrow<T>(v, G, s, cur, sp, j);
+                    for (int w = 0; w < bw; ++w) {
+                        uint32_t word = 0;
+                        const int lim = nv < 32 ? nv : 32;
+                        for (int i = 0; i < lim; ++i) word |= (srow[32 * w + i] < (T)0 ? 1u : 0u) << i;
+                        for (int r = 0; r < 4; ++r) {
+                            const uint32_t m = s.mpos[sp * 4 + r];
+                            if (((dm >> r) & 1u) && (int)(m >> 5) == w) word ^= 1u << (m & 31u);
+                        }
+                        ob[w] = word;
+                    }
+                }
+            }
+            __syncthreads();
+            La = keep;
+            cur = nxt;
+        }
+    }
+
+    // ---------------- final pick (Sec. II-B) ----------------
+    unsigned long long key = KINF64;
+    if (t < La) {
+        uint32_t acc = 0;
+        if (v.crc_len > 0) {
+            const uint8_t *xb = reinterpret_cast<const uint8_t *>(br + t * nbw);
+            for (int b = 0; b < (N >> 3); ++b) acc ^= __ldg(v.syn + ((b << 8) | xb[b]));
+        }
+        key = ((unsigned long long)(acc != 0u ? 1u : 0u) << 63) | ((unsigned long long)s.pen[cur][t] << 8) |
+              (unsigned long long)t;
+    }
+    for (int m = 16; m >= 1; m >>= 1) {
+        const unsigned long long o2 = __shfl_xor_sync(FULLW, key, m);
+        key = o2 < key ? o2 : key;
+    }
+    if (lane == 0) s.red[t >> 5] = key;
+    __syncthreads();
+    key = s.red[0];
+    for (int w = 1; w < (nt >> 5); ++w) key = s.red[w] < key ? s.red[w] : key;
+    const int win = (int)(key & 0xFFu);
+    if (t < 32) {
+        // u = x G_N for the winner (natural-order butterflies); a systematic code keeps x
+        const uint32_t *xw = br + win * nbw;
+        const int R = nbw > 32 ? nbw >> 5 : 1;
+        uint32_t U[4];
+        for (int r = 0; r < 4; ++r) {
+            const int w = lane + 32 * r;
+            U[r] = (r < R && w < nbw) ? xw[w] : 0u;
+        }
+        if (!v.systematic) {
+            const uint32_t Mk[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+            for (int r = 0; r < 4; ++r)
+                for (int e = 0; e < 5; ++e)
+                    if ((1 << e) < N) U[r] ^= (U[r] >> (1 << e)) & Mk[e];
+            for (int d = 1; d < nbw; d <<= 1) {
+                if (d >= 32) {
+                    const int dr = d >> 5;
+                    for (int r = 0; r < 4; ++r)
+                        if (r < R && !(r & dr) && r + dr < 4) U[r] ^= U[r + dr];
+                } else {
+                    for (int r = 0; r < 4; ++r) {
+                        const uint32_t x = __shfl_down_sync(FULLW, U[r], d);
+                        if (!(lane & d)) U[r] ^= x;
+                    }
+                }
+            }
+        }
+        for (int r = 0; r < 4; ++r) {
+            const int w = lane + 32 * r;
+            if (r < R && w < nbw) s.ubuf[w] = U[r];
+        }
+        if (t == 0) {
+            *pm_out = (float)WA<T>::frombits(s.pen[cur][win]);
+            if (ok_out) *ok_out = (uint8_t)((key >> 63) ^ 1ull);
+            if (slot_out) *slot_out = win;
+        }
+    }
+    __syncthreads();
+    for (int b = t; b < v.kb; b += nt) {
+        uint32_t byte = 0;
+        for (int e = 0; e < 8; ++e) {
+            const int pos = 8 * b + e;
+            if (pos < v.k) {
+                const uint32_t u = __ldg(v.info + pos);
+                byte |= ((s.ubuf[u >> 5] >> (u & 31u)) & 1u) << e;
+            }
+        }
+        bits_row[b] = (uint8_t)byte;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) wide_kernel(const WideParams P) {
+    extern __shared__ __align__(16) uint8_t smem_w[];
+    const WideView &v = P.v;
+    const WideSmem s = carve(smem_w, v.L, beta_words(v.n));
+    uint8_t *G = P.scratch + (size_t)blockIdx.x * v.gbytes;
+    const size_t nbytes = (size_t)v.N * sizeof(T);
+    const uint32_t nf = P.frame_idx ? *P.frame_cnt : P.n_frames;
+    for (uint32_t i = blockIdx.x; i < nf; i += gridDim.x) {
+        const uint32_t f = P.frame_idx ? P.frame_idx[i] : i;
+        wide_frame<T>(v, G, s, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
+                      P.bits + (size_t)f * v.kb, P.pm + f, P.ok ? P.ok + f : nullptr, P.slot ? P.slot + f : nullptr);
+    }
+}
+
+}  // namespace
+
+uint32_t wide_smem_bytes(int L, int n) {
+    const uint32_t b = (uint32_t)(4 * L * 16 + 2 * L * 4 + 2 * L * 8 * 8 + L * 4 + L * 16 + 2 * L * 4 +
+                                  beta_words(n) * 4);
+    return ((b + 15u) & ~15u) + 8u * (uint32_t)(L / 32);
+}
+
+int occupancy_wide(int dtype, int L, int n) {
+    const uint32_t sm = wide_smem_bytes(L, n);
+    int nb = 0;
+    cudaError_t e = dtype == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wide_kernel<float>, L, sm)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wide_kernel<int8_t>, L, sm);
+    return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_wide(int dtype, const WideParams &p, int grid, cudaStream_t st) {
+    const uint32_t sm = wide_smem_bytes(p.v.L, p.v.n);
+    if (dtype == 0) wide_kernel<float><<<grid, p.v.L, sm, st>>>(p);
+    else wide_kernel<int8_t><<<grid, p.v.L, sm, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace polar

@@ -68,7 +68,8 @@ def test_create_validation(polar):
     assert _create(polar, 64, 32, fr, crc_len=32) == polar.POLAR_EINVAL  # crc_len >= K
     assert _create(polar, 64, 32, fr, crc_len=33) == polar.POLAR_EINVAL
     assert _create(polar, 64, 32, fr, L=3) == polar.POLAR_EUNSUPPORTED
-    assert _create(polar, 64, 32, fr, L=64) == polar.POLAR_EUNSUPPORTED
+    assert _create(polar, 64, 32, fr, L=64) == polar.POLAR_OK             # the wide kernel
+    assert _create(polar, 64, 32, fr, L=256) == polar.POLAR_EUNSUPPORTED
     assert _create(polar, 64, 32, fr, flags=7) == polar.POLAR_EINVAL
     h = ctypes.c_void_p()
     assert polar.load_library().polar_code_create(None, 64, 32, fr.ctypes.data_as(ctypes.c_void_p), 0, 0, 4, 0) \
