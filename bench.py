@@ -65,6 +65,8 @@ def parse():
                     help="WARPS,SMEM_BUDGET[,CTA_THREADS]: fixed launch shape instead of autotuning")
     ap.add_argument("--skip-fer", action="store_true")
     ap.add_argument("--skip-ablation", action="store_true")
+    ap.add_argument("--skip-wide", action="store_true")
+    ap.add_argument("--wide-frames", type=int, default=1 << 14)
     ap.add_argument("--ablation-frames", type=int, default=1 << 17)
     ap.add_argument("--fer-frames", type=int, default=1 << 17, help="frames per Eb/N0 point of the FER sweep")
     ap.add_argument("--fer-points", default="3.5,4.0,4.5", help="Eb/N0 points (dB) of the FER sweep")
@@ -357,6 +359,41 @@ def measure_ablation(args, torch, dev, stream):
                          "frames_per_s": llr.shape[0] / ms * 1e3, "one_frame_latency_us": statistics.median(lat[2:])})
             code.close()
     return {"code": f"({N},{K}) CRC-32, f32 LLRs at {EBN0_DB} dB, {args.ablation_frames} frames per batch",
+            "rows": rows}
+
+
+def measure_wide(args, torch, dev, stream):
+    """Lists wider than a warp: (1024,860) at L = 128 with CRC-8 vs CRC-32 at the
+    same payload k = 828 (the paper's CRC-length study, Sec. VI, Fig. 3):
+    throughput of the CTA-per-frame kernel and FER per Eb/N0 point."""
+    from paper_1505_01466_gb300 import inputs as I
+    from paper_1505_01466_gb300.polar import PolarCode
+    Nw, kw, Lw = 1024, 828, 128
+    rows = []
+    for crc, poly in ((8, I.CRC8_POLY), (32, I.CRC32_POLY)):
+        Kw = kw + crc
+        frozen = I.ga_frozen_mask(Nw, Kw, DESIGN_DB, kw / Nw)
+        code = PolarCode(frozen, crc, poly, Lw)
+        for ebn0 in (3.0, 3.5):
+            fr = I.make_frames_chunked(frozen, crc, poly, ebn0, args.wide_frames, seed=int(ebn0 * 100) + crc)
+            llr = torch.from_numpy(fr.llr_f32).to(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                code.decode(llr[:256], stream=stream)
+                a.record(stream)
+                out = code.decode(llr, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            err = (I.unpack_bits_lsb(out[0].cpu().numpy(), kw) != fr.payload).any(axis=1)
+            x = int(err.sum())
+            lo, hi = clopper_pearson(x, err.size)
+            rows.append({"crc": crc, "K": Kw, "ebn0_db": ebn0, "frames": int(err.size), "errors": x,
+                         "fer": x / err.size, "ci99": [lo, hi],
+                         "gbps": kw * err.size / ms / 1e6, "frames_per_s": err.size / ms * 1e3})
+            del llr
+        code.close()
+    return {"code": f"({Nw}, k={kw}) + CRC, L={Lw}, f32, GA {DESIGN_DB} dB", "kernel": "one CTA of L threads per frame",
             "rows": rows}
 
 
@@ -665,6 +702,9 @@ def run_ours(args):
     ablation = None
     if rank == 0 and not args.skip_ablation:
         ablation = measure_ablation(args, torch, dev, stream)
+    wide = None
+    if rank == 0 and not args.skip_wide:
+        wide = measure_wide(args, torch, dev, stream)
 
     batched = None
     if not args.skip_batched:
@@ -696,6 +736,7 @@ def run_ours(args):
             "serving": serving,
             "fer": fer_sweep,
             "ablation": ablation,
+            "wide_lists": wide,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
