@@ -120,18 +120,41 @@ struct TreeBuilder {
         expand(OP_COMB, j, dest, start);
     }
 
+    uint32_t push_desc(const std::vector<uint32_t> &types) {
+        unsigned long long w[2] = {0ull, 0ull};
+        for (size_t i = 0; i < types.size(); ++i) w[i / 21] |= (unsigned long long)types[i] << (3 * (i % 21));
+        const uint32_t di = (uint32_t)(desc.size() / 2);
+        desc.push_back(w[0]);
+        desc.push_back(w[1]);
+        return di;
+    }
+
     void build(int j, uint32_t start, uint32_t dest) {
         if (j <= kSubLog) {
             std::vector<uint32_t> types;
             uint32_t logm = 0;
             bool fork = false;
             walk_sub(j, start, dest, types, logm, fork);
-            unsigned long long w[2] = {0ull, 0ull};
-            for (size_t i = 0; i < types.size(); ++i)
-                w[i / 21] |= (unsigned long long)types[i] << (3 * (i % 21));
-            const uint32_t di = (uint32_t)(desc.size() / 2);
-            desc.push_back(w[0]);
-            desc.push_back(w[1]);
+            const uint32_t di = push_desc(types);
+            ops.push_back(op_make(OP_SUB, (uint32_t)j, dest) | (fork ? 1u << 11 : 0u) | (std::min(logm, 6u) << 12) |
+                          (di << 15));
+            return;
+        }
+        if (j == kSubLog + 1 && c->n > (uint32_t)j && classify(j, start) == 0) {
+            // an inner node of 2^(kSubLog+1) bits below the root: F, both
+            // register subtrees, G and Combine as one operation (descriptors
+            // of the left and right subtree stored consecutively)
+            const uint32_t h = 1u << (j - 1);
+            std::vector<uint32_t> tl, tr;
+            uint32_t logm = 0;
+            bool fork = false;
+            expand(OP_F, j, 0, start);
+            walk_sub(j - 1, start, 0, tl, logm, fork);
+            expand(OP_G, j, 0, start);
+            walk_sub(j - 1, start + h, 1, tr, logm, fork);
+            expand(OP_COMB, j, dest, start);
+            const uint32_t di = push_desc(tl);
+            push_desc(tr);
             ops.push_back(op_make(OP_SUB, (uint32_t)j, dest) | (fork ? 1u << 11 : 0u) | (std::min(logm, 6u) << 12) |
                           (di << 15));
             return;

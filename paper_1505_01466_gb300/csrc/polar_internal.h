@@ -24,7 +24,10 @@ enum OpKind : uint32_t {
 };
 
 // Subtrees rooted at this stage or below run as one OP_SUB operation: warp 0,
-// one lane per path, LLRs / beta / penalty in registers.
+// one lane per path, LLRs / beta / penalty in registers. An OP_SUB at stage
+// kSubLog + 1 is an inner node whose two children are such subtrees: F, left
+// subtree, G, right subtree and Combine in one operation (its descriptor index
+// names the left subtree's descriptor; the right one follows it).
 constexpr int kSubLog = 4;
 
 // One schedule entry: kind | stage j << 4 | dest << 8 | solo << 9 | sync << 10.

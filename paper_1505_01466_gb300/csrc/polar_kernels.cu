@@ -584,6 +584,98 @@ __device__ __forceinline__ void run_sub(const CodeView &cv, uint8_t *S, uint8_t 
     }
 }
 
+// ---- one inner node of 32 bits as a single operation ----------------------
+// F (Eq. (1)), the left register subtree, G (Eq. (2)), the right register
+// subtree and Combine (Eq. (3)) of a node just above the register subtrees,
+// on warp 0 with lane s = path s. The node's input row stays in memory and is
+// read twice, the second time through the row index of the path the lane
+// descends from (st.orig), so stage-4 rows and left betas never leave
+// registers.
+template <typename T>
+__device__ __forceinline__ void node32_in(const T *row, Sub<T> &st, int side) {
+    constexpr int o = aoff<kSubLog>();
+    if (sizeof(T) == 4) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 x = r4[q], y = r4[q + 4];
+            const float xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = 4 * q + e;
+                st.a[o + i] = side ? gv(xs[e], ys[e], (st.bl[kSubLog] >> i) & 1u) : fv(xs[e], ys[e]);
+            }
+        }
+    } else {
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        const uint4 x4 = r4[0], y4 = r4[1];
+        const uint32_t xw[4] = {x4.x, x4.y, x4.z, x4.w}, yw[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int a = (int)(int8_t)((xw[i >> 2] >> (8 * (i & 3))) & 0xFF);
+            const int b = (int)(int8_t)((yw[i >> 2] >> (8 * (i & 3))) & 0xFF);
+            st.a[o + i] = side ? gv(a, b, (st.bl[kSubLog] >> i) & 1u) : fv(a, b);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void run_sub32(const CodeView &cv, uint8_t *S, uint8_t *Gs, uint32_t op, int La, int cur,
+                                          int lane) {
+    typedef typename Arith<T>::P PT;
+    typedef typename Arith<T>::K KT;
+    constexpr int JN = kSubLog + 1;
+    const Layout &lay = cv.lay;
+    const int n = cv.n;
+    const int dest = op_dest(op);
+    uint8_t *idxc = S + lay.idx[cur];
+    uint8_t *bidxc = S + lay.bidx[cur];
+    PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
+    const T *stj = alpha_ptr<T>(lay, S, Gs, JN);
+    Sub<T> st;
+#pragma unroll
+    for (int i = 0; i < 31; ++i) st.a[i] = 0;
+    st.pen = lane < La ? penc[lane] : (PT)0;
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) st.bl[jj] = 0u;
+    st.br = 0u;
+    st.orig = lane;
+    SubCtx<T> cx;
+    cx.tab = reinterpret_cast<KT *>(S + lay.surv);
+    cx.lane = lane;
+    cx.La = La;
+    cx.L = cv.L;
+    const uint32_t di = op_sub_desc(op);
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        if (lane < cx.La) node32_in<T>(stj + ((int)idxc[st.orig * 16 + JN] << JN), st, side);
+        Desc d;
+        d.w0 = __ldg(cv.desc + 2 * (di + side));
+        d.w1 = __ldg(cv.desc + 2 * (di + side) + 1);
+        d.pos = 0;
+        sub_node<T, kSubLog>(st, d, side, cx);
+    }
+    const bool act2 = lane < cx.La;
+    const uint32_t beta = ((st.bl[kSubLog] ^ st.br) & 0xFFFFu) | ((st.br & 0xFFFFu) << 16);
+    uint32_t *bout = dest ? br_ptr(lay, S, Gs) : bl_ptr(lay, S, Gs, JN);
+    const int ostride = dest ? beta_words(n) : beta_words(JN);
+    if (act2) {
+        if (op_sub_fork(op)) {
+            const int nxt = cur ^ 1;
+            uint8_t *idxn = S + lay.idx[nxt];
+            uint8_t *bidxn = S + lay.bidx[nxt];
+            reinterpret_cast<PT *>(S + lay.pen[nxt])[lane] = st.pen;
+            reinterpret_cast<uint4 *>(idxn)[lane] = reinterpret_cast<const uint4 *>(idxc)[st.orig];
+            reinterpret_cast<uint4 *>(bidxn)[lane] = reinterpret_cast<const uint4 *>(bidxc)[st.orig];
+            if (!dest) bidxn[lane * 16 + JN] = (uint8_t)lane;
+        } else {
+            penc[lane] = st.pen;
+            if (!dest) bidxc[lane * 16 + JN] = (uint8_t)lane;
+        }
+        bout[lane * ostride] = beta;
+    }
+}
+
 // ---- large leaves (more than 16 bits), warp 0, lane s = source path s ----
 
 // Canonical sums of |min(a,0)| (v0) and |max(a,0)| (v1) over one row of nv
@@ -1065,7 +1157,8 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
         } else if (kind == OP_SUB) {
             // ---------------- a small subtree in registers (warp 0) ----------------
             if (wig == 0) {
-                if (j == 4) run_sub<T, 4>(cv, S, Gs, op, La, cur, lane);
+                if (j == kSubLog) run_sub<T, 4>(cv, S, Gs, op, La, cur, lane);
+                else if (j == kSubLog + 1) run_sub32<T>(cv, S, Gs, op, La, cur, lane);
                 else run_sub<T, 3>(cv, S, Gs, op, La, cur, lane);
             }
             const int lm = op_sub_logmult(op);
