@@ -1,9 +1,12 @@
 // polar_kernels.cu -- list-CRC decoding of polar codes over the unrolled
 // Fast-SSC tree, for GB300 (sm_103a).
 //
-// One frame is decoded by a group of W warps (W = 1, 2, 4); a CTA holds 4 / W
-// groups and every group loops over frames (persistent). All L paths of a
-// frame advance through the same schedule in lockstep, so:
+// One frame is decoded by a group of W warps (W = 1, 2, 4); a CTA of up to
+// 512 threads holds several groups and every group loops over frames
+// (persistent). The groups of a CTA run the same schedule, and while all of
+// them hold a frame a CTA barrier before every leaf or subtree keeps them on
+// the same instructions (they share instruction fetches). All L paths of a frame
+// advance through the schedule in lockstep, so:
 //
 //  * alpha stage j (kSubLog <= j < n) holds one row of 2^j LLRs per physical
 //    slot. F and G (Eq. (1), (2)) read stage j+1 through the path's index-
@@ -16,13 +19,17 @@
 //  * every subtree of at most 16 bits is one operation (OP_SUB) run by warp 0
 //    with one lane per path: its LLRs, betas and penalty stay in registers, a
 //    fork moves a path's state from its parent lane by warp shuffles, and only
-//    the subtree root touches memory. Leaves of more than 16 bits also run one
-//    lane per path (vectorised scans of the path's row).
+//    the subtree root touches memory. An inner node of 32 bits whose children
+//    are such subtrees is one operation too (F and G from its input row, both
+//    subtrees, Combine). Leaves of more than 16 bits also run one lane per
+//    path (vectorised scans of the path's row).
 //  * a forking leaf (Sec. III-C..E) produces keys (penalty, source * C +
-//    candidate) in the source lane. The L smallest survive (Algorithm 1): the
-//    ML column is bitonic-sorted across the warp and later columns are merged
-//    in while their minimum is below the current L-th key; survivors are
-//    numbered in (source, candidate) order by a warp prefix scan.
+//    candidate) in the source lane. The L smallest survive (Algorithm 1). With
+//    a full list the L-th key is at most the largest source-best key, so only
+//    the later candidates below it are sorted and merged with the sorted best
+//    column; otherwise columns are merged in while their minimum is below the
+//    current L-th key. Survivors are numbered in (source, candidate) order by
+//    a warp prefix scan.
 //  * buffers that do not fit the shared-memory budget live in a per-group
 //    global scratch region (L2-resident in practice).
 //  * the final pick (Sec. II-B) checks each path's CRC with byte tables of
@@ -86,15 +93,6 @@ __device__ __forceinline__ float f_op(float a, float b) {
 }
 __device__ __forceinline__ float g_op(float a, float b, uint32_t beta) {
     return b + __uint_as_float(__float_as_uint(a) ^ (beta << 31));
-}
-__device__ __forceinline__ int8_t f_op(int8_t a, int8_t b) {
-    int x = a, y = b;
-    int m = min(abs(x), abs(y));
-    return (int8_t)(((x ^ y) < 0) ? -m : m);
-}
-__device__ __forceinline__ int8_t g_op(int8_t a, int8_t b, uint32_t beta) {
-    int r = beta ? (int)b - (int)a : (int)b + (int)a;
-    return (int8_t)max(-127, min(127, r));
 }
 // Four int8 lanes in one word: F = max(min(a,b), -max(a,b)).
 __device__ __forceinline__ uint32_t f4(uint32_t a, uint32_t b) {
@@ -1175,9 +1173,11 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
         }
         if (op_sync(op)) gsync<W>(gidx);
         else if (wig == 0) __syncwarp();
-        // Every group of the CTA runs the same schedule: a CTA barrier per op
-        // keeps them on the same code, so they share instruction fetches.
-        if (lockstep) asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
+        // Every group of the CTA runs the same schedule: a CTA barrier before
+        // each leaf or subtree (the large code) keeps them on the same
+        // instructions there, so they share instruction fetches; between the
+        // barriers the short stage ops may drift and overlap their latencies.
+        if (lockstep && op_kind(opn) >= OP_R0) asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
         op = opn;
     }
     gsync<W>(gidx);

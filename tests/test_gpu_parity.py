@@ -238,3 +238,31 @@ def test_systematic_codes(torch_cuda, oracle_mod, dtype, case):
         # most frames decode to their payload
         got = I.unpack_bits_lsb(g[0], K - crc)
         assert (got == f.payload).all(axis=1).mean() > 0.5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_full_size_in_the_benchmark_launch_configuration(torch_cuda, oracle_mod, dtype):
+    # (2048,1723) L=32 at 4 dB, 2^20 frames in HBM, the autotuned launch shape the
+    # benchmark times: 4096 distinct frames tiled 256 times. Every copy of a frame
+    # must decode like the first one (the whole batch is checked), and a sample of
+    # the distinct frames, including the last ones, against the oracle.
+    from paper_1505_01466_gb300.polar import PolarCode
+    torch = torch_cuda
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    f = I.make_frames_chunked(fr, 32, I.CRC32_POLY, 4.0, 4096, seed=2020)
+    x = torch.from_numpy(f.llr_i8 if dtype == "i8" else f.llr_f32).cuda()
+    llr = x.repeat(256, 1)
+    code = PolarCode(fr, 32, I.CRC32_POLY, 32)
+    code.autotune(llr[:16384])
+    bits, pm, ok, slot = code.decode(llr)
+    torch.cuda.synchronize()
+    for t in (bits, pm, ok, slot):
+        v = t.view(256, 4096, -1)
+        assert torch.equal(v, v[:1].expand_as(v))
+    sample = np.r_[0:24, 4096 - 24:4096]
+    src = (f.llr_i8 if dtype == "i8" else f.llr_f32)[sample]
+    o = oracle_mod.decode(fr, 32, src, 32, I.CRC32_POLY, 0, n_threads=NT)
+    last = slice(llr.shape[0] - 4096, llr.shape[0])
+    g = tuple(t[last][torch.from_numpy(sample).cuda()].cpu().numpy() for t in (bits, pm, ok, slot))
+    assert_parity(g, o, dtype, "full size, sampled")
+    code.close()
