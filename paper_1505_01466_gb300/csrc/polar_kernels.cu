@@ -4,7 +4,7 @@
 // One frame is decoded by a group of W warps (W = 1, 2, 4); a CTA of up to
 // 512 threads holds several groups and every group loops over frames
 // (persistent). The groups of a CTA run the same schedule, and while all of
-// them hold a frame a CTA barrier before every leaf or subtree keeps them on
+// them hold a frame a CTA barrier before every register subtree keeps them on
 // the same instructions (they share instruction fetches). All L paths of a frame
 // advance through the schedule in lockstep, so:
 //
@@ -1174,10 +1174,10 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
         if (op_sync(op)) gsync<W>(gidx);
         else if (wig == 0) __syncwarp();
         // Every group of the CTA runs the same schedule: a CTA barrier before
-        // each leaf or subtree (the large code) keeps them on the same
+        // each register subtree (the largest code) keeps them on the same
         // instructions there, so they share instruction fetches; between the
-        // barriers the short stage ops may drift and overlap their latencies.
-        if (lockstep && op_kind(opn) >= OP_R0) asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
+        // barriers the other ops may drift and overlap their latencies.
+        if (lockstep && op_kind(opn) == OP_SUB) asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
         op = opn;
     }
     gsync<W>(gidx);
