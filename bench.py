@@ -37,10 +37,10 @@ FRAMES = 1 << 20
 UNIQUE = 1 << 16
 METRIC = "info Gbps at (2048,1723) L=32 on 1 GB300, batched vs plain; FER match; p99 lat"
 # DRAM bytes per frame of decode_kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture over 32768 frames of this workload, 1 warp per frame, 7000-byte budget, 256-thread CTAs; the
+# ncu capture over 32768 frames of this workload, 1 warp per frame, 7000-byte budget, 512-thread CTAs; the
 # capture is summarised in profiles/decode_kernel_2048_1723_L32.md). Valid only for the
 # kernel source with this sha1; any other source reports traffic null.
-NCU_TRAFFIC = {"kernel_sha1": "e0dd8a0a36ddceaa5e2651a8c89423780716e43c", "f32": 1666866, "i8": 189865}
+NCU_TRAFFIC = {"kernel_sha1": "0afef99da334c8d0902fc69df7492dbe07b09f52", "f32": 1680008, "i8": 204086}
 UNIT = "Gbps"
 
 
