@@ -1,10 +1,15 @@
 // polar_capi.cu -- host side of the C ABI declared in include/polar.h.
 //
-// polar_code_create turns a code description into what the decode kernel
-// runs: the Fast-SSC decoding tree flattened into an unrolled operation list
-// (Sec. II-D, Listing 2), the information positions, the CRC syndrome tables
-// and a launch shape (warps per frame, frames per CTA, which alpha stages
-// sit in shared memory and which spill to global scratch).
+// polar_code_create turns a code description into what the decode kernels
+// run: the Fast-SSC decoding tree flattened into an unrolled operation list
+// (Sec. II-D, Listing 2) with small subtrees collapsed into register
+// operations, the information positions, the CRC syndrome tables and a
+// launch shape (warps per frame, CTA size, which alpha stages sit in shared
+// memory and which spill to global scratch). The rest of the file drives the
+// kernels: the plain, host-buffer, allocation-free and adaptive (Sec. V)
+// decodes, the autotuner, wide lists (L = 64, 128), the batched form (work
+// plan, persistent launch, CUDA graph) and the serving engine (admission by
+// device memory, continuous batching on a host thread).
 
 #include <algorithm>
 #include <array>
