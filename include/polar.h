@@ -216,6 +216,23 @@ POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void 
                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out,
                                   uint32_t *cta_threads_out);
 
+/* ---- Test hooks: host-side fault injection ----------------------------------
+ * For tests of error paths and of reads of unwritten memory; they inject on
+ * the host and never make the GPU fault. Process-wide settings, not meant to
+ * change while decodes run on other threads.
+ *   POLAR_INJECT_ALLOC_FAIL  the next `value` device allocations made by
+ *                            decode calls (scratch, staging buffers) succeed
+ *                            and every later one fails, so the call returns
+ *                            POLAR_ENOMEM; value < 0 switches it off.
+ *   POLAR_INJECT_POISON      value != 0: before every decode the global
+ *                            scratch of the launch is filled with bytes no
+ *                            decode writes (0xFF = float NaN, 0x80 = int8
+ *                            -128), so a read of scratch that was never
+ *                            written shows up as a parity failure.
+ * Errors: POLAR_EINVAL for an unknown hook. */
+enum polar_inject { POLAR_INJECT_ALLOC_FAIL = 1, POLAR_INJECT_POISON = 2 };
+POLAR_API int polar_debug_inject(int what, int64_t value);
+
 /* ---- Batched form --------------------------------------------------------
  * Frames of several codes (mixed N, rate and L) decoded by one persistent
  * launch. Frame f uses codes[frame_code[f]]; its LLRs start at byte

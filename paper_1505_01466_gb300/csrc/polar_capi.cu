@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -25,6 +26,8 @@
 #include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/polar.h"
 #include "polar_internal.h"
@@ -57,6 +60,31 @@ struct polar_code {
 };
 
 namespace {
+
+// ---- test hooks (polar_debug_inject): host-side faults, no device fault ------
+std::atomic<int64_t> g_fail_alloc_after{-1};   // < 0: off; else allocations left before failing
+std::atomic<int> g_poison{0};
+
+// Device allocation of a decode call; fails on purpose when the hook says so.
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st, bool async = true) {
+    int64_t k = g_fail_alloc_after.load();
+    while (k >= 0) {
+        if (k == 0) return cudaErrorMemoryAllocation;
+        if (g_fail_alloc_after.compare_exchange_weak(k, k - 1)) break;
+    }
+    return async ? cudaMallocAsync(p, bytes, st) : cudaMalloc(p, bytes);
+}
+
+// Fill scratch with bytes no decode writes before reading (float NaN, int8 -128).
+void scratch_poison(void *p, size_t bytes, int dtype, cudaStream_t st) {
+    if (p && bytes && g_poison.load()) cudaMemsetAsync(p, dtype == POLAR_LLR_F32 ? 0xFF : 0x80, bytes, st);
+}
+
+// NVTX range for the duration of a host call (visible in Nsight timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
 uint64_t al256(uint64_t x) { return (x + 255u) & ~uint64_t(255); }
@@ -400,7 +428,8 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
     void *scratch = nullptr;
     if (sh.lay.gbytes > 0) {
         const size_t bytes = (size_t)grid * sh.groups_per_cta * sh.lay.gbytes;
-        if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) return POLAR_ENOMEM;
+        if (scratch_alloc(&scratch, bytes, st) != cudaSuccess) return POLAR_ENOMEM;
+        scratch_poison(scratch, bytes, dtype, st);
         p.scratch = (uint8_t *)scratch;
     }
     cudaError_t e = launch_decode(dtype, sh, p, (int)grid, st);
@@ -456,7 +485,8 @@ int decode_wide(const polar_code *code, int dtype, const void *llr, uint32_t n_f
     p.frame_idx = frame_idx;
     p.frame_cnt = frame_cnt;
     void *scratch = nullptr;
-    if (cudaMallocAsync(&scratch, (size_t)(grid * p.v.gbytes), st) != cudaSuccess) return POLAR_ENOMEM;
+    if (scratch_alloc(&scratch, (size_t)(grid * p.v.gbytes), st) != cudaSuccess) return POLAR_ENOMEM;
+    scratch_poison(scratch, (size_t)(grid * p.v.gbytes), dtype, st);
     p.scratch = (uint8_t *)scratch;
     cudaError_t e = launch_wide(dtype, p, (int)grid, st);
     cudaFreeAsync(scratch, st);
@@ -616,6 +646,7 @@ int polar_list_decode(const polar_code_t *code, const void *llr_dev, int llr_dty
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     if (n_frames == 0) return POLAR_OK;
     if (!llr_dev || !path_metric_dev || (!info_bits_dev && code->k > 0)) return POLAR_EINVAL;
+    NvtxRange range("polar_list_decode");
     return decode_any(code, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev, winner_slot_dev,
                       reinterpret_cast<cudaStream_t>(stream));
 }
@@ -630,6 +661,7 @@ int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int l
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
     if (dev != code->device) return POLAR_EINVAL;
+    NvtxRange range("polar_list_decode_host");
     const uint64_t row = (uint64_t)code->N * (llr_dtype == POLAR_LLR_I8 ? 1u : 4u);
     const uint64_t kb = (code->k + 7) / 8;
     // chunks of frames in a two-buffer ring: the copy in of chunk c + 1 and the
@@ -651,7 +683,7 @@ int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int l
              cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) rc = POLAR_ECUDA;
     for (int b = 0; rc == POLAR_OK && b < 2 && b < (int)n_chunks; ++b)
-        if (cudaMalloc(&buf[b], buf_bytes) != cudaSuccess) rc = POLAR_ENOMEM;
+        if (scratch_alloc((void **)&buf[b], buf_bytes, nullptr, false) != cudaSuccess) rc = POLAR_ENOMEM;
     // the caller's stream may have pending work on the host buffers' producers
     if (rc == POLAR_OK && cudaEventRecord(ev_dec[0], dec) != cudaSuccess) rc = POLAR_ECUDA;
     if (rc == POLAR_OK && cudaStreamWaitEvent(cin, ev_dec[0], 0) != cudaSuccess) rc = POLAR_ECUDA;
@@ -717,12 +749,13 @@ int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t *list, co
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
     if (n_frames == 0) return POLAR_OK;
     if (!llr_dev || !path_metric_dev || !crc_ok_dev || (!info_bits_dev && fast->k > 0)) return POLAR_EINVAL;
+    NvtxRange range("polar_adaptive_decode");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int rc = decode_any(fast, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev,
                         winner_slot_dev, st);
     if (rc != POLAR_OK) return rc;
     void *tmp = nullptr;
-    if (cudaMallocAsync(&tmp, sizeof(uint32_t) * ((size_t)n_frames + 1), st) != cudaSuccess) return POLAR_ENOMEM;
+    if (scratch_alloc(&tmp, sizeof(uint32_t) * ((size_t)n_frames + 1), st) != cudaSuccess) return POLAR_ENOMEM;
     uint32_t *cnt = (uint32_t *)tmp;
     uint32_t *idx = cnt + 1;
     if (launch_crc_failures(crc_ok_dev, n_frames, idx, cnt, st) != cudaSuccess) {
@@ -837,6 +870,7 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
         if (grid > fit) grid = fit;
         const int st = noalloc_scratch(dev, &scratch);
         if (st != POLAR_OK) return st;
+        scratch_poison(scratch, (size_t)(grid * per_cta), llr_dtype, reinterpret_cast<cudaStream_t>(stream));
     }
     Params p;
     std::memset(&p, 0, sizeof(p));
@@ -854,6 +888,18 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
 }
 
 size_t polar_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
+int polar_debug_inject(int what, int64_t value) {
+    if (what == POLAR_INJECT_ALLOC_FAIL) {
+        g_fail_alloc_after.store(value < 0 ? -1 : value);
+        return POLAR_OK;
+    }
+    if (what == POLAR_INJECT_POISON) {
+        g_poison.store(value != 0 ? 1 : 0);
+        return POLAR_OK;
+    }
+    return POLAR_EINVAL;
+}
 
 // ---- batched form ------------------------------------------------------------
 struct polar_batch {
@@ -957,6 +1003,7 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget, uint32_t cta_threads
 int batch_launch(polar_batch *b, const void *llr, uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot,
                  cudaStream_t st) {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return POLAR_ECUDA;
+    scratch_poison(b->d_scratch, b->scratch_bytes, b->dtype, st);
     BatchParams p;
     std::memset(&p, 0, sizeof(p));
     p.classes = b->d_classes;
@@ -1058,6 +1105,7 @@ int polar_batch_run(polar_batch_t *b, const void *llr_dev, uint8_t *bits_dev, fl
                     int32_t *slot_dev, polar_stream_t stream) {
     if (!b || (b->n_frames > 0 && (!llr_dev || !pm_dev || !bits_dev))) return POLAR_EINVAL;
     if (b->n_frames == 0) return POLAR_OK;
+    NvtxRange range("polar_batch_run");
     return batch_launch(b, llr_dev, bits_dev, pm_dev, ok_dev, slot_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -19,6 +19,7 @@ POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
 POLAR_EUNSUPPORTED, POLAR_ETIMEDOUT, POLAR_EBUSY = -4, -5, -6
 LLR_F32, LLR_I8 = 0, 1
 SPC_MAX_4, SPC_ANY, NO_SPECIAL_NODES, HOST_ONLY, SYSTEMATIC = 0, 1, 2, 0x100, 0x200
+INJECT_ALLOC_FAIL, INJECT_POISON = 1, 2
 
 # Every symbol include/polar.h declares.
 EXPORTED = [
@@ -29,6 +30,7 @@ EXPORTED = [
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
     "polar_server_create", "polar_server_destroy", "polar_server_submit", "polar_server_poll", "polar_server_wait",
     "polar_server_pause", "polar_server_stats", "polar_adaptive_decode", "polar_list_decode_host",
+    "polar_debug_inject",
 ]
 
 
@@ -129,6 +131,7 @@ def _lib():
         lib.polar_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats), i32]
         lib.polar_adaptive_decode.argtypes = [vp, vp, vp, i32, u32, vp, vp, vp, vp, vp, vp]
         lib.polar_list_decode_host.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
+        lib.polar_debug_inject.argtypes = [i32, ctypes.c_int64]
         for name in EXPORTED:
             if name != "polar_strerror":
                 getattr(lib, name).restype = i32
@@ -140,6 +143,11 @@ def _lib():
 def load_library():
     """Load the C-ABI library (raises if it is not built)."""
     return _lib()
+
+
+def debug_inject(what: int, value: int):
+    """polar_debug_inject: host-side fault injection for tests."""
+    _check(_lib().polar_debug_inject(what, value), "polar_debug_inject")
 
 
 def _check(status: int, what: str):
