@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--skip-fer", action="store_true")
     ap.add_argument("--skip-ablation", action="store_true")
     ap.add_argument("--skip-wide", action="store_true")
+    ap.add_argument("--skip-rates", action="store_true")
     ap.add_argument("--wide-frames", type=int, default=1 << 14)
     ap.add_argument("--ablation-frames", type=int, default=1 << 17)
     ap.add_argument("--fer-frames", type=int, default=1 << 17, help="frames per Eb/N0 point of the FER sweep")
@@ -397,6 +398,48 @@ def measure_wide(args, torch, dev, stream):
             "rows": rows}
 
 
+def measure_rates(args, torch, dev, stream):
+    """The polar side of the paper's LDPC comparison (Table IV shape): systematic
+    polar-CRC codes of length 1024 at rates 1/2, 2/3, 3/4, 5/6 (payload
+    k = rate * 1024, CRC-8 inside K), L = 2, f32 at 3.5 dB; throughput of a
+    2^17-frame batch and the latency of one frame decoded alone, autotuned."""
+    from paper_1505_01466_gb300 import inputs as I
+    from paper_1505_01466_gb300.polar import PolarCode
+    rows = []
+    for num, den in ((1, 2), (2, 3), (3, 4), (5, 6)):
+        kr = int(round(1024 * num / den))
+        Kr = kr + 8
+        frozen = I.ga_frozen_mask(1024, Kr, 3.5, kr / 1024)
+        fr = I.make_frames_chunked(frozen, 8, I.CRC8_POLY, 3.5, 16384, seed=kr, systematic=True)
+        x = torch.from_numpy(fr.llr_f32).to(dev)
+        llr = x.repeat(8, 1).contiguous()
+        code = PolarCode(frozen, 8, I.CRC8_POLY, 2, systematic=True)
+        code.autotune(llr[:16384], stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            code.decode(llr, stream=stream)
+            a.record(stream)
+            out = code.decode(llr, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        lat = []
+        for _ in range(7):
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                code.decode(llr[:1], stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            lat.append(a.elapsed_time(b) * 1e3)
+        got = I.unpack_bits_lsb(out[0][:16384].cpu().numpy(), kr)
+        rows.append({"rate": f"{num}/{den}", "K": Kr, "k": kr, "gbps": kr * llr.shape[0] / ms / 1e6,
+                     "one_frame_latency_us": statistics.median(lat[2:]),
+                     "fer": float((got != fr.payload).any(axis=1).mean())})
+        code.close()
+        del llr, x
+    return {"code": "systematic polar-CRC (1024, k) + CRC-8, L=2, f32, GA 3.5 dB, Eb/N0 3.5 dB", "rows": rows}
+
+
 def measure_batched(args, torch, dev, stream, barrier):
     """125-class Zipf mix (int8, 4 dB): one graph-replayed persistent launch vs
     one plain launch per class, same frames."""
@@ -705,6 +748,9 @@ def run_ours(args):
     wide = None
     if rank == 0 and not args.skip_wide:
         wide = measure_wide(args, torch, dev, stream)
+    rates = None
+    if rank == 0 and not args.skip_rates:
+        rates = measure_rates(args, torch, dev, stream)
 
     batched = None
     if not args.skip_batched:
@@ -737,6 +783,7 @@ def run_ours(args):
             "fer": fer_sweep,
             "ablation": ablation,
             "wide_lists": wide,
+            "rates_table4": rates,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
