@@ -129,6 +129,9 @@ POLAR_API int polar_code_destroy(polar_code_t *code);
  *                    selection); may be NULL.
  * Re-entrant: concurrent calls on distinct streams are safe (each call takes
  * its own scratch from the stream-ordered allocator when the code needs any).
+ * A call with no more frames than the device has SMs runs them with a
+ * latency shape (four warps and a CTA's shared memory per frame) unless
+ * polar_code_set_launch fixed the shape; results do not depend on the shape.
  * Errors: POLAR_EINVAL (NULL code/required pointer, bad dtype, host-only
  * code), POLAR_ENOMEM (scratch), POLAR_ECUDA (launch failure). n_frames = 0
  * is a no-op. */

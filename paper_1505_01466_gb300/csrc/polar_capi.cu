@@ -53,6 +53,11 @@ struct polar_code {
     uint16_t *d_info = nullptr;
     unsigned long long *d_desc = nullptr;
     LaunchShape shape[2];
+    // Latency shape for small batches (at most one frame per SM): 4 warps per
+    // frame, as much shared memory as a CTA has. Used unless set_launch fixed
+    // the shape.
+    LaunchShape lat[2];
+    bool explicit_shape[2] = {false, false};
     // L = 64 / 128: the wide kernel over the fully unrolled schedule
     bool wide = false;
     uint32_t *d_xops = nullptr;
@@ -347,6 +352,8 @@ void free_device(polar_code *c) {
     for (int d = 0; d < 2; ++d) {
         if (c->shape[d].d_ops) cudaFree(c->shape[d].d_ops);
         c->shape[d].d_ops = nullptr;
+        if (c->lat[d].d_ops) cudaFree(c->lat[d].d_ops);
+        c->lat[d].d_ops = nullptr;
     }
     if (c->d_syn) cudaFree(c->d_syn);
     if (c->d_info) cudaFree(c->d_info);
@@ -498,8 +505,12 @@ int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx = nullptr,
                const uint32_t *frame_cnt = nullptr) {
     if (code->wide) return decode_wide(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
-    return decode_shape(code, dtype, code->shape[dtype], llr, n_frames, bits, pm, ok, slot, st, frame_idx,
-                        frame_cnt);
+    // a batch no larger than the SM count is latency-bound: give each frame a
+    // CTA of its own with everything on chip (unless the shape was fixed)
+    const bool small = n_frames <= (uint32_t)code->sm_count && !frame_idx;
+    const LaunchShape &sh = (small && !code->explicit_shape[dtype] && code->lat[dtype].d_ops) ? code->lat[dtype]
+                                                                                                : code->shape[dtype];
+    return decode_shape(code, dtype, sh, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
 }
 
 // ---- allocation-free decoding ----------------------------------------------
@@ -618,6 +629,12 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
         }
         *out = c;
         return POLAR_OK;
+    }
+    for (int d = 0; d < 2; ++d) {
+        LaunchShape lat;
+        if (!c->host_only && make_shape(c, d, 4, 0xffffffffu, lat, 128) &&
+            upload(&lat.d_ops, flag_ops(c->ops, 4)) == cudaSuccess)
+            c->lat[d] = lat;
     }
     for (int d = 0; d < 2; ++d) {
         LaunchShape sh;
@@ -840,6 +857,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     if (warps_out) *warps_out = best_w;
     if (budget_out) *budget_out = best_b == 0xffffffffu ? 0u : best_b;
     if (cta_out) *cta_out = best_t;
+    code->explicit_shape[llr_dtype] = false;
     return install_shape(code, llr_dtype, best);
 }
 
@@ -1266,7 +1284,9 @@ int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_fra
     if (c->wide) return POLAR_EUNSUPPORTED;
     LaunchShape sh;
     if (!make_shape(c, llr_dtype, warps_per_frame, smem_budget, sh, cta_threads)) return POLAR_EINVAL;
-    return install_shape(c, llr_dtype, sh);
+    const int st = install_shape(c, llr_dtype, sh);
+    if (st == POLAR_OK) c->explicit_shape[llr_dtype] = true;
+    return st;
 }
 
 }  // extern "C"

@@ -266,3 +266,31 @@ def test_full_size_in_the_benchmark_launch_configuration(torch_cuda, oracle_mod,
     g = tuple(t[last][torch.from_numpy(sample).cuda()].cpu().numpy() for t in (bits, pm, ok, slot))
     assert_parity(g, o, dtype, "full size, sampled")
     code.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_small_batches_take_the_latency_shape(torch_cuda, oracle_mod, dtype):
+    # at most one frame per SM: four warps and a CTA's shared memory per frame;
+    # a fixed shape (set_launch) is kept, and the results never depend on it
+    from paper_1505_01466_gb300.polar import PolarCode
+    torch = torch_cuda
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 100, seed=55)
+    x = torch.from_numpy(f.llr_i8 if dtype == "i8" else f.llr_f32).cuda()
+    code = PolarCode(fr, 32, I.CRC32_POLY, 32)
+    small = [t.cpu() for t in code.decode(x)]                      # latency shape
+    code.set_launch(1 if dtype == "i8" else 0, 1, 7000, 512)        # fixed shape from now on
+    fixed = [t.cpu() for t in code.decode(x)]
+    for a, b in zip(small, fixed):
+        assert torch.equal(a, b)
+    o = oracle_mod.decode(fr, 32, (f.llr_i8 if dtype == "i8" else f.llr_f32)[:24], 32, I.CRC32_POLY, 0,
+                          n_threads=NT)
+    assert_parity(tuple(t[:24].numpy() for t in small), o, dtype, "latency shape")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    code.autotune(x.repeat(64, 1))                                  # autotune lifts the fix
+    ev0.record()
+    code.decode(x[:1])
+    ev1.record()
+    torch.cuda.synchronize()
+    assert ev0.elapsed_time(ev1) < 50.0
+    code.close()
