@@ -121,11 +121,42 @@ __device__ __forceinline__ int cta_excl_scan(int x, int *scan, int *total) {
     return base + v - x;
 }
 
-// Exact L-th smallest of keys[0, M) (M > L): bitonic sort of a padded copy.
-__device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, int L) {
+// Exact L-th smallest of keys[0, M) (M = La * C > L), source t owning
+// keys[t*C, t*C + C). With a full list (La = L) the answer is at most t0, the
+// largest of the sources' best keys, so only keys <= t0 are sorted: the L
+// best keys plus the few later candidates below t0. Otherwise all M keys are.
+__device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, int L, int La, int C) {
+    const int t = threadIdx.x;
+    unsigned long long t0 = KINF64;
+    if (La == L) {
+        unsigned long long m = 0ull;
+        if (t < La) {
+            m = KINF64;
+            for (int c = 0; c < C; ++c) m = s.keys[t * C + c] < m ? s.keys[t * C + c] : m;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULLW, m, d);
+            m = o > m ? o : m;
+        }
+        if ((t & 31) == 0) s.red[t >> 5] = m;
+        __syncthreads();
+        t0 = s.red[0];
+        for (int w = 1; w < ((int)blockDim.x >> 5); ++w) t0 = s.red[w] > t0 ? s.red[w] : t0;
+        __syncthreads();
+    }
+    // compact the keys <= t0 (all of them without a full list)
+    int cnt = 0;
+    if (t < La)
+        for (int c = 0; c < C; ++c) cnt += s.keys[t * C + c] <= t0 ? 1 : 0;
+    int S = 0;
+    int off = cta_excl_scan(cnt, s.scan, &S);
+    if (S == L) return t0;               // no later candidate below t0
+    if (t < La)
+        for (int c = 0; c < C; ++c)
+            if (s.keys[t * C + c] <= t0) s.sortb[off++] = s.keys[t * C + c];
     int P = 1;
-    while (P < M) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) s.sortb[i] = i < M ? s.keys[i] : KINF64;
+    while (P < S) P <<= 1;
+    for (int i = S + t; i < P; i += blockDim.x) s.sortb[i] = KINF64;
     __syncthreads();
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -212,17 +243,53 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
             const int bwc = beta_words(jo);
             const uint32_t *blb = reinterpret_cast<const uint32_t *>(G + v.gbl[jo]);
             T *outb = reinterpret_cast<T *>(G + v.galpha[jo]);
-            for (int e = t; e < (La << jo); e += nt) {
-                const int p = e >> jo, i = e & (h - 1);
-                const T *in = wrow<T>(v, G, s, cur, p, j);
-                T r;
-                if (kind == OP_F) {
-                    r = WA<T>::f(in[i], in[i + h]);
-                } else {
-                    const uint32_t bit = (blb[(int)s.bidx[cur][p * 16 + jo] * bwc + (i >> 5)] >> (i & 31)) & 1u;
-                    r = WA<T>::g(in[i], in[i + h], bit);
+            if (h >= 4) {
+                // four consecutive elements per item (16-byte float / 4-byte int8 vectors)
+                const int lq = jo - 2;
+                for (int e = t; e < (La << lq); e += nt) {
+                    const int p = e >> lq, i = (e & ((h >> 2) - 1)) << 2;
+                    const T *in = wrow<T>(v, G, s, cur, p, j);
+                    uint32_t bits4 = 0u;
+                    if (kind == OP_G)
+                        bits4 = (blb[(int)s.bidx[cur][p * 16 + jo] * bwc + (i >> 5)] >> (i & 31)) & 15u;
+                    T x[4], y[4], r[4];
+                    if (sizeof(T) == 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(in + i);
+                        const float4 b = *reinterpret_cast<const float4 *>(in + i + h);
+                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                        for (int q = 0; q < 4; ++q) { x[q] = (T)av[q]; y[q] = (T)bv[q]; }
+                    } else {
+                        const uint32_t a = *reinterpret_cast<const uint32_t *>(in + i);
+                        const uint32_t b = *reinterpret_cast<const uint32_t *>(in + i + h);
+                        for (int q = 0; q < 4; ++q) {
+                            x[q] = (T)(int8_t)((a >> (8 * q)) & 0xFF);
+                            y[q] = (T)(int8_t)((b >> (8 * q)) & 0xFF);
+                        }
+                    }
+                    for (int q = 0; q < 4; ++q)
+                        r[q] = kind == OP_F ? WA<T>::f(x[q], y[q]) : WA<T>::g(x[q], y[q], (bits4 >> q) & 1u);
+                    T *o = outb + ((size_t)p << jo) + i;
+                    if (sizeof(T) == 4) {
+                        *reinterpret_cast<float4 *>(o) = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+                    } else {
+                        *reinterpret_cast<uint32_t *>(o) = ((uint32_t)(uint8_t)r[0]) | ((uint32_t)(uint8_t)r[1] << 8) |
+                                                           ((uint32_t)(uint8_t)r[2] << 16) |
+                                                           ((uint32_t)(uint8_t)r[3] << 24);
+                    }
                 }
-                outb[((size_t)p << jo) + i] = r;
+            } else {
+                for (int e = t; e < (La << jo); e += nt) {
+                    const int p = e >> jo, i = e & (h - 1);
+                    const T *in = wrow<T>(v, G, s, cur, p, j);
+                    T r;
+                    if (kind == OP_F) {
+                        r = WA<T>::f(in[i], in[i + h]);
+                    } else {
+                        const uint32_t bit = (blb[(int)s.bidx[cur][p * 16 + jo] * bwc + (i >> 5)] >> (i & 31)) & 1u;
+                        r = WA<T>::g(in[i], in[i + h], bit);
+                    }
+                    outb[((size_t)p << jo) + i] = r;
+                }
             }
             // this op reads only the stage-j entries of the index rows
             if (t < La) s.idx[cur][t * 16 + jo] = (uint8_t)t;
@@ -293,13 +360,26 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
                     const int R = kind == OP_R1 ? 2 : 4;
                     unsigned long long top[4] = {KINF64, KINF64, KINF64, KINF64};
                     int neg = 0;
-                    for (int i = 0; i < nv; ++i) {
-                        const T a = row[i];
-                        neg += a < (T)0 ? 1 : 0;
-                        unsigned long long key = ((unsigned long long)WA<T>::absbits(a) << 16) | (unsigned)i;
-                        if (key < top[R - 1]) {
-                            for (int r = 0; r < R; ++r)
-                                if (key < top[r]) { const unsigned long long x = top[r]; top[r] = key; key = x; }
+                    for (int i0 = 0; i0 < nv; i0 += 4) {
+                        T q[4];
+                        const int nq = nv < 4 ? nv : 4;
+                        if (nv >= 4 && sizeof(T) == 4) {
+                            const float4 f = *reinterpret_cast<const float4 *>(row + i0);
+                            q[0] = (T)f.x; q[1] = (T)f.y; q[2] = (T)f.z; q[3] = (T)f.w;
+                        } else if (nv >= 4) {
+                            const uint32_t w = *reinterpret_cast<const uint32_t *>(row + i0);
+                            for (int e = 0; e < 4; ++e) q[e] = (T)(int8_t)((w >> (8 * e)) & 0xFF);
+                        } else {
+                            for (int e = 0; e < nq; ++e) q[e] = row[i0 + e];
+                        }
+                        for (int e = 0; e < nq; ++e) {
+                            const T a = q[e];
+                            neg += a < (T)0 ? 1 : 0;
+                            unsigned long long key = ((unsigned long long)WA<T>::absbits(a) << 16) | (unsigned)(i0 + e);
+                            if (key < top[R - 1]) {
+                                for (int r = 0; r < R; ++r)
+                                    if (key < top[r]) { const unsigned long long x = top[r]; top[r] = key; key = x; }
+                            }
                         }
                     }
                     P ar[4];
@@ -334,7 +414,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
             // ---------------- selection (Algorithm 1) ----------------
             const int M = La * C;
             const int keep = M < L ? M : L;
-            const unsigned long long tau = M > L ? cta_kth(s, M, L) : KINF64;
+            const unsigned long long tau = M > L ? cta_kth(s, M, L, La, C) : KINF64;
             // survivors in (source, candidate) order: thread t scans items [t*q, t*q + q)
             const int q = (M + nt - 1) / nt;
             int cnt = 0;
@@ -366,7 +446,21 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
                     for (int w = 0; w < bw; ++w) {
                         uint32_t word = 0;
                         const int lim = nv < 32 ? nv : 32;
-                        for (int i = 0; i < lim; ++i) word |= (srow[32 * w + i] < (T)0 ? 1u : 0u) << i;
+                        if (lim >= 4 && sizeof(T) == 4) {
+                            for (int i = 0; i < lim; i += 4) {
+                                const float4 f = *reinterpret_cast<const float4 *>(srow + 32 * w + i);
+                                word |= ((f.x < 0.f ? 1u : 0u) | (f.y < 0.f ? 2u : 0u) | (f.z < 0.f ? 4u : 0u) |
+                                         (f.w < 0.f ? 8u : 0u)) << i;
+                            }
+                        } else if (lim >= 4) {
+                            for (int i = 0; i < lim; i += 4) {
+                                const uint32_t x = *reinterpret_cast<const uint32_t *>(srow + 32 * w + i);
+                                const uint32_t sg = (x >> 7) & 0x01010101u;     // sign bit of each byte
+                                word |= (((sg * 0x01020408u) >> 24) & 0xFu) << i;
+                            }
+                        } else {
+                            for (int i = 0; i < lim; ++i) word |= (srow[32 * w + i] < (T)0 ? 1u : 0u) << i;
+                        }
                         for (int r = 0; r < 4; ++r) {
                             const uint32_t m = s.mpos[sp * 4 + r];
                             if (((dm >> r) & 1u) && (int)(m >> 5) == w) word ^= 1u << (m & 31u);
