@@ -73,6 +73,12 @@
  *      N_v <= 4 in mode OR_SPC4) -> SPC; otherwise split (Sec. II-D). In
  *      mode OR_BITWISE every node longer than one bit is split.
  *
+ * Pins: every mode is checked by the tests against brute-force ML, noiseless
+ * frames, a textbook SC decoder, the Fig. 1 / Listing 2 example and FER
+ * agreement between modes. Parity unpinned: SPC nodes longer than four bits
+ * (mode OR_SPC_ANY) are not exhaustive, so nothing outside this file fixes
+ * their list exactly; the paper only expects a small FER loss for them.
+ *
  * Build: cc -O2 -std=c11 -ffp-contract=off -fPIC -shared -pthread.
  */
 #include <stdint.h>

@@ -294,3 +294,14 @@ def test_small_batches_take_the_latency_shape(torch_cuda, oracle_mod, dtype):
     torch.cuda.synchronize()
     assert ev0.elapsed_time(ev1) < 50.0
     code.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("L", [32, 128])
+def test_maximum_sizes(torch_cuda, oracle_mod, dtype, L):
+    # the largest code length (4096) with the largest narrow and wide lists
+    fr = I.ga_frozen_mask(4096, 3686, 4.0, 3654 / 4096)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 24 if L == 32 else 8, seed=4096 + L)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    g, o = run_case(torch_cuda, oracle_mod, fr, 32, I.CRC32_POLY, L, llr)
+    assert_parity(g, o, dtype, f"(4096,3686) L={L}")
