@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--pool-frames", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-rate", type=float, default=2e5, help="offered frames per second")
+    ap.add_argument("--serve-warps", type=int, default=0, help="server warps per frame (0: library default)")
+    ap.add_argument("--serve-budget", type=int, default=0, help="server shared memory per frame (0: default)")
     ap.add_argument("--launch", default=None,
                     help="WARPS,SMEM_BUDGET[,CTA_THREADS]: fixed launch shape instead of autotuning")
     ap.add_argument("--skip-fer", action="store_true")
@@ -540,7 +542,8 @@ def measure_serving(args):
     rng = np.random.default_rng(2024)
     mean_size = 4096.0 / np.log(4097.0)
     lam = args.serve_rate / mean_size                      # requests per second
-    srv = PolarServer(device_mem_budget=8 << 30, max_frames_in_flight=1 << 21)
+    srv = PolarServer(device_mem_budget=8 << 30, max_frames_in_flight=1 << 21, warps_per_frame=args.serve_warps,
+                      smem_budget=args.serve_budget)
     # warm-up: register every code, both dtypes
     for c, p in enumerate(pools):
         for dt in ("f32", "i8"):
@@ -587,6 +590,7 @@ def measure_serving(args):
         "max_ms": st["max_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
         "info_gbps": st["info_bits"] / (st["span_us"] * 1e-6) / 1e9 if st["span_us"] > 0 else None,
         "batches": st["batches"], "max_batches_in_flight": st["max_batches_in_flight"],
+        "server_launch": {"warps_per_frame": args.serve_warps or 1, "smem_budget": args.serve_budget or 7000},
     }
 
 

@@ -321,7 +321,8 @@ typedef struct {
 
 enum { POLAR_SERVER_PAUSED = 1 };   /* create with admission paused (tests) */
 
-/* warps_per_frame 0 = 4; smem_budget 0 = default per-frame shared-memory budget. */
+/* warps_per_frame 0 = 1; smem_budget 0 = default per-frame shared-memory budget
+ * (7000 bytes with one warp per frame: larger stages go to scratch). */
 POLAR_API int polar_server_create(polar_server_t **out, size_t device_mem_budget, uint32_t max_frames_in_flight,
                                   uint32_t warps_per_frame, uint32_t smem_budget, uint32_t flags);
 /* Stops the engine after the batches in flight and frees everything; results

@@ -1434,8 +1434,11 @@ int srv_register(polar_server *s, const polar_code *c, uint32_t &idx) {
 uint32_t srv_view_bytes() { return al16((uint32_t)sizeof(CodeView) + 16u); }
 
 // Shared memory per CTA and grid for a dtype's batches.
+// Server launches: 256-thread CTAs (lockstep units of up to 8 frames of one code).
+constexpr int kSrvCtaThreads = 256;
+
 void srv_shape(const polar_server *s, int d, uint32_t &group_bytes, uint32_t &cta_smem, int &gpc) {
-    gpc = 4 / s->warps;
+    gpc = kSrvCtaThreads / (32 * s->warps);
     group_bytes = srv_view_bytes() + s->frame_bytes[d];
     cta_smem = group_bytes * (uint32_t)gpc;
 }
@@ -1519,7 +1522,7 @@ int srv_launch(polar_server *s, int i) {
     uint32_t group_bytes, cta_smem;
     int gpc;
     srv_shape(s, d, group_bytes, cta_smem, gpc);
-    const int occ = occupancy_batch(d, s->warps, cta_smem, 128);
+    const int occ = occupancy_batch(d, s->warps, cta_smem, kSrvCtaThreads);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * s->sm_count;
     const uint64_t need = (n_items + gpc - 1) / gpc;
@@ -1548,7 +1551,7 @@ int srv_launch(polar_server *s, int i) {
     p.group_bytes = group_bytes;
     p.view_bytes = srv_view_bytes();
     p.groups_per_cta = gpc;
-    okc &= launch_batch(d, s->warps, p, (int)grid, cta_smem, 128, st) == cudaSuccess;
+    okc &= launch_batch(d, s->warps, p, (int)grid, cta_smem, kSrvCtaThreads, st) == cudaSuccess;
     for (SrvReq *r : take) {
         const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
         okc &= cudaMemcpyAsync(s->h_arena + bits_base, s->d_arena + bits_base, r->bits_sz, cudaMemcpyDeviceToHost,
@@ -1661,15 +1664,19 @@ int polar_server_create(polar_server_t **out, size_t device_mem_budget, uint32_t
     if (!out) return POLAR_EINVAL;
     *out = nullptr;
     if (device_mem_budget < 4096 || max_frames_in_flight == 0 || (flags & ~POLAR_SERVER_PAUSED)) return POLAR_EINVAL;
-    if (warps_per_frame == 0) warps_per_frame = 4;
+    if (warps_per_frame == 0) warps_per_frame = 1;
     if (warps_per_frame != 1 && warps_per_frame != 2 && warps_per_frame != 4) return POLAR_EINVAL;
     polar_server *s = new (std::nothrow) polar_server();
     if (!s) return POLAR_ENOMEM;
     s->warps = (int)warps_per_frame;
-    const uint32_t gpc = 4u / warps_per_frame;
+    const uint32_t gpc = (uint32_t)kSrvCtaThreads / (32u * warps_per_frame);
     const uint32_t cap = kMaxSmemPerCta / gpc - al16((uint32_t)sizeof(CodeView) + 16u);
+    // default: one warp per frame with a small shared-memory share (larger
+    // stages in scratch), the shape that gives the mixed request stream of the
+    // benchmark its lowest p50 / p99 latency (four lockstep groups per CTA)
     s->smem_budget = smem_budget ? std::min(smem_budget, cap)
-                                 : std::min(cap, (kMaxSmemPerCta / (warps_per_frame == 4 ? 4u : (warps_per_frame == 2 ? 6u : 8u))) & ~15u);
+                                 : std::min(cap, warps_per_frame == 1 ? 7000u
+                                                                     : (kMaxSmemPerCta / (warps_per_frame == 4 ? 4u : 6u)) & ~15u);
     s->arena_bytes = device_mem_budget;
     s->max_frames = max_frames_in_flight;
     s->max_pending = 1u << 16;
