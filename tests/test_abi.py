@@ -138,3 +138,28 @@ def test_fer_statistics_helpers():
     assert t["errors"] == [120, 120] and t["only_first_failed"] == 1 and t["match"] and not t["underpowered"]
     c = np.zeros(1000, bool); c[:10] = True
     assert not bench.paired_fer_test(a, c)["match"]
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # the product path has no CPU fallback: a missing library is an ImportError
+    import subprocess
+    import sys
+    code = ("import paper_1505_01466_gb300.polar as p\n"
+            f"p.LIB_PATH = {str(tmp_path / 'missing.so')!r}\n"
+            "try:\n    p.PolarCode([1, 0, 1, 0, 1, 1, 0, 0], 0, 0, 2)\n"
+            "except ImportError as e:\n    print('import-error', e)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, timeout=120)
+    assert out.returncode == 0 and "import-error" in out.stdout, out.stderr[-1000:]
+
+
+def test_workload_pools_cover_the_batched_mix():
+    from paper_1505_01466_gb300 import workloads as WL
+    pools = WL.class_pools(pool_frames=4, seed=3)
+    assert len(pools) == 125
+    shapes = {(p.N, p.L) for p in pools}
+    assert {N for N, _ in shapes} == {256, 512, 1024, 2048, 4096} and {L for _, L in shapes} == {2, 4, 8, 16, 32}
+    p = pools[7]
+    x = p.rows(2, 3, "i8")
+    assert x.shape == (3, p.N) and x.dtype == np.int8
+    assert np.array_equal(p.rows(5, 1, "f32")[0], p.rows(1, 1, "f32")[0])      # rows wrap around the pool
