@@ -213,6 +213,27 @@ __device__ __forceinline__ K warp_kth(const K (&k)[8], int C, int L, int La, int
         const int base = warp_excl_scan(t, lane);
         const int tot = __shfl_sync(FULL, base + t, 31);
         if (tot == 0) return t0;
+        if (tot <= 3) {
+            // few extra keys: the result is the (tot + 1)-th largest of the L
+            // best keys and the extras; take the largest tot times away
+            if (t > 0) {
+#pragma unroll
+                for (int r = 1; r < 8; ++r)
+                    if (r <= t) tmp[base + r - 1] = k[r];
+            }
+            __syncwarp();
+            K c0 = lane < La ? k[0] : (K)0;
+            K c1 = lane < tot ? tmp[lane] : (K)0;
+            __syncwarp();
+            for (int r = 0;; ++r) {
+                K m = kmax(c0, c1);
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) m = kmax(m, __shfl_xor_sync(FULL, m, d));
+                if (r == tot) return m;
+                if (c0 == m) c0 = (K)0;
+                else if (c1 == m) c1 = (K)0;
+            }
+        }
         if (tot <= L) {
 #pragma unroll
             for (int r = 1; r < 8; ++r)
