@@ -155,6 +155,7 @@ typedef struct {
     uint32_t spill_mask[2];          /* alpha stages kept in global scratch */
 } polar_code_info_t;
 
+/* Fill *info (host memory, caller-owned). Errors: POLAR_EINVAL (NULL). */
 POLAR_API int polar_code_get_info(const polar_code_t *code, polar_code_info_t *info);
 
 /* The unrolled operation list (Listing 2) as triples (kind, N_v, first u
@@ -175,7 +176,10 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
  * shared memory of one frame (0 = default), larger alpha stages move to
  * global scratch to meet it; cta_threads (a multiple of 32 * warps_per_frame,
  * at most 512; 0 = 128) sets how many frame groups share a CTA and run the
- * schedule in lockstep. POLAR_EINVAL if the shape cannot hold the code. */
+ * schedule in lockstep. Later decodes of that dtype keep this shape even for
+ * small batches. Errors: POLAR_EINVAL (bad arguments, or the shape cannot
+ * hold the code), POLAR_EUNSUPPORTED (a wide code, L > 32), POLAR_ENOMEM /
+ * POLAR_ECUDA (uploading the flagged schedule). */
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                                     uint32_t smem_budget, uint32_t cta_threads);
 
