@@ -61,7 +61,7 @@ enum polar_status {
     POLAR_EINVAL = -1,        /* an argument is out of range or NULL */
     POLAR_ENOMEM = -2,        /* host or device allocation failed */
     POLAR_ECUDA = -3,         /* a CUDA call failed (no device, launch error, ...) */
-    POLAR_EUNSUPPORTED = -4,  /* valid request this build does not support */
+    POLAR_EUNSUPPORTED = -4,  /* a valid request the library does not support */
     POLAR_ETIMEDOUT = -5,     /* a bounded device or host wait ran out */
     POLAR_EBUSY = -6          /* no room right now (serving admission) */
 };
