@@ -8,8 +8,8 @@ use it; the product decoder never does.
 
 Modes: ``BITWISE`` (SC-list, length-one leaves), ``SPC4`` (the paper's
 "Dec-SPC-4"), ``SPC_ANY`` ("Dec-SPC-4+"); any of them | ``SYSTEMATIC`` for a
-systematic code. Parity unpinned: ``SPC_ANY`` (SPC nodes longer than four
-bits are not exhaustive, so no external result fixes their list).
+systematic code. ``SPC_ANY``'s long SPC nodes are not exhaustive; the tests
+pin them against an independent Chase-II enumeration instead of brute-force ML.
 """
 
 from __future__ import annotations

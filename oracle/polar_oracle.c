@@ -75,9 +75,10 @@
  *
  * Pins: every mode is checked by the tests against brute-force ML, noiseless
  * frames, a textbook SC decoder, the Fig. 1 / Listing 2 example and FER
- * agreement between modes. Parity unpinned: SPC nodes longer than four bits
- * (mode OR_SPC_ANY) are not exhaustive, so nothing outside this file fixes
- * their list exactly; the paper only expects a small FER loss for them.
+ * agreement between modes. SPC nodes longer than four bits (mode OR_SPC_ANY)
+ * are not exhaustive, so brute-force ML does not fix them; their candidate
+ * lists are pinned instead against an independent Chase-II enumeration (all
+ * flips of the four least reliable bits, even weight).
  *
  * Build: cc -O2 -std=c11 -ffp-contract=off -fPIC -shared -pthread.
  */

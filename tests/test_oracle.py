@@ -336,3 +336,42 @@ def test_systematic_mode(oracle_mod, mode):
     b, _, ok, _ = oracle_mod.decode(fr, 8, f.llr_f32, 32, I.CRC32_POLY, m | oracle_mod.SYSTEMATIC)
     err = (I.unpack_bits_lsb(b, 96) != f.payload).any(axis=1)
     assert err.mean() < 0.5 and (ok[~err] == 1).all()
+
+
+def _chase2_even(y, n_lrb=4):
+    """Chase-II list of a single-parity-check code, written independently of
+    the node rule: flip every subset of the n_lrb least reliable positions of
+    the hard decision (ranked by |y|, then index), keep the even-weight words,
+    and score each by the sum of |y| over the flipped positions."""
+    y = np.asarray(y, np.float64)
+    hd = (y < 0).astype(np.uint8)
+    order = sorted(range(y.size), key=lambda i: (abs(float(y[i])), i))[:n_lrb]
+    out = []
+    for mask in range(1 << n_lrb):
+        w = hd.copy()
+        pen = 0.0
+        for r in range(n_lrb):
+            if (mask >> r) & 1:
+                w[order[r]] ^= 1
+                pen += abs(float(y[order[r]]))
+        if int(w.sum()) % 2 == 0:
+            out.append((pen, tuple(int(v) for v in w)))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_long_spc_nodes_equal_chase2(oracle_mod, N):
+    # Dec-SPC-4+ (SPC nodes of any length, Sec. III-D): a code whose only
+    # frozen bit is the first is one SPC node at the root; with L = 8 its final
+    # list is every candidate, which must be the Chase-II list over the four
+    # least reliable bits restricted to even weight
+    fr = np.zeros(N, np.uint8)
+    fr[0] = 1
+    rng = np.random.default_rng(N)
+    for _ in range(30):
+        y = np.round(rng.normal(0, 3, N), 1).astype(np.float32)
+        got = {w: p for p, w in _final_list(oracle_mod, fr, 8, y, oracle_mod.SPC_ANY)}
+        want = {w: p for p, w in _chase2_even(y)}
+        assert set(got) == set(want)                       # the same eight words
+        for w in want:                                     # with the same metrics (float32 vs float64 sums)
+            assert got[w] == pytest.approx(want[w], rel=1e-6, abs=1e-6)
