@@ -252,6 +252,17 @@ def paired_fer_test(err_a, err_b, conf: float = 0.99):
             "underpowered": min(xa, xb) < 100}
 
 
+def adaptive_throughput(k: float, fer_f: float, lat_f: float, lat_l: float, pays_both: bool = True) -> float:
+    """Information throughput of the adaptive decoder of Sec. V, k bits per
+    cost of one frame. pays_both=False is Eq. (tp) as printed: a frame that the
+    Fast-SSC pass fails costs the list latency alone. pays_both=True charges
+    such a frame both passes, as the latency equation of Sec. V does and as
+    adaptive_decode runs them; the paper's Table II follows this form more
+    closely (about 1 % against about 8 % for the printed one)."""
+    cost = lat_f + fer_f * lat_l if pays_both else (1.0 - fer_f) * lat_f + fer_f * lat_l
+    return k / cost
+
+
 def measure_fer(args, torch, dev, stream):
     """FER of the fast decoder (Dec-SPC-4) against plain SC-list decoding
     (length-one leaves, the same list size) on the same frames, and the
@@ -289,6 +300,7 @@ def measure_fer(args, torch, dev, stream):
             errs, ms = {}, {}
             for name, fn in (("fast", lambda: fast.decode(llr, stream=stream)),
                              ("scl", lambda: scl.decode(llr, stream=stream)),
+                             ("sc1", lambda: sc1.decode(llr, stream=stream)),
                              ("adaptive", lambda: adaptive_decode(sc1, fast, llr, stream=stream)),
                              ("adaptive8", lambda: adaptive_decode(sc1, fast8, llr, stream=stream))):
                 fn()                                     # warm-up
@@ -309,6 +321,10 @@ def measure_fer(args, torch, dev, stream):
                 "gbps_fast": k * args.fer_frames / ms["fast"] / 1e6,
                 "gbps_scl": k * args.fer_frames / ms["scl"] / 1e6,
                 "gbps_adaptive": k * args.fer_frames / ms["adaptive"] / 1e6,
+                "gbps_adaptive_model": adaptive_throughput(k * args.fer_frames, relisted / args.fer_frames,
+                                                           ms["sc1"], ms["fast"]) / 1e6,
+                "gbps_adaptive_eq_tp": adaptive_throughput(k * args.fer_frames, relisted / args.fer_frames,
+                                                           ms["sc1"], ms["fast"], pays_both=False) / 1e6,
                 "fer_adaptive_L8": float(errs["adaptive8"].mean()),
                 "gbps_adaptive_L8": k * args.fer_frames / ms["adaptive8"] / 1e6,
             })

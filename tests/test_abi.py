@@ -163,3 +163,54 @@ def test_workload_pools_cover_the_batched_mix():
     x = p.rows(2, 3, "i8")
     assert x.shape == (3, p.N) and x.dtype == np.int8
     assert np.array_equal(p.rows(5, 1, "f32")[0], p.rows(1, 1, "f32")[0])      # rows wrap around the pool
+
+
+def _paper_alpha_elems(N, L, V):
+    # Sec. IV-E: N channel values shared by all paths plus, per path, one stage
+    # of max(2^i, V) values for every i < log2 N
+    return N + L * sum(max(1 << i, V) for i in range(N.bit_length() - 1))
+
+
+def _paper_beta_elems(N, L, V):
+    # Sec. IV-F: per path the root stage plus a left and a right copy of every lower stage
+    return L * (N + 2 * sum(max(1 << i, V) for i in range(N.bit_length() - 1)))
+
+
+@pytest.mark.parametrize("dtype,es", [(0, 4), (1, 1)])
+@pytest.mark.parametrize("L", [4, 8, 32])
+def test_stage_memory_follows_the_paper_accounting(polar, dtype, es, L):
+    """Growth of the per-frame memory with N, everything in shared memory.
+
+    Alpha: the paper's count, N + L sum_{i<n} max(2^i, V), with V = 1 and
+    without the four lowest stages, which live in registers. Per doubling of N the formula grows by N(1 + L)
+    elements, and so must the layout. Beta: bit-packed, one left stage per
+    level plus one root row updated in place, so it grows by 2LN + N bits
+    where the paper's padded float layout grows by 3LN elements.
+    """
+    sizes = {}
+    for N in (256, 512, 1024):
+        fr = I.ga_frozen_mask(N, N // 2, 2.0)
+        code = polar.PolarCode(fr, 8, I.CRC8_POLY, L, host_only=True)
+        code.set_launch(dtype, 1, 232448, 32)
+        info = code.info()
+        if info["spill_mask"][dtype] or info["scratch_per_frame"][dtype]:
+            pytest.skip("does not fit shared memory")
+        sizes[N] = info["smem_per_frame"][dtype]
+    for N in (256, 512):
+        grow = sizes[2 * N] - sizes[N]
+        alpha = es * (_paper_alpha_elems(2 * N, L, 16) - _paper_alpha_elems(N, L, 16))
+        assert alpha == es * N * (1 + L)
+        assert grow == alpha + (2 * L * N + N) // 8
+        # the paper's beta layout would need 3LN more elements; bit packing
+        # and the in-place root row keep it below that even counted in bytes
+        assert (2 * L * N + N) // 8 < _paper_beta_elems(2 * N, L, 16) - _paper_beta_elems(N, L, 16)
+    # absolute alpha: the formula without SIMD padding (V = 1) minus the
+    # 1 + 2 + 4 + 8 register-held values of stages 0..3 of each path, in bytes
+    N = 1024
+    fr = I.ga_frozen_mask(N, N // 2, 2.0)
+    code = polar.PolarCode(fr, 8, I.CRC8_POLY, L, host_only=True)
+    code.set_launch(dtype, 1, 232448, 32)
+    per_path_tables = 2 * 16 + 2 * 16 + 2 * 4 + 8          # alpha/beta index rows, penalties, survivors
+    beta_bytes = L * 4 * (sum(max(1, (1 << j) // 32) for j in range(4, 10)) + N // 32) + N // 8
+    expect = es * (_paper_alpha_elems(N, L, 1) - 15 * L) + beta_bytes + L * per_path_tables
+    assert code.info()["smem_per_frame"][dtype] == expect

@@ -1,9 +1,12 @@
 """The benchmark's reference arm (the CPU oracle on host cores) runs without a
-GPU and prints the one-line JSON contract."""
+GPU and prints the one-line JSON contract; the throughput model of Sec. V
+reproduces the paper's Tables I and II."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -23,3 +26,47 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["N"] == 2048 and d["config"]["L"] == 32 and d["config"]["workload"]
+
+
+def _tables_1_2():
+    lat, tp, k = {}, {}, None
+    with open(os.path.join(ROOT, "tests", "golden", "adaptive_throughput_tables_1_2.txt")) as fh:
+        for line in fh:
+            f = line.split()
+            if not f or f[0].startswith("#"):
+                continue
+            if f[0] == "k":
+                k = float(f[1])
+            elif f[0] == "latency":
+                lat[int(f[1])] = float(f[2])
+            else:
+                tp[(int(f[1]), float(f[2]))] = float(f[3])
+    return k, lat, tp
+
+
+def test_adaptive_throughput_reproduces_table_2():
+    """Eq. (tp) against the paper's own tables. The Fast-SSC latency is not
+    printed; the 4.5 dB column, equal for both list sizes, gives it (the
+    Fast-SSC pass almost never fails there). At each lower point one FER_F,
+    solved from the L = 8 row and Table I's L = 8 latency, must then predict
+    the L = 32 row from Table I's L = 32 latency."""
+    sys.path.insert(0, ROOT)
+    import bench
+    k, lat, tp = _tables_1_2()
+    lat_f = k / tp[(8, 4.5)]
+    assert tp[(32, 4.5)] == tp[(8, 4.5)]
+    for pays_both, tol in ((True, 0.02), (False, 0.10)):
+        for db in (3.5, 4.0):
+            cost8 = k / tp[(8, db)]
+            fer_f = (cost8 - lat_f) / (lat[8] if pays_both else lat[8] - lat_f)
+            assert 0.0 < fer_f < 1.0
+            assert bench.adaptive_throughput(k, fer_f, lat_f, lat[8], pays_both) == pytest.approx(tp[(8, db)])
+            pred = bench.adaptive_throughput(k, fer_f, lat_f, lat[32], pays_both)
+            assert pred == pytest.approx(tp[(32, db)], rel=tol), (pays_both, db, pred)
+    # the end points: no failures gives the Fast-SSC rate, all failures the list
+    # rate (printed form) or the rate of both passes in a row
+    assert bench.adaptive_throughput(k, 0.0, lat_f, lat[32]) == pytest.approx(k / lat_f)
+    assert bench.adaptive_throughput(k, 1.0, lat_f, lat[32], False) == pytest.approx(k / lat[32])
+    assert bench.adaptive_throughput(k, 1.0, lat_f, lat[32]) == pytest.approx(k / (lat_f + lat[32]))
+    # and the list decoder alone at L = 32: 4.0 Mbps (Sec. VI-B)
+    assert round(k / lat[32], 1) == 4.0
