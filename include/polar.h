@@ -177,9 +177,12 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
  * global scratch to meet it; cta_threads (a multiple of 32 * warps_per_frame,
  * at most 512; 0 = 128) sets how many frame groups share a CTA and run the
  * schedule in lockstep. Later decodes of that dtype keep this shape even for
- * small batches. Errors: POLAR_EINVAL (bad arguments, or the shape cannot
- * hold the code), POLAR_EUNSUPPORTED (a wide code, L > 32), POLAR_ENOMEM /
- * POLAR_ECUDA (uploading the flagged schedule). */
+ * small batches. A code with L = 1 normally runs a kernel of its own
+ * (Fast-SSC decoding, one warp per frame with every stage in shared memory,
+ * no scratch); after set_launch it runs the list kernels with this shape
+ * instead, until polar_code_autotune hands it back. Errors: POLAR_EINVAL (bad
+ * arguments, or the shape cannot hold the code), POLAR_EUNSUPPORTED (a wide
+ * code, L > 32), POLAR_ENOMEM / POLAR_ECUDA (uploading the flagged schedule). */
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                                     uint32_t smem_budget, uint32_t cta_threads);
 
@@ -217,7 +220,9 @@ POLAR_API int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t
  * frames of llr_dev (device, [n_frames][N]) on `stream`, installs the fastest
  * and reports it (any out pointer may be NULL; *budget_out = 0 means no cap).
  * Blocks until the timing runs finish. Results of later decodes do not depend
- * on the shape (only speed does). Errors: POLAR_EINVAL, POLAR_ENOMEM,
+ * on the shape (only speed does). A code with L = 1 gets its own kernel back
+ * without timing anything (1 warp per frame, budget 0, 256-thread CTAs), as
+ * does a wide code (its one shape). Errors: POLAR_EINVAL, POLAR_ENOMEM,
  * POLAR_ECUDA. */
 POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out,

@@ -62,6 +62,10 @@ struct polar_code {
     bool wide = false;
     uint32_t *d_xops = nullptr;
     uint64_t wide_gbytes[2] = {0, 0};
+    // L = 1: the Fast-SSC kernel over sc1_op entries (used unless set_launch
+    // fixed a shape of the list kernels)
+    std::vector<uint32_t> sops;
+    uint32_t *d_sops = nullptr;
 };
 
 namespace {
@@ -360,6 +364,8 @@ void free_device(polar_code *c) {
     if (c->d_desc) cudaFree(c->d_desc);
     if (c->d_xops) cudaFree(c->d_xops);
     c->d_xops = nullptr;
+    if (c->d_sops) cudaFree(c->d_sops);
+    c->d_sops = nullptr;
     c->d_syn = nullptr;
     c->d_info = nullptr;
     c->d_desc = nullptr;
@@ -500,11 +506,48 @@ int decode_wide(const polar_code *code, int dtype, const void *llr, uint32_t n_f
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
-// The installed shape of the narrow kernels, or the wide kernel.
+// ---- L = 1 ----------------------------------------------------------------------
+bool use_sc1(const polar_code *c, int dtype) { return c->L == 1 && c->d_sops && !c->explicit_shape[dtype]; }
+
+// Needs no scratch: every stage of a frame sits in its warp's shared memory.
+int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
+               uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx, const uint32_t *frame_cnt) {
+    Sc1Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.ops = code->d_sops;
+    p.n_ops = (int)code->sops.size();
+    p.syn = code->d_syn;
+    p.info = code->d_info;
+    p.n = (int)code->n;
+    p.k = (int)code->k;
+    p.kb = (int)((code->k + 7) / 8);
+    p.crc_len = (int)code->crc_len;
+    p.systematic = (code->flags & POLAR_SYSTEMATIC) ? 1 : 0;
+    p.root_leaf = code->sops.size() == 1 ? 1 : 0;
+    p.warp_bytes = sc1_warp_bytes((int)code->n, dtype == POLAR_LLR_I8 ? 1 : 4, p.root_leaf != 0, &p.beta_off);
+    p.llr = llr;
+    p.bits = bits;
+    p.pm = pm;
+    p.ok = ok;
+    p.slot = slot;
+    p.n_frames = n_frames;
+    p.frame_idx = frame_idx;
+    p.frame_cnt = frame_cnt;
+    const int warps = std::min<int>(kSc1Threads / 32, (int)(kMaxSmemPerCta / (uint32_t)p.warp_bytes));
+    const int occ = occupancy_sc1(dtype, (int)code->n, p.root_leaf != 0, warps);
+    if (occ <= 0) return POLAR_ECUDA;
+    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
+    const uint64_t need = ((uint64_t)n_frames + warps - 1) / warps;
+    if (grid > need) grid = need;
+    return launch_sc1(dtype, p, (int)grid, warps, st) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
+// The installed shape of the narrow kernels, the L = 1 kernel or the wide kernel.
 int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx = nullptr,
                const uint32_t *frame_cnt = nullptr) {
     if (code->wide) return decode_wide(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
+    if (use_sc1(code, dtype)) return decode_sc1(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
     // a batch no larger than the SM count is latency-bound: give each frame a
     // CTA of its own with everything on chip (unless the shape was fixed)
     const bool small = n_frames <= (uint32_t)code->sm_count && !frame_idx;
@@ -598,6 +641,8 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     c->xops = std::move(tb.xops);
     c->desc = std::move(tb.desc);
     c->sched = std::move(tb.sched);
+    for (size_t i = 0; i < c->xops.size(); ++i)
+        c->sops.push_back(sc1_op(op_kind(c->xops[i]), (uint32_t)op_stage(c->xops[i]), (uint32_t)c->sched[3 * i + 2]));
     c->n_leaves = tb.leaves;
     c->n_r0 = tb.r0;
     c->n_r1 = tb.r1;
@@ -615,6 +660,7 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
         if (e == cudaSuccess) e = upload(&c->d_syn, c->syn);
         if (e == cudaSuccess) e = upload(&c->d_desc, c->desc);
         if (e == cudaSuccess && L > (uint32_t)kMaxL) e = upload(&c->d_xops, c->xops);
+        if (e == cudaSuccess && L == 1) e = upload(&c->d_sops, c->sops);
         if (e != cudaSuccess) {
             free_device(c);
             delete c;
@@ -800,6 +846,13 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
         if (cta_out) *cta_out = code->L;
         return POLAR_OK;
     }
+    if (code->L == 1 && code->d_sops) {   // the L = 1 kernel: one warp per frame, no budget
+        code->explicit_shape[llr_dtype] = false;
+        if (warps_out) *warps_out = 1;
+        if (budget_out) *budget_out = 0;
+        if (cta_out) *cta_out = kSc1Threads;
+        return POLAR_OK;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t kb = (code->k + 7) / 8;
     uint8_t *bits = nullptr;
@@ -872,6 +925,9 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
     if (dev != code->device) return POLAR_EINVAL;
+    if (use_sc1(code, llr_dtype))
+        return decode_sc1(code, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev,
+                          winner_slot_dev, reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr);
     const LaunchShape &sh = code->shape[llr_dtype];
     const int occ = occupancy(llr_dtype, sh);
     if (occ <= 0) return POLAR_ECUDA;
@@ -1229,6 +1285,14 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
             info->smem_per_frame[d] = wide_smem_bytes((int)c->L, (int)c->n);
             info->scratch_per_frame[d] = c->wide_gbytes[d];
             info->spill_mask[d] = (1u << c->n) - 1u;
+            continue;
+        }
+        if (c->L == 1 && !c->explicit_shape[d]) {
+            const uint32_t wb =
+                (uint32_t)sc1_warp_bytes((int)c->n, d == POLAR_LLR_I8 ? 1 : 4, c->sops.size() == 1, nullptr);
+            info->warps_per_frame[d] = 1;
+            info->frames_per_cta[d] = std::min<uint32_t>((uint32_t)kSc1Threads / 32, kMaxSmemPerCta / wb);
+            info->smem_per_frame[d] = wb;
             continue;
         }
         info->warps_per_frame[d] = (uint32_t)c->shape[d].warps;

@@ -191,4 +191,34 @@ uint32_t wide_smem_bytes(int L, int n);
 int occupancy_wide(int dtype, int L, int n);
 cudaError_t launch_wide(int dtype, const WideParams &p, int grid, cudaStream_t stream);
 
+// ---- L = 1 (Fast-SSC): one warp per frame, lanes over the elements of a node ----
+constexpr int kSc1Threads = 256;   // CTA size, unless 8 warps' shared memory does not fit
+
+// Schedule entry of the L = 1 kernel: kind | stage j << 4 | first bit s << 8.
+__host__ __device__ inline uint32_t sc1_op(uint32_t kind, uint32_t j, uint32_t s) {
+    return kind | (j << 4) | (s << 8);
+}
+
+struct Sc1Params {
+    const uint32_t *ops;           // sc1_op entries, fully unrolled (F/G/Combine/leaves)
+    int n_ops;
+    const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
+    const uint16_t *info;          // [K] information positions, ascending
+    int n, k, kb, crc_len, systematic;
+    int root_leaf;                 // the root is a leaf: its input (the channel) is copied to stage n
+    int warp_bytes, beta_off;      // shared memory of one warp; offset of its beta row
+    const void *llr;               // [n_frames][N]
+    uint8_t *bits;                 // [n_frames][kb]
+    float *pm;
+    uint8_t *ok;
+    int32_t *slot;
+    uint32_t n_frames;
+    const uint32_t *frame_idx;     // optional indirection, as in Params
+    const uint32_t *frame_cnt;
+};
+
+int sc1_warp_bytes(int n, int es, bool root_leaf, int *beta_off);
+int occupancy_sc1(int dtype, int n, bool root_leaf, int warps);
+cudaError_t launch_sc1(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t stream);
+
 }  // namespace polar
