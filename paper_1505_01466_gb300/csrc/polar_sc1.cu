@@ -13,13 +13,18 @@
 //    |alpha|                                                    (Sec. III-D)
 //
 // One warp decodes one frame, and the warps of a CTA take frames in turn
-// (persistent). The lanes run over the elements of a node. Alpha stages
-// 0..n-1 sit in the warp's shared memory (stage j at element offset 2^j), and
-// the channel row is read from global memory by the two operations at the
-// root. Only a code whose root is itself a leaf copies the channel row into
-// shared memory (stage n, offset N). Beta is one bit-packed row of N bits: a leaf writes its bits at its
-// own position and Combine (Eq. (3)) xors the right half into the left in
-// place, so at the end the row holds the codeword x.
+// (persistent). The lanes run over the elements of a node.
+//  * Alpha stages 6..n-1 sit in the warp's shared memory (stage j at element
+//    offset 2^j); the channel row is read from global memory by the two
+//    operations at the root (a code whose root is itself a leaf copies it to
+//    shared memory first).
+//  * Every node of at most 32 bits runs in registers: stage 5 in one register
+//    (element e in lane e), stages 0..4 together in another (stage j in lanes
+//    2^j .. 2^(j+1)-1), F and G by two warp shuffles each, and the node's 32
+//    beta bits in one word.
+//  * Beta is one bit-packed row of N bits in shared memory: a leaf writes its
+//    bits at its own position and Combine (Eq. (3)) xors the right half into
+//    the left in place, so at the end the row holds the codeword x.
 //
 // Float sums follow the pairwise tree s[i] = x[i] + x[i + n/2]; int8 LLRs use
 // saturated G and exact integer penalties. These are the conventions of the
@@ -51,6 +56,9 @@ template <> struct A1<float> {
     static __device__ __forceinline__ float st(float v) { return v; }
     static __device__ __forceinline__ uint32_t absbits(float a) { return __float_as_uint(fabsf(a)); }
     static __device__ __forceinline__ float absv(float a) { return fabsf(a); }
+    static __device__ __forceinline__ float unabs(uint32_t b) { return __uint_as_float(b); }
+    static __device__ __forceinline__ float negpart(float a) { return a < 0.f ? -a : 0.f; }
+    static __device__ __forceinline__ float pospart(float a) { return a > 0.f ? a : 0.f; }
 };
 
 template <> struct A1<int8_t> {
@@ -72,6 +80,9 @@ template <> struct A1<int8_t> {
     static __device__ __forceinline__ int8_t st(int v) { return (int8_t)v; }
     static __device__ __forceinline__ uint32_t absbits(int a) { return (uint32_t)abs(a); }
     static __device__ __forceinline__ int absv(int a) { return abs(a); }
+    static __device__ __forceinline__ int unabs(uint32_t b) { return (int)b; }
+    static __device__ __forceinline__ int negpart(int a) { return a < 0 ? -a : 0; }
+    static __device__ __forceinline__ int pospart(int a) { return a > 0 ? a : 0; }
 };
 
 // Four int8 LLRs in one word: F = max(min(a, b), -max(a, b)); G with the four
@@ -200,10 +211,61 @@ __device__ __forceinline__ void fg(const Sc1Params &p, T *alpha, const uint32_t 
     }
 }
 
+// Pairwise tree sum over lanes [base, base + nv) of t (zero elsewhere),
+// returned to every lane: lane base + e adds lane base + e + h, h = nv/2, ...
+template <typename V>
+__device__ __forceinline__ V wsum(V t, int nv, int base) {
+    for (int h = nv >> 1; h >= 1; h >>= 1) t = t + __shfl_down_sync(FULL, t, h);
+    return __shfl_sync(FULL, t, base);
+}
+
+// A leaf of 64 or more bits, read from its stage in shared memory (a: its
+// input, scr: the dead stage below it, scratch for float sums).
 template <typename T>
-__global__ void __launch_bounds__(kSc1Threads) sc1_kernel(const Sc1Params p) {
+__device__ void leaf_smem(int kind, const T *a, T *scr, uint32_t *bw, int nv, int s, typename A1<T>::V &pen,
+                          int lane) {
     typedef A1<T> A;
-    typedef typename A::V PT;                       // penalty: float, or exact int for int8
+    typedef typename A::V V;
+    if (kind == OP_R0) {                                               // Eq. (10)
+        pen = pen + tree_sum(a, nv, true, scr, lane);
+        for (int c = 0; c < nv / 32; ++c) put_chunk(bw, s, nv, c, false, lane);
+    } else if (kind == OP_R1) {
+        for (int c = 0; c < nv / 32; ++c) put_chunk(bw, s, nv, c, A::ld(a + 32 * c + lane) < 0, lane);
+    } else if (kind == OP_REP) {                                       // Eq. (5), ties to all zero
+        const V p0 = tree_sum(a, nv, true, scr, lane);
+        const V p1 = tree_sum(a, nv, false, scr, lane);
+        const bool one = !(p0 <= p1);
+        pen = pen + (one ? p1 : p0);
+        for (int c = 0; c < nv / 32; ++c) put_chunk(bw, s, nv, c, one, lane);
+    } else {                                                           // SPC, Sec. III-D
+        uint32_t par = 0;
+        unsigned long long best = ~0ull;
+        for (int c = 0; c < nv / 32; ++c) {
+            const int e = 32 * c + lane;
+            const V x = A::ld(a + e);
+            const unsigned long long key = ((unsigned long long)A::absbits(x) << 32) | (uint32_t)e;
+            best = key < best ? key : best;
+            par ^= (uint32_t)__popc(__ballot_sync(FULL, x < 0)) & 1u;
+            put_chunk(bw, s, nv, c, x < 0, lane);
+        }
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o2 = __shfl_xor_sync(FULL, best, off);
+            best = o2 < best ? o2 : best;
+        }
+        if (par) {
+            const int e = (int)(uint32_t)best;
+            __syncwarp();
+            if (lane == 0) bw[(s + e) >> 5] ^= 1u << ((s + e) & 31);
+            pen = pen + A::unabs((uint32_t)(best >> 32));
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSc1Threads, 6) sc1_kernel(const Sc1Params p) {
+    typedef A1<T> A;
+    typedef typename A::V V;                        // an LLR in arithmetic: float, or int for int8
+    typedef V PT;                                   // penalty: float, or exact int for int8
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -219,85 +281,104 @@ __global__ void __launch_bounds__(kSc1Threads) sc1_kernel(const Sc1Params p) {
         const uint32_t f = p.frame_idx ? p.frame_idx[i] : i;
         const T *ch = reinterpret_cast<const T *>(p.llr) + (size_t)f * N;
         PT pen = 0;
-        if (p.root_leaf) {
+        // The 32-bit window in registers: R holds alpha stages 0..4, stage j
+        // in lanes [2^j, 2^(j+1)); R5 holds stage 5, element e in lane e; W
+        // holds the window's 32 beta bits (lane 0 stores it after each change).
+        V R = 0, R5 = 0;
+        uint32_t W = 0;
+        if (p.n <= 5) {
+            if (p.n == 5) R5 = A::ldch(ch + lane);
+            else if (lane >= N && lane < 2 * N) R = A::ldch(ch + lane - N);
+        } else if (p.root_leaf) {
             T *top = stage(alpha, p.n);
             for (int e = lane; e < N; e += 32) top[e] = A::st(A::ldch(ch + e));
             __syncwarp();
         }
+        // Only operations on shared memory synchronise the warp: the window
+        // operations touch registers, and lane 0 alone stores W.
+        uint32_t op = __ldg(p.ops);
         for (int o = 0; o < p.n_ops; ++o) {
-            const uint32_t op = __ldg(p.ops + o);
+            const uint32_t next = o + 1 < p.n_ops ? __ldg(p.ops + o + 1) : 0u;
             const int kind = (int)(op & 15u), j = (int)((op >> 4) & 15u), s = (int)(op >> 8);
             const int nv = 1 << j;
-            switch (kind) {
-                case OP_F: fg<T, false>(p, alpha, bw, ch, vec_ch, j, s, lane); break;
-                case OP_G: fg<T, true>(p, alpha, bw, ch, vec_ch, j, s, lane); break;
-                case OP_COMB: {                                        // Eq. (3), in place
-                    const int h = nv >> 1;
-                    if (h >= 32) {
-                        for (int w = lane; w < (h >> 5); w += 32) bw[(s >> 5) + w] ^= bw[((s + h) >> 5) + w];
-                    } else if (lane == 0) {
-                        const uint32_t m = ((1u << h) - 1u) << (s & 31);
-                        uint32_t &w = bw[s >> 5];
-                        w ^= (w >> h) & m;
-                    }
-                    break;
+            if (kind == OP_F || kind == OP_G) {                        // Eq. (1), (2)
+                const bool isg = kind == OP_G;
+                if (j >= 7) {
+                    __syncwarp();
+                    if (isg) fg<T, true>(p, alpha, bw, ch, vec_ch, j, s, lane);
+                    else fg<T, false>(p, alpha, bw, ch, vec_ch, j, s, lane);
+                    __syncwarp();
+                } else if (j == 6) {                                   // stage 6 -> R5
+                    __syncwarp();
+                    const bool root = p.n == 6;
+                    const T *in = root ? ch : stage(alpha, 6);
+                    const V a = root ? A::ldch(in + lane) : A::ld(in + lane);
+                    const V b = root ? A::ldch(in + lane + 32) : A::ld(in + lane + 32);
+                    R5 = isg ? A::g(a, b, (W >> lane) & 1u) : A::f(a, b);
+                } else {                                               // inside the window
+                    const int h = nv >> 1, e = lane & (h - 1);
+                    const V src = j == 5 ? R5 : R;
+                    const int base = j == 5 ? 0 : nv;
+                    const V a = __shfl_sync(FULL, src, base + e);
+                    const V b = __shfl_sync(FULL, src, base + e + h);
+                    const V r = isg ? A::g(a, b, (W >> ((s & 31) + e)) & 1u) : A::f(a, b);
+                    if (lane >= h && lane < nv) R = r;
                 }
-                case OP_R0: {                                          // Eq. (10)
-                    const T *a = stage(alpha, j);
-                    pen = pen + tree_sum(a, nv, true, j > 0 ? stage(alpha, j - 1) : alpha, lane);
-                    for (int c = 0; c < (nv + 31) / 32; ++c) put_chunk(bw, s, nv, c, false, lane);
-                    break;
+            } else if (kind == OP_COMB) {                              // Eq. (3), in place
+                const int h = nv >> 1;
+                if (h >= 32) {
+                    __syncwarp();
+                    for (int w = lane; w < (h >> 5); w += 32) bw[(s >> 5) + w] ^= bw[((s + h) >> 5) + w];
+                    __syncwarp();
+                } else {
+                    W ^= (W >> h) & (((1u << h) - 1u) << (s & 31));
+                    if (lane == 0) bw[s >> 5] = W;
                 }
-                case OP_R1: {                                          // hard decisions
-                    const T *a = stage(alpha, j);
-                    for (int c = 0; c < (nv + 31) / 32; ++c) {
-                        const int e = 32 * c + lane;
-                        put_chunk(bw, s, nv, c, e < nv && A::ld(a + e) < 0, lane);
-                    }
-                    break;
-                }
-                case OP_REP: {                                         // Eq. (5), ties to all zero
-                    const T *a = stage(alpha, j);
-                    T *scr = stage(alpha, j - 1);
-                    const PT p0 = tree_sum(a, nv, true, scr, lane);
-                    const PT p1 = tree_sum(a, nv, false, scr, lane);
+            } else if (j >= 6) {
+                __syncwarp();
+                leaf_smem<T>(kind, stage(alpha, j), stage(alpha, j - 1), bw, nv, s, pen, lane);
+                __syncwarp();
+            } else {                                                   // a leaf inside the window
+                const V v = j == 5 ? R5 : R;
+                const int base = j == 5 ? 0 : nv;
+                const bool in = lane >= base && lane < base + nv;
+                const uint32_t mask = j == 5 ? FULL : ((1u << nv) - 1u);
+                uint32_t bits = 0;
+                if (kind == OP_R0) {                                   // Eq. (10)
+                    pen = pen + wsum<V>(in ? A::negpart(v) : V(0), nv, base);
+                } else if (kind == OP_R1) {
+                    bits = (__ballot_sync(FULL, in && v < 0) >> base) & mask;
+                } else if (kind == OP_REP) {                           // Eq. (5), ties to all zero
+                    const V p0 = wsum<V>(in ? A::negpart(v) : V(0), nv, base);
+                    const V p1 = wsum<V>(in ? A::pospart(v) : V(0), nv, base);
                     const bool one = !(p0 <= p1);
                     pen = pen + (one ? p1 : p0);
-                    for (int c = 0; c < (nv + 31) / 32; ++c) put_chunk(bw, s, nv, c, one && 32 * c + lane < nv, lane);
-                    break;
+                    bits = one ? mask : 0u;
+                } else {                                               // SPC, Sec. III-D
+                    bits = (__ballot_sync(FULL, in && v < 0) >> base) & mask;
+                    unsigned long long key =
+                        in ? (((unsigned long long)A::absbits(v) << 32) | (uint32_t)(lane - base)) : ~0ull;
+                    for (int off = nv >> 1; off >= 1; off >>= 1) {
+                        const unsigned long long o2 = __shfl_xor_sync(FULL, key, off);
+                        key = o2 < key ? o2 : key;
+                    }
+                    key = __shfl_sync(FULL, key, base);
+                    if (__popc(bits) & 1) {
+                        bits ^= 1u << (uint32_t)key;
+                        pen = pen + A::unabs((uint32_t)(key >> 32));
+                    }
                 }
-                case OP_SPC: {                                         // Sec. III-D
-                    const T *a = stage(alpha, j);
-                    uint32_t par = 0;
-                    unsigned long long best = ~0ull;
-                    for (int c = 0; c < (nv + 31) / 32; ++c) {
-                        const int e = 32 * c + lane;
-                        bool hd = false;
-                        if (e < nv) {
-                            const typename A::V x = A::ld(a + e);
-                            hd = x < 0;
-                            const unsigned long long key = ((unsigned long long)A::absbits(x) << 32) | (uint32_t)e;
-                            best = key < best ? key : best;
-                        }
-                        par ^= (uint32_t)__popc(__ballot_sync(FULL, hd)) & 1u;
-                        put_chunk(bw, s, nv, c, hd, lane);
-                    }
-                    for (int off = 16; off >= 1; off >>= 1) {
-                        const unsigned long long o2 = __shfl_xor_sync(FULL, best, off);
-                        best = o2 < best ? o2 : best;
-                    }
-                    if (par) {
-                        const int e = (int)(uint32_t)best;
-                        __syncwarp();
-                        if (lane == 0) bw[(s + e) >> 5] ^= 1u << ((s + e) & 31);
-                        pen = pen + A::absv(A::ld(a + e));
-                    }
-                    break;
+                if (j == 5) {
+                    W = bits;
+                } else {
+                    const int sh = s & 31;
+                    W = (W & ~(mask << sh)) | (bits << sh);
                 }
-                default: break;
+                if (lane == 0) bw[s >> 5] = W;
             }
-            __syncwarp();
+            op = next;
         }
+        __syncwarp();
 
         // ---------------- final pick (Sec. II-B) ----------------
         uint32_t acc = 0;
