@@ -339,8 +339,10 @@ def measure_fer(args, torch, dev, stream):
 
 def measure_ablation(args, torch, dev, stream):
     """Node-set ablation in the shape of the paper's Table I: (2048,1723) at
-    L = 2, 8, 32 with plain SC-list leaves, Dec-SPC-4 and Dec-SPC-4+ (L <= 8).
-    Throughput over a full batch and the latency of one frame decoded alone."""
+    L = 2, 8, 32 with plain SC-list leaves, Dec-SPC-4 and Dec-SPC-4+ (L <= 8),
+    and the same three node sets at L = 1 (SC, Fast-SSC: the first stage of
+    the adaptive decoder). Throughput over a full batch and the latency of one
+    frame decoded alone."""
     from paper_1505_01466_gb300 import inputs as I
     from paper_1505_01466_gb300.polar import PolarCode
     frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
@@ -350,7 +352,7 @@ def measure_ablation(args, torch, dev, stream):
     llr = x.repeat(reps, 1)[: args.ablation_frames].contiguous()
     k = K - CRC_LEN
     rows = []
-    for Ls in (2, 8, 32):
+    for Ls in (1, 2, 8, 32):
         for mode, name in ((2, "SC-list (length-one leaves)"), (0, "Dec-SPC-4"), (1, "Dec-SPC-4+")):
             if mode == 1 and Ls > 8:
                 continue
