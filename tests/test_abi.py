@@ -214,3 +214,24 @@ def test_stage_memory_follows_the_paper_accounting(polar, dtype, es, L):
     beta_bytes = L * 4 * (sum(max(1, (1 << j) // 32) for j in range(4, 10)) + N // 32) + N // 8
     expect = es * (_paper_alpha_elems(N, L, 1) - 15 * L) + beta_bytes + L * per_path_tables
     assert code.info()["smem_per_frame"][dtype] == expect
+
+
+def test_l1_codes_report_their_own_kernel(polar):
+    """L = 1 codes run the Fast-SSC kernel: one warp per frame, every stage in
+    shared memory, no scratch; set_launch hands them to the list kernels."""
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    code = polar.PolarCode(fr, 32, I.CRC32_POLY, 1, host_only=True)
+    info = code.info()
+    assert info["warps_per_frame"] == [1, 1] and info["frames_per_cta"] == [8, 8]
+    assert info["smem_per_frame"] == [2048 * 4 + 256, 2048 + 256]     # alpha row + beta row
+    assert info["scratch_per_frame"] == [0, 0] and info["spill_mask"] == [0, 0]
+    code.set_launch(0, 1, 7000, 512)
+    assert code.info()["frames_per_cta"][0] == 16 and code.info()["scratch_per_frame"][0] > 0
+    assert code.info()["frames_per_cta"][1] == 8                        # the other dtype keeps it
+    # a code whose root is a leaf keeps a copy of the channel row as well
+    rep = np.ones(4096, np.uint8)
+    rep[-1] = 0
+    root = polar.PolarCode(rep, 0, 0, 1, host_only=True)
+    assert root.schedule() == [(13, 4096, 0)]
+    assert root.info()["smem_per_frame"] == [2 * 4096 * 4 + 512, 2 * 4096 + 512]
+    assert root.info()["frames_per_cta"] == [232448 // (2 * 4096 * 4 + 512), 8]
