@@ -132,6 +132,8 @@ POLAR_API int polar_code_destroy(polar_code_t *code);
  * A call with no more frames than the device has SMs runs them with a
  * latency shape (four warps and a CTA's shared memory per frame) unless
  * polar_code_set_launch fixed the shape; results do not depend on the shape.
+ * The call is asynchronous: it reports launch errors; an error raised while
+ * its kernels run shows up in polar_sync (or the next CUDA call).
  * Errors: POLAR_EINVAL (NULL code/required pointer, bad dtype, host-only
  * code), POLAR_ENOMEM (scratch), POLAR_ECUDA (launch failure). n_frames = 0
  * is a no-op. */
@@ -141,6 +143,12 @@ POLAR_API int polar_list_decode(const polar_code_t *code, const void *llr_dev, i
 
 /* A short English name for a status code (never NULL). */
 POLAR_API const char *polar_strerror(int status);
+
+/* Wait until everything enqueued on `stream` (NULL: the legacy default stream)
+ * has finished, and report the errors of asynchronous work: POLAR_OK, or
+ * POLAR_ECUDA when the stream or an earlier kernel on the current device
+ * failed. Blocks the calling host thread. */
+POLAR_API int polar_sync(polar_stream_t stream);
 
 /* Facts about a code object (sizes, tree statistics, launch shape). */
 typedef struct {

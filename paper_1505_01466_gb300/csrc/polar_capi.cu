@@ -590,6 +590,12 @@ int noalloc_scratch(int device, uint8_t **out) {
 
 extern "C" {
 
+int polar_sync(polar_stream_t stream) {
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+}
+
 const char *polar_strerror(int status) {
     switch (status) {
         case POLAR_OK: return "ok";

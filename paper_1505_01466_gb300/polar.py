@@ -23,7 +23,7 @@ INJECT_ALLOC_FAIL, INJECT_POISON = 1, 2
 
 # Every symbol include/polar.h declares.
 EXPORTED = [
-    "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror",
+    "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror", "polar_sync",
     "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
     "polar_code_autotune", "polar_list_decode_noalloc", "polar_noalloc_scratch_bytes",
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
@@ -104,6 +104,7 @@ def _lib():
         lib.polar_list_decode.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
         lib.polar_strerror.argtypes = [i32]
         lib.polar_strerror.restype = ctypes.c_char_p
+        lib.polar_sync.argtypes = [vp]
         lib.polar_code_get_info.argtypes = [vp, ctypes.POINTER(CodeInfo)]
         lib.polar_code_schedule.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
         lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
@@ -143,6 +144,12 @@ def _lib():
 def load_library():
     """Load the C-ABI library (raises if it is not built)."""
     return _lib()
+
+
+def sync(stream=None):
+    """polar_sync: wait for ``stream`` (default: torch's current stream) and
+    raise PolarError if asynchronous work on the device failed."""
+    _check(_lib().polar_sync(_stream_handle(stream)), "polar_sync")
 
 
 def debug_inject(what: int, value: int):

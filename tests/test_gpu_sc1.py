@@ -142,3 +142,27 @@ def test_codes_whose_root_is_a_leaf(torch_cuda, oracle_mod, dtype):
                 llr = I.quantize_i8(llr)
                 llr[:4, :3] = -128
             _both_kernels(torch_cuda, oracle_mod, fr, 0, 0, llr, mode)
+
+
+def test_sync_waits_for_the_stream(torch_cuda, oracle_mod):
+    """polar_sync waits for a decode enqueued on a side stream and reports no
+    error; the outputs are complete afterwards without any other wait."""
+    from paper_1505_01466_gb300 import polar
+    torch = torch_cuda
+    fr = I.ga_frozen_mask(1024, 860, 4.0, 828 / 1024)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 512, seed=12)
+    o = oracle_mod.decode(fr, 1, f.llr_f32, 32, I.CRC32_POLY, 0, n_threads=NT)
+    code = polar.PolarCode(fr, 32, I.CRC32_POLY, 1)
+    side = torch.cuda.Stream()
+    llr = torch.from_numpy(f.llr_f32).cuda()
+    torch.cuda.synchronize()
+    bits = torch.empty((512, 104), dtype=torch.uint8, device="cuda")
+    pm = torch.empty(512, dtype=torch.float32, device="cuda")
+    ok = torch.empty(512, dtype=torch.uint8, device="cuda")
+    slot = torch.empty(512, dtype=torch.int32, device="cuda")
+    code.decode_into(llr, bits, pm, ok, slot, stream=side)
+    polar.sync(side)
+    g = tuple(t.cpu().numpy() for t in (bits, pm, ok, slot))
+    _check(g, o, "f32", "after polar_sync")
+    polar.sync()                                        # the current stream: nothing pending
+    code.close()
