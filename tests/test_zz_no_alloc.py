@@ -77,3 +77,29 @@ def test_noalloc_small_code_without_scratch(env):
         for a, b in zip(got, ref):
             assert torch.equal(a, b)
     code.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_noalloc_l1_code(env, dtype):
+    """An L = 1 code runs its own kernel, which needs no scratch, through the
+    allocation-free entry point too; with a list-kernel shape fixed it goes
+    through the fixed array like any list code. All four agree."""
+    torch, polar = env
+    lib = polar.load_library()
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 2000, seed=41)
+    x = f.llr_i8 if dtype == "i8" else f.llr_f32
+    dt = polar.LLR_I8 if dtype == "i8" else polar.LLR_F32
+    llr = torch.from_numpy(x).cuda()
+    code = polar.PolarCode(fr, 32, I.CRC32_POLY, 1)
+    ref = _call(torch, polar, lib.polar_list_decode, code, llr, dt)
+    got = _call(torch, polar, lib.polar_list_decode_noalloc, code, llr, dt)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    code.set_launch(dt, 1, 2000, 512)                      # small enough to spill for both dtypes
+    assert code.info()["scratch_per_frame"][dt] > 0
+    for fn in (lib.polar_list_decode, lib.polar_list_decode_noalloc):
+        got = _call(torch, polar, fn, code, llr, dt)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b)
+    code.close()
