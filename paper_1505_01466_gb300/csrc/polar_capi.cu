@@ -89,6 +89,40 @@ void scratch_poison(void *p, size_t bytes, int dtype, cudaStream_t st) {
     if (p && bytes && g_poison.load()) cudaMemsetAsync(p, dtype == POLAR_LLR_F32 ? 0xFF : 0x80, bytes, st);
 }
 
+// ---- launches from several host threads ------------------------------------
+// The kernels' launch helpers raise the function's dynamic shared-memory limit
+// to what the launch needs just before launching it (and the occupancy queries
+// do the same). The limit belongs to the function, not to the call, so two
+// threads launching the same kernel with different sizes could lower it in
+// between; these wrappers make each set-and-launch (or set-and-query) atomic.
+std::mutex g_launch_mu;
+
+int occupancy_locked(int dtype, const LaunchShape &sh) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return occupancy(dtype, sh);
+}
+cudaError_t launch_decode_locked(int dtype, const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return launch_decode(dtype, sh, p, grid, st);
+}
+int occupancy_batch_locked(int dtype, int warps, uint32_t smem, int threads) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return occupancy_batch(dtype, warps, smem, threads);
+}
+cudaError_t launch_batch_locked(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
+                                cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return launch_batch(dtype, warps, b, grid, smem, threads, st);
+}
+int occupancy_sc1_locked(int dtype, int n, bool root_leaf, int warps) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return occupancy_sc1(dtype, n, root_leaf, warps);
+}
+cudaError_t launch_sc1_locked(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return launch_sc1(dtype, p, grid, warps, st);
+}
+
 // NVTX range for the duration of a host call (visible in Nsight timelines).
 struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
@@ -421,7 +455,7 @@ CodeView make_view(const polar_code *code, const LaunchShape &sh) {
 int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const void *llr, uint32_t n_frames,
                  uint8_t *bits, float *pm, uint8_t *ok, int32_t *slot, cudaStream_t st,
                  const uint32_t *frame_idx = nullptr, const uint32_t *frame_cnt = nullptr) {
-    int occ = occupancy(dtype, sh);
+    int occ = occupancy_locked(dtype, sh);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
     const uint64_t need_ctas = ((uint64_t)n_frames + sh.groups_per_cta - 1) / sh.groups_per_cta;
@@ -445,7 +479,7 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
         scratch_poison(scratch, bytes, dtype, st);
         p.scratch = (uint8_t *)scratch;
     }
-    cudaError_t e = launch_decode(dtype, sh, p, (int)grid, st);
+    cudaError_t e = launch_decode_locked(dtype, sh, p, (int)grid, st);
     if (scratch) cudaFreeAsync(scratch, st);
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
@@ -534,12 +568,12 @@ int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
     p.frame_idx = frame_idx;
     p.frame_cnt = frame_cnt;
     const int warps = std::min<int>(kSc1Threads / 32, (int)(kMaxSmemPerCta / (uint32_t)p.warp_bytes));
-    const int occ = occupancy_sc1(dtype, (int)code->n, p.root_leaf != 0, warps);
+    const int occ = occupancy_sc1_locked(dtype, (int)code->n, p.root_leaf != 0, warps);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
     const uint64_t need = ((uint64_t)n_frames + warps - 1) / warps;
     if (grid > need) grid = need;
-    return launch_sc1(dtype, p, (int)grid, warps, st) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+    return launch_sc1_locked(dtype, p, (int)grid, warps, st) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 // The installed shape of the narrow kernels, the L = 1 kernel or the wide kernel.
@@ -935,7 +969,7 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
         return decode_sc1(code, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev,
                           winner_slot_dev, reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr);
     const LaunchShape &sh = code->shape[llr_dtype];
-    const int occ = occupancy(llr_dtype, sh);
+    const int occ = occupancy_locked(llr_dtype, sh);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
     const uint64_t need_ctas = ((uint64_t)n_frames + sh.groups_per_cta - 1) / sh.groups_per_cta;
@@ -963,7 +997,7 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
     p.n_frames = n_frames;
     p.groups_per_cta = sh.groups_per_cta;
     p.scratch = scratch;
-    const cudaError_t e = launch_decode(llr_dtype, sh, p, (int)grid, reinterpret_cast<cudaStream_t>(stream));
+    const cudaError_t e = launch_decode_locked(llr_dtype, sh, p, (int)grid, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
@@ -1050,7 +1084,7 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget, uint32_t cta_threads
     const uint32_t group_bytes = view_bytes + gb;
     const uint32_t cta_smem = group_bytes * (uint32_t)gpc;
     if (cta_smem > kMaxSmemPerCta) return POLAR_EINVAL;
-    const int occ = occupancy_batch(b->dtype, warps, cta_smem, (int)cta_threads);
+    const int occ = occupancy_batch_locked(b->dtype, warps, cta_smem, (int)cta_threads);
     if (occ <= 0) return POLAR_ECUDA;
     batch_free_shape(b);
     for (size_t c = 0; c < b->codes.size(); ++c) {
@@ -1100,8 +1134,8 @@ int batch_launch(polar_batch *b, const void *llr, uint8_t *bits, float *pm, uint
     p.group_bytes = b->group_bytes;
     p.view_bytes = b->view_bytes;
     p.groups_per_cta = b->groups_per_cta;
-    return launch_batch(b->dtype, b->warps, p, b->grid, b->cta_smem, b->threads, st) == cudaSuccess ? POLAR_OK
-                                                                                                 : POLAR_ECUDA;
+    const cudaError_t e = launch_batch_locked(b->dtype, b->warps, p, b->grid, b->cta_smem, b->threads, st);
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 }  // namespace
@@ -1592,7 +1626,7 @@ int srv_launch(polar_server *s, int i) {
     uint32_t group_bytes, cta_smem;
     int gpc;
     srv_shape(s, d, group_bytes, cta_smem, gpc);
-    const int occ = occupancy_batch(d, s->warps, cta_smem, kSrvCtaThreads);
+    const int occ = occupancy_batch_locked(d, s->warps, cta_smem, kSrvCtaThreads);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * s->sm_count;
     const uint64_t need = (n_items + gpc - 1) / gpc;
@@ -1621,7 +1655,7 @@ int srv_launch(polar_server *s, int i) {
     p.group_bytes = group_bytes;
     p.view_bytes = srv_view_bytes();
     p.groups_per_cta = gpc;
-    okc &= launch_batch(d, s->warps, p, (int)grid, cta_smem, kSrvCtaThreads, st) == cudaSuccess;
+    okc &= launch_batch_locked(d, s->warps, p, (int)grid, cta_smem, kSrvCtaThreads, st) == cudaSuccess;
     for (SrvReq *r : take) {
         const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
         okc &= cudaMemcpyAsync(s->h_arena + bits_base, s->d_arena + bits_base, r->bits_sz, cudaMemcpyDeviceToHost,
