@@ -22,6 +22,7 @@ import numpy as np
 
 SPC4, SPC_ANY, BITWISE = 0, 1, 2
 SYSTEMATIC = 0x100   # or-ed into a mode: payload and CRC read from x, not u = x G_N
+SPC_ALL_CANDIDATES = 0x200   # tests only: all eight SPC candidates even at L = 2
 F32, I8 = 0, 1
 OP_F, OP_G, OP_COMBINE = 0, 1, 2
 LEAF_RATE0, LEAF_RATE1, LEAF_REP, LEAF_SPC = 11, 12, 13, 14

@@ -22,6 +22,8 @@
  * Any mode may be or-ed with OR_SYSTEMATIC: the code is systematic (the
  * encoder cited in Sec. I puts payload and CRC in the codeword x itself), so
  * the final pick reads the information bits from x instead of u = x G_N.
+ * OR_SPC_ALL_CANDIDATES (tests only) generates all eight SPC candidates even
+ * at L = 2; the tests use it to pin the two-candidate rule of R6.
  *
  * Inner nodes apply F (Eq. (1), min-sum), G (Eq. (2)) and Combine (Eq. (3))
  * to every path independently (Sec. III). Leaves generate candidates from
@@ -51,7 +53,9 @@
  *      the sum of |a| over the positions where the candidate differs from
  *      HD. (The expanded metrics printed in Sec. III-D agree for even parity
  *      and give odd-weight words for odd parity.) With L = 2 only the first
- *      two candidates are generated (Sec. III-D).
+ *      two candidates are generated (Sec. III-D). They are each source's two
+ *      best under the key of R4, so the L = 2 survivors equal those of all
+ *      eight (pinned against OR_SPC_ALL_CANDIDATES).
  *  R7  Repetition: the ML candidate (listed first) is all-zero when
  *      P0 <= P1, else all-one (Eq. (5) with the tie to 0).
  *  R8  Float sums: a penalty increment made of least-reliable-bit terms is
@@ -95,6 +99,7 @@
 #define OR_SPC_ANY 1
 #define OR_BITWISE 2
 #define OR_SYSTEMATIC 0x100
+#define OR_SPC_ALL_CANDIDATES 0x200   /* test only: all eight SPC candidates even at L = 2 */
 
 #define NODE_INNER 0
 #define NODE_RATE0 1
@@ -103,7 +108,7 @@
 #define NODE_SPC 4
 
 typedef struct {
-    int N, n, K, L, dtype, crc_len, mode, systematic, bad_flags;
+    int N, n, K, L, dtype, crc_len, mode, systematic, spc_all, bad_flags;
     uint64_t crc_poly;
     const uint8_t *frozen; /* N bytes, 1 = frozen */
 } ocode_t;
@@ -263,7 +268,7 @@ static int gen_candidates(const ocode_t *c, int type, const float *a, int nv, in
         int parity = 0;
         for (int i = 0; i < nv; ++i) parity ^= h_of(a[i]);
         int q = parity == 0;                      /* q = 1 when the parity check holds */
-        int ncand = c->L == 2 ? 2 : 8;
+        int ncand = (c->L == 2 && !c->spc_all) ? 2 : 8;
         for (int t = 0; t < ncand; ++t) {
             /* positions differing from HD: T, symmetric-difference {rank 1} when q = 0 */
             int diff[4];
@@ -488,7 +493,8 @@ static void fill_code(ocode_t *c, int N, int K, const uint8_t *frozen, int L, in
     c->crc_poly = crc_poly;
     c->mode = mode & 0xFF;
     c->systematic = (mode & OR_SYSTEMATIC) ? 1 : 0;
-    c->bad_flags = (mode & ~(0xFF | OR_SYSTEMATIC)) != 0;
+    c->spc_all = (mode & OR_SPC_ALL_CANDIDATES) ? 1 : 0;
+    c->bad_flags = (mode & ~(0xFF | OR_SYSTEMATIC | OR_SPC_ALL_CANDIDATES)) != 0;
 }
 
 /* ---------------- exported entry points ---------------- */

@@ -375,3 +375,33 @@ def test_long_spc_nodes_equal_chase2(oracle_mod, N):
         assert set(got) == set(want)                       # the same eight words
         for w in want:                                     # with the same metrics (float32 vs float64 sums)
             assert got[w] == pytest.approx(want[w], rel=1e-6, abs=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_l2_spc_two_candidates_equal_all_eight(oracle_mod, dtype):
+    """Sec. III-D: at L = 2 an SPC node needs only its first two candidates.
+    Under the key (penalty, source, candidate) they are each source's two best
+    (the others add least-reliable-bit terms at least as large), so the two
+    survivors of all eight candidates are the same paths in the same slots."""
+    rng = np.random.default_rng(212)
+    with_spc = 0
+    for mode in (oracle_mod.SPC4, oracle_mod.SPC_ANY):
+        for N in (16, 32, 64, 128, 256):
+            for _ in range(3):
+                K = int(rng.integers(N // 4, N - 2))
+                crc = 8 if K > 12 else 0
+                fr = I.ga_frozen_mask(N, K, float(rng.uniform(0, 3)), max(K - crc, 1) / N)
+                f = I.make_frames(fr, crc, I.CRC8_POLY, float(rng.uniform(-1, 2.5)), 60,
+                                  seed=int(rng.integers(1 << 30)))
+                llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+                if dtype == "i8":
+                    llr[:10] = rng.integers(-3, 4, (10, N))          # many ties
+                two = oracle_mod.decode(fr, 2, llr, crc, I.CRC8_POLY, mode)
+                eight = oracle_mod.decode(fr, 2, llr, crc, I.CRC8_POLY, mode | oracle_mod.SPC_ALL_CANDIDATES)
+                for a, b in zip(two, eight):
+                    assert np.array_equal(a, b), (mode, N, K)
+                with_spc += any(op[0] == oracle_mod.LEAF_SPC for op in oracle_mod.schedule(fr, mode))
+    assert with_spc >= 15
+    # an unknown flag bit is still refused
+    with pytest.raises(Exception):
+        oracle_mod.decode(I.ga_frozen_mask(16, 8, 2.0), 2, np.zeros((1, 16), np.float32), 0, 0, 0x400)
