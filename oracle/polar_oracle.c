@@ -79,7 +79,11 @@
  *
  * Pins: every mode is checked by the tests against brute-force ML, noiseless
  * frames, a textbook SC decoder, the Fig. 1 / Listing 2 example and FER
- * agreement between modes. SPC nodes longer than four bits (mode OR_SPC_ANY)
+ * agreement between modes. The final pick (R11) is recomputed outside this
+ * file from the final list on frames where a lower-penalty path fails the
+ * CRC; int8 saturation (R9) against a hand-worked (4,2) example; pruned
+ * selection (R4) against an independent bit-by-bit SC-list written in
+ * Python. SPC nodes longer than four bits (mode OR_SPC_ANY)
  * are not exhaustive, so brute-force ML does not fix them; their candidate
  * lists are pinned instead against an independent Chase-II enumeration (all
  * flips of the four least reliable bits, even weight).

@@ -14,6 +14,12 @@ The oracle is checked against things that do not come from it:
   fast decoder and bit-by-bit SC-list take identical decisions at any L;
 * the fast decoder's frame-error rate matches SC-list (Sec. VI) within
   Monte-Carlo confidence;
+* the final pick (Sec. II-B) recomputed outside the oracle from its final
+  list: u = x G_N, the CRC from ``inputs``, the least (penalty, slot) among
+  the passing paths, on frames where a lower-penalty path fails the CRC;
+* int8 G saturation at +-127 on a (4,2) example worked by hand;
+* pruned selection (2 <= L < 2^K) against an independently written
+  bit-by-bit SC-list that recomputes every LLR from the channel;
 * plausible single mistakes planted in a copy of the oracle source fail at
   least one of these checks.
 """
@@ -229,6 +235,197 @@ def test_fast_fer_matches_scl(oracle_mod, dtype):
 
 
 # ---------------------------------------------------------------------------
+# Final pick (Sec. II-B): the output is the best path that passes the CRC.
+# ---------------------------------------------------------------------------
+def _crc_first_pick(frozen, crc_len, poly, words, pens):
+    """Winner of a final list, recomputed outside the oracle: u = x G_N, the
+    information bits in ascending index, the payload/CRC split and the CRC
+    from ``inputs``; the least (penalty, slot) among the passing paths, else
+    among all paths. Returns (slot, crc_ok, payload bits)."""
+    info = I.info_positions(frozen)
+    k = info.size - crc_len
+    u = I.polar_transform(np.asarray(words, np.uint8))[:, info]
+    ok = (I.crc_bits(u[:, :k], crc_len, poly) == u[:, k:]).all(axis=1)
+    order = np.lexsort((np.arange(len(pens)), np.asarray(pens)))   # by (penalty, slot)
+    passing = [s for s in order if ok[s]]
+    s = int(passing[0] if passing else order[0])
+    return s, int(ok[s]), u[s, :k]
+
+
+def _crc_first_frames(mod, N, K, L, ebn0, n, seed, dtype="f32", mode=None):
+    """Noisy frames whose least-penalty final path fails the CRC while
+    another path passes it: (frozen, llr [F, N], expected picks)."""
+    mode = mod.SPC4 if mode is None else mode
+    fr = I.ga_frozen_mask(N, K, 2.0, (K - 8) / N)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, ebn0, n, seed=seed)
+    llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+    rows, want = [], []
+    for i in range(n):
+        words, pens = mod.decode_list(fr, L, llr[i], mode)
+        s, ok, payload = _crc_first_pick(fr, 8, I.CRC8_POLY, words, pens)
+        least = int(np.lexsort((np.arange(len(pens)), pens))[0])
+        if ok and s != least:
+            rows.append(i)
+            want.append((s, float(pens[s]), payload))
+    return fr, llr[rows], want
+
+
+@pytest.mark.parametrize("N,K,L,ebn0,dtype", [(64, 40, 8, 1.0, "f32"), (64, 40, 4, 1.0, "i8"),
+                                              (256, 128, 8, 1.0, "f32"), (256, 128, 4, 1.0, "i8")])
+def test_final_pick_prefers_crc_passing_path(oracle_mod, N, K, L, ebn0, dtype):
+    fr, llr, want = _crc_first_frames(oracle_mod, N, K, L, ebn0, 300, seed=77 + N + L, dtype=dtype)
+    assert len(want) >= 20, len(want)       # frames where the rule decides the output
+    bits, pm, ok, slot = oracle_mod.decode(fr, L, llr, 8, I.CRC8_POLY, oracle_mod.SPC4)
+    for i, (s, pen, payload) in enumerate(want):
+        assert slot[i] == s and ok[i] == 1 and pm[i] == pen
+        assert np.array_equal(I.unpack_bits_lsb(bits[i], K - 8), payload)
+
+
+def test_final_pick_falls_back_to_least_penalty(oracle_mod):
+    # a CRC that no path passes: every word's CRC bits are forced wrong by
+    # decoding against a different polynomial than the frames were built with
+    fr = I.ga_frozen_mask(64, 40, 2.0, 32 / 64)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 1.0, 40, seed=5)
+    bits, pm, ok, slot = oracle_mod.decode(fr, 4, f.llr_f32, 8, 0x9B, oracle_mod.SPC4)
+    for i in range(40):
+        words, pens = oracle_mod.decode_list(fr, 4, f.llr_f32[i], oracle_mod.SPC4)
+        s, okk, payload = _crc_first_pick(fr, 8, 0x9B, words, pens)
+        assert slot[i] == s and ok[i] == okk and pm[i] == pens[s]
+        assert np.array_equal(I.unpack_bits_lsb(bits[i], 32), payload)
+
+
+# ---------------------------------------------------------------------------
+# int8 G saturates at +-127 (the int8 convention; the paper is float-only).
+# ---------------------------------------------------------------------------
+# A (4,2) code with u0 and u2 frozen, decoded bit by bit with L = 4 so every
+# codeword stays on the list. Worked by hand from Eqs. (1)-(3) and Eq. (6):
+#
+#   y = (100, 100, 100, 100):
+#     F at the root: (f(100,100), f(100,100)) = (100, 100); u0: f(100,100)
+#     = 100, frozen, h = 0, no penalty. u1: G = 100 + 100 = 200 -> 127 in int8.
+#     Slots (s, c) order: A = (u1 = 0, P = 0), B = (u1 = 1, P = 127 | 200).
+#     G at the root with beta_left = (u0^u1, u1): A gets (200, 200) -> (127,
+#     127); B gets (0, 0). u2 frozen: A f(127,127) = 127, B f(0,0) = 0: no
+#     penalty. u3: A lambda = 127 + 127 -> 127 (f32: 400), B lambda = 0.
+#     Final slots (A,0) (A,1) (B,0) (B,1), words x = uG:
+#       0000 P 0; 1111 P 127 | 400; 1100 P 127 | 200; 0011 P 127 | 200.
+#   y = (100, -100, 100, -100):
+#     the same up to the root's G, which gives A (200, -200) -> (127, -127)
+#     and B (0, 0). u2 frozen: A f(127, -127) = -127, h = 1, P += 127 | 200;
+#     B: 0. u3: A lambda = -127 + 127 = 0 (f32: -200 + 200 = 0), B lambda = 0.
+#     Final: every slot P = 127 (int8) | 200 (f32), the same four words.
+# The f32 penalties equal each word's correlation discrepancy (100 x the
+# positions where x differs from h(y)); int8 caps every G at 127.
+SAT_CASES = [
+    ((100, 100, 100, 100), [0, 127, 127, 127], [0, 400, 200, 200]),
+    ((100, -100, 100, -100), [127, 127, 127, 127], [200, 200, 200, 200]),
+]
+SAT_WORDS = [(0, 0, 0, 0), (1, 1, 1, 1), (1, 1, 0, 0), (0, 0, 1, 1)]
+
+
+def _saturation_pins(mod):
+    fr = np.array([1, 0, 1, 0], np.uint8)
+    for y, pen_i8, pen_f32 in SAT_CASES:
+        for arr, want in ((np.array(y, np.int8), pen_i8), (np.array(y, np.float32), pen_f32)):
+            words, pens = mod.decode_list(fr, 4, arr, mod.BITWISE)
+            if [tuple(int(v) for v in w) for w in words] != SAT_WORDS:
+                return False
+            if [float(p) for p in pens] != [float(v) for v in want]:
+                return False
+    return True
+
+
+def test_int8_g_saturates_hand_worked(oracle_mod):
+    assert _saturation_pins(oracle_mod)
+
+
+def test_int8_fast_nodes_see_saturated_llrs(oracle_mod):
+    # The same frames through the fast node rules: the root of the (4,2) code
+    # splits into two repetition nodes of length 2; the right one sees the
+    # saturated G outputs, so its repetition penalties are sums of +-127.
+    fr = np.array([1, 0, 1, 0], np.uint8)
+    words, pens = oracle_mod.decode_list(fr, 4, np.array((100, 100, 100, 100), np.int8), oracle_mod.SPC4)
+    got = sorted((float(p), tuple(int(v) for v in w)) for w, p in zip(words, pens))
+    # left rep node: alpha = (100, 100): P0 = 0, P1 = 200 (sums of the inputs
+    # themselves, no G). Right node: path u1 = 0 sees (127, 127) -> P0 = 0,
+    # P1 = 254; path u1 = 1 sees (0, 0) -> 0 and 0.
+    assert got == sorted([(0.0, (0, 0, 0, 0)), (254.0, (1, 1, 1, 1)),
+                          (200.0, (1, 1, 0, 0)), (200.0, (0, 0, 1, 1))])
+
+
+# ---------------------------------------------------------------------------
+# Pruned selection (Algorithm 1 with 2 <= L < 2^K): an independent SC-list.
+# ---------------------------------------------------------------------------
+def _py_scl(frozen, y, L, sat):
+    """Bit-by-bit LLR SC-list, written independently of the oracle: the LLR
+    of bit i is recomputed from the channel for every path by the recursion
+    on the halves of the code (left half: F of the two halves; right half:
+    G with the re-encoded left half), the metric follows Eq. (6), and the L
+    best of (penalty, source, candidate) survive in (source, candidate)
+    order. Integer-valued inputs, so every sum is exact."""
+    def clamp(v):
+        return max(-127, min(127, v)) if sat else v
+
+    def lam(a, u, i):
+        if len(a) == 1:
+            return a[0]
+        h = len(a) // 2
+        if i < h:
+            fa = [(1 if (a[t] < 0) == (a[t + h] < 0) else -1) * min(abs(a[t]), abs(a[t + h]))
+                  for t in range(h)]
+            return lam(fa, u, i)
+        bl = I.polar_transform(np.array(u[:h], np.uint8))
+        ga = [clamp(a[t + h] + (1 - 2 * int(bl[t])) * a[t]) for t in range(h)]
+        return lam(ga, u[h:], i - h)
+
+    y = [max(-127, int(v)) if sat else int(v) for v in y]
+    paths = [(0, [])]
+    for i in range(len(y)):
+        if frozen[i]:
+            new = []
+            for pen, u in paths:
+                v = lam(y, u, i)
+                new.append((pen + (abs(v) if v < 0 else 0), u + [0]))
+            paths = new
+            continue
+        cands = []
+        for s, (pen, u) in enumerate(paths):
+            v = lam(y, u, i)
+            hd = 1 if v < 0 else 0
+            cands.append((pen, s, 0, u + [hd]))
+            cands.append((pen + abs(v), s, 1, u + [1 - hd]))
+        keep = sorted(cands, key=lambda c: (c[0], c[1], c[2]))[:L]
+        keep.sort(key=lambda c: (c[1], c[2]))
+        paths = [(c[0], c[3]) for c in keep]
+    return [(float(p), tuple(int(b) for b in I.polar_transform(np.array(u, np.uint8)))) for p, u in paths]
+
+
+def _pruned_selection_pins(mod, trials, seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(trials):
+        N = int(rng.choice([8, 16, 32]))
+        K = int(rng.integers(3, min(N, 10) + 1))
+        fr = _random_code(rng, N, K)
+        for L in (2, 4):
+            if L >= (1 << K):
+                continue
+            sat = bool(rng.integers(0, 2))
+            if sat:
+                y = rng.integers(-127, 128, N).astype(np.int8)
+            else:
+                y = rng.integers(-8, 9, N).astype(np.float32)
+            words, pens = mod.decode_list(fr, L, y, mod.BITWISE)
+            got = [(float(p), tuple(int(v) for v in w)) for w, p in zip(words, pens)]
+            if got != _py_scl(fr, y, L, sat):
+                return False
+    return True
+
+
+def test_pruned_selection_equals_independent_scl(oracle_mod):
+    assert _pruned_selection_pins(oracle_mod, 60, 31)
+
+
+# ---------------------------------------------------------------------------
 # Planted mistakes: each textual mutation of the oracle must fail a pin.
 # ---------------------------------------------------------------------------
 MUTATIONS = [
@@ -247,6 +444,13 @@ MUTATIONS = [
     ("selection keeps worst", "if (x->pen < y->pen) return -1;", "if (x->pen < y->pen) return 1;"),
     ("h of zero", "static int h_of(float a) { return a < 0.0f ? 1 : 0; }",
      "static int h_of(float a) { return a <= 0.0f ? 1 : 0; }"),
+    ("final pick ignores CRC", "else if (ok != best.ok) better = ok > best.ok;",
+     "else if (0) better = ok > best.ok;"),
+    ("G unsaturated", "    if (sat) {\n        if (r > 127.0f)", "    if (0) {\n        if (r > 127.0f)"),
+    ("G saturates one side", "if (r < -127.0f) r = -127.0f;", "if (r < -128.0f) r = -128.0f;"),
+    ("survivors in key order", "    int slot = 0;\n    for (int i = 0; i < nc; ++i) {",
+     "    memcpy(cand, sorted, sizeof(ocand_t) * (size_t)nc);\n    memset(survive, 0, (size_t)nc);\n"
+     "    memset(survive, 1, (size_t)keep);\n    int slot = 0;\n    for (int i = 0; i < nc; ++i) {"),
 ]
 
 
@@ -274,7 +478,18 @@ def _pins_pass(mod):
         bits, pm, ok, _ = mod.decode(fr, 4, f.llr_f32, 8, I.CRC8_POLY, mode)
         if not np.array_equal(I.unpack_bits_lsb(bits, 32), f.payload) or pm.any():
             return False
-    return True
+    # the CRC decides the final pick over a lower penalty (Sec. II-B)
+    fr, llr, want = _crc_first_frames(mod, 64, 40, 8, 1.0, 120, seed=149)
+    if len(want) < 5:
+        return False
+    bits, pm, ok, slot = mod.decode(fr, 8, llr, 8, I.CRC8_POLY, mod.SPC4)
+    for i, (s, pen, payload) in enumerate(want):
+        if slot[i] != s or ok[i] != 1 or pm[i] != pen:
+            return False
+        if not np.array_equal(I.unpack_bits_lsb(bits[i], 32), payload):
+            return False
+    # int8 G saturation, worked by hand; pruned selection against an independent SC-list
+    return _saturation_pins(mod) and _pruned_selection_pins(mod, 12, 5)
 
 
 def test_pins_pass_on_the_oracle(oracle_mod):
