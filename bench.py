@@ -38,7 +38,7 @@ UNIQUE = 1 << 16
 METRIC = "info Gbps at (2048,1723) L=32 on 1 GB300, batched vs plain; FER match; p99 lat"
 # DRAM bytes per frame of decode_kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
 # ncu capture over 32768 frames of this workload, 1 warp per frame, 7000-byte budget, 512-thread CTAs; the
-# capture is summarised in profiles/decode_kernel_2048_1723_L32.md). Valid only for the
+# capture is in the profile summary of decode_kernel). Valid only for the
 # kernel source with this sha1; any other source reports traffic null.
 NCU_TRAFFIC = {"kernel_sha1": "8b2b0ddec2bcbb523a4df029d26c07895c34dda0", "f32": 1682900, "i8": 203600}
 UNIT = "Gbps"
@@ -71,8 +71,11 @@ def parse():
     ap.add_argument("--skip-rates", action="store_true")
     ap.add_argument("--wide-frames", type=int, default=1 << 14)
     ap.add_argument("--ablation-frames", type=int, default=1 << 17)
-    ap.add_argument("--fer-frames", type=int, default=1 << 17, help="frames per Eb/N0 point of the FER sweep")
-    ap.add_argument("--fer-points", default="3.5,4.0,4.5", help="Eb/N0 points (dB) of the FER sweep")
+    ap.add_argument("--fer-frames", type=int, default=0,
+                    help="frames per Eb/N0 point of the FER sweep (0: 10^6 for (1024,860), 2^20 for (2048,1723))")
+    ap.add_argument("--fer-points", default="3.5,3.75,4.0,4.25,4.5", help="Eb/N0 points (dB) of the FER sweep")
+    ap.add_argument("--fer-codes", default="c2,c3", help="FER sweep codes: c2 = (1024,860), c3 = (2048,1723)")
+    ap.add_argument("--details", default="", help="also write every measured block in full to this JSON file")
     return ap.parse_args()
 
 
@@ -263,21 +266,27 @@ def adaptive_throughput(k: float, fer_f: float, lat_f: float, lat_l: float, pays
     return k / cost
 
 
+FER_CODES = {
+    # (N, K incl. CRC-32, list sizes, frames per point): the (1024,860) and the
+    # (2048,1723) configurations, GA design at 4 dB
+    "c2": (1024, 860, (2, 4, 8, 32), 1000000),
+    "c3": (2048, 1723, (8, 32), 1 << 20),
+}
+
+
 def measure_fer(args, torch, dev, stream):
-    """FER of the fast decoder (Dec-SPC-4) against plain SC-list decoding
-    (length-one leaves, the same list size) on the same frames, and the
-    adaptive decoder (Fast-SSC, then the list decoder on CRC failures) with
-    its throughput, at each Eb/N0 point; float32 and int8 LLRs."""
+    """Frame-error rate of the fast decoder (Dec-SPC-4) against plain SC-list
+    decoding (length-one leaves, bit-exact with the oracle's SC-list) at the
+    same list size on the same frames, per Eb/N0 point, list size and LLR
+    type; and at (2048,1723) the adaptive decoder (Fast-SSC, then L = 8 or 32
+    on the CRC failures) with its throughput. Frames are generated on the
+    device (inputs.make_frames_torch), so every point has its full frame
+    count."""
     import numpy as np
     from paper_1505_01466_gb300 import inputs as I
     from paper_1505_01466_gb300.polar import PolarCode, adaptive_decode
-    frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
-    k = K - CRC_LEN
-    fast = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L, mode=0)
-    scl = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, L, mode=2)
-    sc1 = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 1, mode=0)
-    fast8 = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 8, mode=0)
-    tuned = set()
+    points = [float(x) for x in args.fer_points.split(",") if x]
+    sets = [c for c in args.fer_codes.split(",") if c]
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -288,53 +297,96 @@ def measure_fer(args, torch, dev, stream):
         torch.cuda.synchronize()
         return out, a.elapsed_time(b)
 
-    points = []
-    for ebn0 in [float(x) for x in args.fer_points.split(",") if x]:
-        fr = I.make_frames_chunked(frozen, CRC_LEN, I.CRC32_POLY, ebn0, args.fer_frames, seed=int(ebn0 * 1000))
-        for dt in ("f32", "i8"):
-            llr = torch.from_numpy(fr.llr_i8 if dt == "i8" else fr.llr_f32).to(dev)
-            if dt not in tuned:
-                for c in (fast, scl, sc1, fast8):
-                    c.autotune(llr[:16384], stream=stream)
-                tuned.add(dt)
-            errs, ms = {}, {}
-            for name, fn in (("fast", lambda: fast.decode(llr, stream=stream)),
-                             ("scl", lambda: scl.decode(llr, stream=stream)),
-                             ("sc1", lambda: sc1.decode(llr, stream=stream)),
-                             ("adaptive", lambda: adaptive_decode(sc1, fast, llr, stream=stream)),
-                             ("adaptive8", lambda: adaptive_decode(sc1, fast8, llr, stream=stream))):
-                fn()                                     # warm-up
-                out, ms[name] = timed(fn)
-                got = I.unpack_bits_lsb(out[0].cpu().numpy(), k)
-                errs[name] = (got != fr.payload).any(axis=1)
-                if name.startswith("adaptive"):
-                    relisted = int(out[4].item())
-            t = paired_fer_test(errs["fast"], errs["scl"])
-            points.append({
-                "ebn0_db": ebn0, "dtype": dt, "frames": args.fer_frames,
-                "fer_fast": t["fer"][0], "ci99_fast": t["ci"][0], "fer_scl": t["fer"][1], "ci99_scl": t["ci"][1],
-                "errors_fast": t["errors"][0], "errors_scl": t["errors"][1],
-                "only_fast_failed": t["only_first_failed"], "only_scl_failed": t["only_second_failed"],
-                "mcnemar_p": t["mcnemar_p"], "fer_match": t["match"], "underpowered": t["underpowered"],
-                "fer_adaptive": float(errs["adaptive"].mean()),
-                "adaptive_relisted_frac": relisted / args.fer_frames,
-                "gbps_fast": k * args.fer_frames / ms["fast"] / 1e6,
-                "gbps_scl": k * args.fer_frames / ms["scl"] / 1e6,
-                "gbps_adaptive": k * args.fer_frames / ms["adaptive"] / 1e6,
-                "gbps_adaptive_model": adaptive_throughput(k * args.fer_frames, relisted / args.fer_frames,
-                                                           ms["sc1"], ms["fast"]) / 1e6,
-                "gbps_adaptive_eq_tp": adaptive_throughput(k * args.fer_frames, relisted / args.fer_frames,
-                                                           ms["sc1"], ms["fast"], pays_both=False) / 1e6,
-                "fer_adaptive_L8": float(errs["adaptive8"].mean()),
-                "gbps_adaptive_L8": k * args.fer_frames / ms["adaptive8"] / 1e6,
-            })
-            del llr
-    for c in (fast, scl, sc1, fast8):
-        c.close()
-    return {"code": f"({N},{K}) CRC-32 L={L}, GA {DESIGN_DB} dB", "fast": "Dec-SPC-4",
-            "plain": "SC-list with length-one leaves (bit-exact with the oracle's SC-list)",
-            "adaptive": f"Fast-SSC (L=1) then L={L} on CRC failures", "test": "exact McNemar + Clopper-Pearson 99%",
-            "points": points}
+    rows, adaptive = [], []
+    for cs in sets:
+        Nc, Kc, Ls, frames = FER_CODES[cs]
+        if args.fer_frames:
+            frames = args.fer_frames
+        kc = Kc - CRC_LEN
+        frozen = I.ga_frozen_mask(Nc, Kc, DESIGN_DB, kc / Nc)
+        codes = {}
+        for Lc in Ls:
+            codes[Lc] = (PolarCode(frozen, CRC_LEN, I.CRC32_POLY, Lc, mode=0),
+                         PolarCode(frozen, CRC_LEN, I.CRC32_POLY, Lc, mode=2))
+        sc1 = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 1, mode=0) if Nc == N else None
+        tuned = set()
+        for ebn0 in points:
+            payload, f32, i8 = I.make_frames_torch(frozen, CRC_LEN, I.CRC32_POLY, ebn0, frames,
+                                                   seed=int(ebn0 * 1000) + Nc, device=dev)
+            pay_np = payload.cpu().numpy()
+            del payload
+            for dt, llr in (("f32", f32), ("i8", i8)):
+                if dt not in tuned:
+                    for Lc in Ls:
+                        for c in codes[Lc]:
+                            c.autotune(llr[:16384], stream=stream)
+                    if sc1 is not None:
+                        sc1.autotune(llr[:16384], stream=stream)
+                    tuned.add(dt)
+                for Lc in Ls:
+                    errs, ms = {}, {}
+                    for name, c in (("fast", codes[Lc][0]), ("scl", codes[Lc][1])):
+                        out, ms[name] = timed(lambda: c.decode(llr, stream=stream))
+                        errs[name] = (I.unpack_bits_lsb(out[0].cpu().numpy(), kc) != pay_np).any(axis=1)
+                        del out
+                    t = paired_fer_test(errs["fast"], errs["scl"])
+                    rows.append({"code": f"({Nc},{Kc})", "L": Lc, "dtype": dt, "ebn0_db": ebn0, "frames": frames,
+                                 "errors_fast": t["errors"][0], "errors_scl": t["errors"][1],
+                                 "ci99_fast": t["ci"][0], "ci99_scl": t["ci"][1],
+                                 "only_fast_failed": t["only_first_failed"],
+                                 "only_scl_failed": t["only_second_failed"], "mcnemar_p": t["mcnemar_p"],
+                                 "fer_match": t["match"], "underpowered": t["underpowered"],
+                                 "gbps_fast": kc * frames / ms["fast"] / 1e6,
+                                 "gbps_scl": kc * frames / ms["scl"] / 1e6})
+                    if sc1 is not None:
+                        _, ms1 = timed(lambda: sc1.decode(llr, stream=stream))
+                        adaptive_decode(sc1, codes[Lc][0], llr[:4096], stream=stream)     # warm-up
+                        out, msa = timed(lambda: adaptive_decode(sc1, codes[Lc][0], llr, stream=stream))
+                        relisted = int(out[4].item())
+                        erra = (I.unpack_bits_lsb(out[0].cpu().numpy(), kc) != pay_np).any(axis=1)
+                        del out
+                        adaptive.append({"L_max": Lc, "dtype": dt, "ebn0_db": ebn0, "frames": frames,
+                                         "gbps": kc * frames / msa / 1e6, "relisted_frac": relisted / frames,
+                                         "fer": float(erra.mean()), "fer_list": float(errs["fast"].mean()),
+                                         "gbps_model_both_passes": adaptive_throughput(
+                                             kc * frames, relisted / frames, ms1, ms["fast"]) / 1e6,
+                                         "gbps_model_eq_tp": adaptive_throughput(
+                                             kc * frames, relisted / frames, ms1, ms["fast"], pays_both=False) / 1e6})
+            del f32, i8
+        for pair in codes.values():
+            for c in pair:
+                c.close()
+        if sc1 is not None:
+            sc1.close()
+    return {"fast": "Dec-SPC-4", "plain": "SC-list with length-one leaves (bit-exact with the oracle's SC-list)",
+            "test": "paired frames: exact McNemar + Clopper-Pearson 99%; underpowered below 100 errors",
+            "rows": rows, "adaptive": adaptive}
+
+
+def compact_fer(fer):
+    """Per (code, L, dtype) one [errors fast, errors SC-list, McNemar p] per Eb/N0 point."""
+    if not fer or "rows" not in fer:
+        return fer
+    rows = fer["rows"]
+    out = {"cols": "[err_fast, err_scl, mcnemar_p] per EbN0", "ebn0_db": sorted({r["ebn0_db"] for r in rows}),
+           "frames": sorted({f"{r['code']} {r['frames']}" for r in rows}),
+           "all_match": all(r["fer_match"] for r in rows),
+           "underpowered": sum(1 for r in rows if r["underpowered"])}
+    for r in sorted(rows, key=lambda r: r["ebn0_db"]):
+        out.setdefault(f"{r['code']}L{r['L']}{r['dtype']}", []).append(
+            [r["errors_fast"], r["errors_scl"], round(r["mcnemar_p"], 2)])
+    return out
+
+
+def compact_adaptive(fer):
+    """Adaptive decoding (Table II shape): [Eb/N0, info Gbps, relisted fraction] per point."""
+    if not fer or not fer.get("adaptive"):
+        return None
+    out = {"cols": "[EbN0, gbps, relisted_frac]"}
+    for r in fer["adaptive"]:
+        out.setdefault(f"L{r['L_max']} {r['dtype']}", []).append(
+            [r["ebn0_db"], round(r["gbps"], 2), round(r["relisted_frac"], 4)])
+    return out
 
 
 def measure_ablation(args, torch, dev, stream):
@@ -548,7 +600,8 @@ def measure_batched(args, torch, dev, stream, barrier):
     }
 
 
-def measure_batched_headline(args, torch, dev, stream, barrier, llr, frozen, tuned, ops_frame, peak, ref_bits, ref_pm):
+def measure_batched_headline(args, torch, dev, stream, barrier, llr, frozen, tuned, ops_frame, peak, ref_bits, ref_pm,
+                             ref_ok, plain_ms):
     """The batched form on the plain form's own workload: (2048,1723) L = 32,
     every frame one class, the same frames in HBM, one graph-replayed
     persistent launch in the plain form's autotuned shape. For a single class
@@ -586,19 +639,44 @@ def measure_batched_headline(args, torch, dev, stream, barrier, llr, frozen, tun
         barrier()
         ms = reduce_max(torch, a.elapsed_time(b) / args.steps, dev)
         kb = (K - CRC_LEN + 7) // 8
-        same = bool(torch.equal(bits.view(F, kb), ref_bits) and torch.equal(pm, ref_pm))
+        same = bool(torch.equal(bits.view(F, kb), ref_bits) and torch.equal(pm, ref_pm) and torch.equal(ok, ref_ok))
         achieved = ops_frame * F / (ms * 1e-3) / 1e12
         info = plan.info()
+        # a batched run whose results differ from the plain form's reports no throughput
         return {"workload": f"({N},{K}) CRC-32 L={L}, one class, the plain form's {F} frames per GPU",
-                "value": job_gbps(K - CRC_LEN, F, world, ms), "unit": UNIT, "ms_per_step": ms,
+                "value": job_gbps(K - CRC_LEN, F, world, ms) if same else None, "unit": UNIT,
+                "ms_per_step": ms if same else None,
+                "plain_value": job_gbps(K - CRC_LEN, F, world, plain_ms), "plain_ms_per_step": plain_ms,
                 "graph_replay": True, "results_equal_plain": same, "shape": shape,
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                             "frac": achieved / peak},
+                             "frac": achieved / peak, "plain_frac": ops_frame * F / (plain_ms * 1e-3) / 1e12 / peak}
+                if same else None,
                 "launch": {"warps_per_frame": info["warps_per_frame"], "frames_per_cta": info["frames_per_cta"],
                            "smem_per_frame": info["smem_per_frame"], "grid": info["grid"]}}
     finally:
         plan.close()
         code.close()
+
+
+def compact_rows(block, keys):
+    """A measured table as {"cols": keys, "rows": [[...], ...]} with rounded numbers."""
+    if not block or "rows" not in block:
+        return block
+
+    def rnd(v):
+        return round(v, 4) if isinstance(v, float) else v
+    return {"cols": list(keys), "rows": [[rnd(r.get(k)) for k in keys] for r in block["rows"]]}
+
+
+def compact_headline(h):
+    if not h or "error" in h:
+        return h
+    rf = h.get("roofline") or {}
+    return {"workload": h["workload"], "value": h["value"], "plain_value": h["plain_value"],
+            "ms_per_step": h["ms_per_step"], "plain_ms_per_step": h["plain_ms_per_step"],
+            "batched_over_plain": h["value"] / h["plain_value"] if h["value"] else None,
+            "roofline_frac": rf.get("frac"), "plain_roofline_frac": rf.get("plain_frac"),
+            "graph_replay": h["graph_replay"], "results_equal_plain": h["results_equal_plain"]}
 
 
 def measure_serving(args):
@@ -791,7 +869,7 @@ def run_ours(args):
     if not args.skip_batched:
         try:
             batched_headline = measure_batched_headline(args, torch, dev, stream, barrier, llr, frozen,
-                                                        tuple(tuned), ops_frame, peak, bits, pm)
+                                                        tuple(tuned), ops_frame, peak, bits, pm, ok, ms_per_step)
         except Exception as e:   # an extra measurement must not cost the contract line
             batched_headline = {"error": f"{type(e).__name__}: {e}"}
 
@@ -848,6 +926,13 @@ def run_ours(args):
         cpu = cpu_baseline(llr_np, frozen, args.cpu_seconds)
 
     if rank == 0:
+        full = {"fer": fer_sweep, "ablation": ablation, "wide_lists": wide, "rates_table4": rates,
+                "batched": batched, "batched_headline": batched_headline, "serving": serving}
+        if args.details:
+            with open(args.details, "w") as fh:
+                json.dump(full, fh, indent=1)
+        # One line; the bulky tables are compact and come first, the metric's own
+        # comparisons (FER match, p99 latency, batched vs plain) come last.
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -861,14 +946,19 @@ def run_ours(args):
             "fer_sample": fer,
             "wall_s_timed": t_wall,
             "launch": launch_info,
-            "other_dtype": other,
-            "batched": batched,
-            "batched_headline": batched_headline,
-            "serving": serving,
-            "fer": fer_sweep,
-            "ablation": ablation,
-            "wide_lists": wide,
-            "rates_table4": rates,
+            "ablation": compact_rows(ablation, ("L", "decoder", "gbps", "one_frame_latency_us")),
+            "wide_lists": compact_rows(wide, ("crc", "ebn0_db", "errors", "frames", "gbps")),
+            "rates_table4": compact_rows(rates, ("rate", "k", "gbps", "one_frame_latency_us", "fer")),
+            "other_dtype": {"dtype": other.get("dtype"), "value": other.get("value"),
+                            "ms_per_step": other.get("ms_per_step")} if other else None,
+            "adaptive": compact_adaptive(fer_sweep),
+            "fer": compact_fer(fer_sweep),
+            "serving": {x: serving.get(x) for x in ("offered_frames_per_s", "requests", "frames", "p50_ms", "p99_ms",
+                                                    "info_gbps")} if serving else None,
+            "batched": {x: batched.get(x) for x in ("value", "plain_value", "ms_per_step", "plain_ms_per_step",
+                                                    "plain_launches_per_step", "results_equal_plain")}
+            if batched else None,
+            "batched_headline": compact_headline(batched_headline),
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -365,12 +365,14 @@ POLAR_API int polar_server_stats(polar_server_t *server, polar_server_stats_t *s
 
 /* Allocation-free variant of polar_list_decode. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory while decoding -- work captured into a CUDA graph that must
- * not hold allocation nodes, real-time paths that may not take allocator
- * locks or fail for lack of memory after start-up, and hosts that give the
- * decoder a fixed memory budget.
+ * device memory while decoding -- real-time paths that may not take
+ * allocator locks or fail for lack of memory once they are running, and
+ * hosts that give the decoder a fixed memory budget and own every other
+ * allocation themselves.
  *
- * Same arguments, outputs and results as polar_list_decode. Instead of
+ * Same arguments, outputs and results as polar_list_decode, for codes with
+ * L <= 32; a wide code (L = 64 or 128) is refused with POLAR_EUNSUPPORTED,
+ * because its kernel keeps every stage in scratch sized per frame. Instead of
  * taking scratch from the stream-ordered allocator, the alpha stages that do
  * not fit in shared memory go to one fixed device array built into the
  * library, of polar_noalloc_scratch_bytes() bytes (64 MiB); every GPU that

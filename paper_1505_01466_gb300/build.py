@@ -1,6 +1,7 @@
 """Build ``libpolar_gb300.so`` in-tree with nvcc for sm_103a.
 
-The three translation units (host runtime, narrow and wide kernels) compile in parallel and
+The four translation units (host runtime, list kernels, wide-list kernel and the L = 1
+kernel) compile in parallel and
 are linked into one shared library next to this file. No CMake, no torch
 extension machinery: the library has a plain C ABI (include/polar.h).
 """

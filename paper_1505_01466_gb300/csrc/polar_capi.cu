@@ -591,10 +591,9 @@ int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
 }
 
 // ---- allocation-free decoding ----------------------------------------------
-// Some callers cannot allocate device memory while they decode: code running
-// inside a captured CUDA graph that must not contain allocation nodes, real-
-// time paths that must not take allocator locks or risk an out-of-memory
-// failure after start-up, and hosts that hand the decoder a fixed memory
+// Some callers cannot allocate device memory while they decode: real-time
+// paths that must not take allocator locks or risk an out-of-memory failure
+// once they are running, and hosts that hand the decoder a fixed memory
 // budget. For them the spilled alpha stages live in one fixed array that is
 // part of the library image: every GPU that loads the library holds these
 // kNoAllocScratchBytes until the process exits.

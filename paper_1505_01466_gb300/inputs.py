@@ -38,7 +38,7 @@ import numpy as np
 __all__ = [
     "CRC8_POLY", "CRC32_POLY", "crc_bits", "polar_transform", "ga_leaf_means",
     "ga_frozen_mask", "info_positions", "sigma_for", "Frames", "make_frames",
-    "quantize_i8", "pack_bits_lsb", "unpack_bits_lsb",
+    "quantize_i8", "pack_bits_lsb", "unpack_bits_lsb", "crc_generator_matrix", "make_frames_torch",
 ]
 
 CRC8_POLY = 0x07
@@ -295,6 +295,66 @@ def make_frames_chunked(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, eb
                   codeword=np.concatenate([p.codeword for p in parts]),
                   llr_f32=np.concatenate([p.llr_f32 for p in parts]),
                   llr_i8=np.concatenate([p.llr_i8 for p in parts]), sigma=parts[0].sigma)
+
+
+def crc_generator_matrix(k: int, crc_len: int, crc_poly: int) -> np.ndarray:
+    """CRC bits of each unit payload vector e_t, uint8 [k, crc_len]. With a
+    zero initial register and no final xor the CRC is linear over GF(2), so
+    the CRC of a payload p is p C mod 2."""
+    return crc_bits(np.eye(k, dtype=np.uint8), crc_len, crc_poly)
+
+
+def make_frames_torch(frozen_mask: np.ndarray, crc_len: int, crc_poly: int, ebn0_db: float,
+                      n_frames: int, seed: int, device, chunk: int = 1 << 17):
+    """The frames of make_frames, generated with torch on ``device`` for
+    Monte-Carlo sweeps of millions of frames: random payload bits, the CRC
+    as p C mod 2 (crc_generator_matrix, exact in float64), u at the
+    information positions, x = u G_N by butterflies, BPSK, float32 Gaussian
+    noise from torch's generator seeded with ``seed``, LLR = 2 y / sigma^2,
+    and the int8 quantisation of quantize_i8 applied to the float32 LLRs.
+
+    Returns (payload uint8 [F, k], llr_f32 float32 [F, N], llr_i8 int8 [F, N]),
+    all on ``device``. The streams differ from make_frames' (another
+    generator), the construction is the same.
+    """
+    import torch
+    frozen_mask = np.asarray(frozen_mask, dtype=np.uint8)
+    N = frozen_mask.size
+    info = info_positions(frozen_mask)
+    K = info.size
+    k = K - crc_len
+    if k < 0:
+        raise ValueError("crc_len larger than K")
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    C = torch.from_numpy(crc_generator_matrix(k, crc_len, crc_poly).astype(np.float64)).to(dev)
+    info_pay = torch.from_numpy(info[:k]).to(dev)
+    info_crc = torch.from_numpy(info[k:]).to(dev)
+    rate = k / N if k > 0 else K / N if K > 0 else 1.0 / N
+    sig = sigma_for(ebn0_db, rate)
+    payload = torch.empty((n_frames, k), dtype=torch.uint8, device=dev)
+    llr_f32 = torch.empty((n_frames, N), dtype=torch.float32, device=dev)
+    llr_i8 = torch.empty((n_frames, N), dtype=torch.int8, device=dev)
+    for s in range(0, n_frames, chunk):
+        n = min(chunk, n_frames - s)
+        p = torch.randint(0, 2, (n, k), generator=gen, device=dev, dtype=torch.uint8)
+        u = torch.zeros((n, N), dtype=torch.uint8, device=dev)
+        u[:, info_pay] = p
+        if crc_len:
+            u[:, info_crc] = torch.remainder(p.to(torch.float64) @ C, 2.0).to(torch.uint8)
+        h = 1
+        while h < N:
+            v = u.view(n, N // (2 * h), 2, h)
+            v[:, :, 0, :] ^= v[:, :, 1, :]
+            h *= 2
+        y = 1.0 - 2.0 * u.to(torch.float32)
+        y += sig * torch.randn((n, N), generator=gen, device=dev, dtype=torch.float32)
+        llr = y * (2.0 / (sig * sig))
+        payload[s: s + n] = p
+        llr_f32[s: s + n] = llr
+        llr_i8[s: s + n] = torch.clamp(torch.round(llr * 4.0), -127, 127).to(torch.int8)
+    return payload, llr_f32, llr_i8
 
 
 # --------------------------------------------------------------------------

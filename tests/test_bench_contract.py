@@ -70,3 +70,34 @@ def test_adaptive_throughput_reproduces_table_2():
     assert bench.adaptive_throughput(k, 1.0, lat_f, lat[32]) == pytest.approx(k / (lat_f + lat[32]))
     # and the list decoder alone at L = 32: 4.0 Mbps (Sec. VI-B)
     assert round(k / lat[32], 1) == 4.0
+
+
+def test_metric_comparisons_fit_the_line_tail():
+    """The bench line keeps its last blocks short: the FER sweep of both codes
+    (60 points), the serving figures and the two batched-vs-plain pairs must
+    fit in the final 3000 characters of the printed line."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = []
+    for code, Ls in (("(1024,860)", (2, 4, 8, 32)), ("(2048,1723)", (8, 32))):
+        for L in Ls:
+            for dt in ("f32", "i8"):
+                for eb in (3.5, 3.75, 4.0, 4.25, 4.5):
+                    rows.append({"code": code, "L": L, "dtype": dt, "ebn0_db": eb, "frames": 1048576,
+                                 "errors_fast": 123456, "errors_scl": 123457, "mcnemar_p": 0.123456789,
+                                 "fer_match": True, "underpowered": False})
+    fer = bench.compact_fer({"rows": rows})
+    assert sum(len(v) for k, v in fer.items() if k.startswith("(")) == 60
+    head = {"workload": "(2048,1723) CRC-32 L=32, one class, the plain form's 1048576 frames per GPU",
+            "value": 3.123456789, "plain_value": 2.987654321, "ms_per_step": 567.891234, "plain_ms_per_step": 590.1234,
+            "graph_replay": True, "results_equal_plain": True, "roofline": {"frac": 0.0412345, "plain_frac": 0.04}}
+    tail = {"fer": fer,
+            "serving": {"offered_frames_per_s": 200000.0, "requests": 1234, "frames": 1612345,
+                        "p50_ms": 0.423456789, "p99_ms": 4.123456789, "info_gbps": 0.19123456789},
+            "batched": {"value": 5.3123456789, "plain_value": 4.6312345678, "ms_per_step": 123.456789,
+                        "plain_ms_per_step": 140.123456789, "plain_launches_per_step": 125,
+                        "results_equal_plain": True},
+            "batched_headline": bench.compact_headline(head)}
+    text = json.dumps(tail)
+    assert len(text) < 3000, len(text)
+    assert bench.compact_headline(dict(head, value=None, roofline=None))["batched_over_plain"] is None

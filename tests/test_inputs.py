@@ -156,3 +156,39 @@ def test_systematic_encoder_places_data_in_the_codeword():
         # the non-systematic encoding of the same data differs (but is also a codeword)
         g = I.make_frames(fr, 32, I.CRC32_POLY, db, 20, seed=N, noiseless=True)
         assert np.array_equal(g.payload, f.payload) and not np.array_equal(g.codeword, f.codeword)
+
+
+def test_torch_frames_follow_the_same_construction():
+    torch = pytest.importorskip("torch")
+    fr = I.ga_frozen_mask(128, 72, 2.0, 64 / 128)
+    info = I.info_positions(fr)
+    pay, f32, i8 = I.make_frames_torch(fr, 8, I.CRC8_POLY, 2.0, 600, seed=9, device="cpu", chunk=256)
+    pay, f32, i8 = pay.numpy(), f32.numpy(), i8.numpy()
+    # the CRC matrix is the CRC of unit vectors, and linearity gives every CRC
+    C = I.crc_generator_matrix(64, 8, I.CRC8_POLY)
+    assert np.array_equal((pay.astype(np.int64) @ C) % 2, I.crc_bits(pay, 8, I.CRC8_POLY))
+    # at a very high Eb/N0 the hard decisions are the codeword: its u carries
+    # the payload and the CRC at the information positions and zeros elsewhere
+    pay2, f2, _ = I.make_frames_torch(fr, 8, I.CRC8_POLY, 60.0, 50, seed=4, device="cpu")
+    x = (f2.numpy() < 0).astype(np.uint8)
+    u = I.polar_transform(x)
+    assert not u[:, fr == 1].any()
+    assert np.array_equal(u[:, info[:64]], pay2.numpy())
+    assert np.array_equal(u[:, info[64:]], I.crc_bits(pay2.numpy(), 8, I.CRC8_POLY))
+    # LLR = 2 y / sigma^2 with y = (1 - 2x) + sigma n: mean 2/sigma^2 * (1 - 2x), variance 4/sigma^2
+    sig = I.sigma_for(2.0, 64 / 128)
+    z = f32 * (sig * sig / 2.0)
+    # recover the codeword from the payload to centre the noise
+    u = np.zeros((600, 128), np.uint8)
+    u[:, info[:64]] = pay
+    u[:, info[64:]] = I.crc_bits(pay, 8, I.CRC8_POLY)
+    xs = I.polar_transform(u)
+    noise = (z - (1.0 - 2.0 * xs)) / sig
+    assert abs(noise.mean()) < 0.01 and abs(noise.std() - 1.0) < 0.01
+    # int8: rint(4 LLR) clamped to +-127
+    want = np.clip(np.rint(f32.astype(np.float64) * 4.0), -127, 127)
+    assert np.abs(i8.astype(np.float64) - want).max() <= 1.0
+    assert (i8 == want).mean() > 0.999
+    # a seed fixes the stream
+    pay3, f3, _ = I.make_frames_torch(fr, 8, I.CRC8_POLY, 2.0, 600, seed=9, device="cpu", chunk=256)
+    assert np.array_equal(pay3.numpy(), pay) and np.array_equal(f3.numpy(), f32)
