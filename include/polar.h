@@ -161,6 +161,8 @@ typedef struct {
     uint32_t smem_per_frame[2];      /* bytes of shared memory per frame in flight */
     uint64_t scratch_per_frame[2];   /* bytes of global scratch per frame in flight */
     uint32_t spill_mask[2];          /* alpha stages kept in global scratch */
+    uint32_t recomputed_stages[2];   /* alpha stages not stored: evaluated from the channel */
+    uint32_t max_recompute_depth;    /* how many top stages may be (see polar_code_set_recompute) */
 } polar_code_info_t;
 
 /* Fill *info (host memory, caller-owned). Errors: POLAR_EINVAL (NULL). */
@@ -193,6 +195,22 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
  * code, L > 32), POLAR_ENOMEM / POLAR_ECUDA (uploading the flagged schedule). */
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                                     uint32_t smem_budget, uint32_t cta_threads);
+
+/* Stage memory against recomputation (Sec. IV-E counts one alpha row per
+ * path and stage). The top `depth` alpha stages (at most
+ * max_recompute_depth, at most 3) are not stored: an F or G that reads one
+ * evaluates it from the channel row and the paths' left-sibling betas by
+ * Eqs. (1)-(2), 2^depth channel values per element. That removes
+ * L (2^(n-1) + ... + 2^(n-depth)) values per frame in flight from the
+ * scratch working set (at (2048,1723) L = 32 f32, depth 2: 192 KB of 260 KB).
+ * Only stages every node of which is an inner node qualify. Results do not
+ * depend on the depth. The default is 0 (every stage stored); keeps the
+ * current warps, budget and CTA size. polar_code_autotune times depths
+ * 1 .. max_recompute_depth on the best fully stored shape and keeps a depth
+ * only if it is faster. Errors: POLAR_EINVAL (bad
+ * arguments, depth too large), POLAR_EUNSUPPORTED (a wide code),
+ * POLAR_ENOMEM / POLAR_ECUDA (uploading the schedule). */
+POLAR_API int polar_code_set_recompute(polar_code_t *code, int llr_dtype, uint32_t depth);
 
 /* polar_list_decode on HOST buffers (same layouts, host pointers): the frames
  * go through the device in chunks, the copy in of one chunk and the copy out

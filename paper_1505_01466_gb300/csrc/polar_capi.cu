@@ -66,6 +66,12 @@ struct polar_code {
     // fixed a shape of the list kernels)
     std::vector<uint32_t> sops;
     uint32_t *d_sops = nullptr;
+    // Top alpha stages that may be evaluated from the channel instead of
+    // stored (every node there an inner node of the list schedule, at most
+    // three stages, none below stage kSubLog + 2), and the number in use for
+    // each LLR type.
+    uint32_t vmax = 0;
+    uint32_t vdepth[2] = {0, 0};
 };
 
 namespace {
@@ -243,10 +249,10 @@ struct TreeBuilder {
         }
         const uint32_t h = 1u << (j - 1);
         expand(OP_F, j, 0, start);
-        ops.push_back(op_make(OP_F, (uint32_t)j, 0));
+        ops.push_back(op_with_start(op_make(OP_F, (uint32_t)j, 0), start));
         build(j - 1, start, 0);
         expand(OP_G, j, 0, start);
-        ops.push_back(op_make(OP_G, (uint32_t)j, 0));
+        ops.push_back(op_with_start(op_make(OP_G, (uint32_t)j, 0), start));
         build(j - 1, start + h, 1);
         expand(OP_COMB, j, dest, start);
         ops.push_back(op_make(OP_COMB, (uint32_t)j, dest));
@@ -296,13 +302,15 @@ void build_syndrome(polar_code *c) {
 // together with the right/root beta and the channel row they go to shared
 // memory until the budget is reached, the largest ones spilling to the
 // group's global scratch first.
-bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &lay) {
+bool build_layout(uint32_t n, uint32_t L, uint32_t es, uint32_t budget, Layout &lay, uint32_t virt_mask = 0) {
     std::memset(&lay, 0, sizeof(lay));
     const uint32_t N = 1u << n;
     const uint32_t lo = std::min<uint32_t>((uint32_t)kSubLog, n);
     struct Buf { int kind; uint32_t j; uint32_t bytes; bool spill; };
     std::vector<Buf> bufs;
-    for (uint32_t j = lo; j < n; ++j) bufs.push_back({0, j, al16(L * (1u << j) * es), false});
+    lay.virt_mask = virt_mask;
+    for (uint32_t j = lo; j < n; ++j)
+        if (!((virt_mask >> j) & 1u)) bufs.push_back({0, j, al16(L * (1u << j) * es), false});
     for (uint32_t j = lo; j < n; ++j) bufs.push_back({1, j, al16(L * 4u * (uint32_t)beta_words((int)j)), false});
     bufs.push_back({2, 0, al16(L * 4u * (uint32_t)beta_words((int)n)), false});
     bufs.push_back({3, 0, al16(N * es), false});
@@ -354,8 +362,11 @@ std::vector<uint32_t> flag_ops(const std::vector<uint32_t> &ops, uint32_t warps)
     return out;
 }
 
+// Stages n - d .. n - 1, the ones evaluated from the channel at depth d.
+uint32_t virt_mask_of(uint32_t n, uint32_t d) { return d == 0 ? 0u : ((1u << d) - 1u) << (n - d); }
+
 bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget, LaunchShape &sh,
-                uint32_t cta_threads = 0) {
+                uint32_t cta_threads = 0, int vdepth = -1) {
     if (warps != 1 && warps != 2 && warps != 4) return false;
     if (cta_threads == 0) cta_threads = 128;
     if (cta_threads % (32u * warps) != 0 || cta_threads > (uint32_t)kMaxCtaThreads) return false;
@@ -368,9 +379,12 @@ bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget,
         budget = (kMaxSmemPerCta / std::max(groups_per_sm, gpc)) & ~15u;
     }
     budget = std::min(budget, kMaxSmemPerCta / gpc);
+    const uint32_t vd = vdepth < 0 ? c->vdepth[dtype] : (uint32_t)vdepth;
+    if (vd > c->vmax) return false;
     Layout lay;
-    if (!build_layout(c->n, c->L, es, budget, lay)) return false;
+    if (!build_layout(c->n, c->L, es, budget, lay, virt_mask_of(c->n, vd))) return false;
     sh.d_ops = nullptr;
+    sh.budget = budget;
     sh.warps = (int)warps;
     sh.groups_per_cta = (int)gpc;
     sh.threads = (int)cta_threads;
@@ -682,6 +696,20 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     c->sched = std::move(tb.sched);
     for (size_t i = 0; i < c->xops.size(); ++i)
         c->sops.push_back(sc1_op(op_kind(c->xops[i]), (uint32_t)op_stage(c->xops[i]), (uint32_t)c->sched[3 * i + 2]));
+    // stages every node of which is an inner node run by F / G / Combine can be
+    // evaluated from the channel (top stages only, at most three, >= kSubLog + 2)
+    for (uint32_t d = 1; d <= 3 && d + (uint32_t)kSubLog + 2 <= c->n; ++d) {
+        const uint32_t j = c->n - d;
+        bool inner = true;
+        for (uint32_t op : c->ops) {
+            const uint32_t k = op_kind(op);
+            if ((uint32_t)op_stage(op) == j && k != OP_F && k != OP_G && k != OP_COMB) inner = false;
+        }
+        if (!inner) break;
+        c->vmax = d;
+    }
+    // stored by default: measured, evaluating them costs more than it saves
+    for (int d = 0; d < 2; ++d) c->vdepth[d] = 0;
     c->n_leaves = tb.leaves;
     c->n_r0 = tb.r0;
     c->n_r1 = tb.r1;
@@ -717,7 +745,7 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     }
     for (int d = 0; d < 2; ++d) {
         LaunchShape lat;
-        if (!c->host_only && make_shape(c, d, 4, 0xffffffffu, lat, 128) &&
+        if (!c->host_only && make_shape(c, d, 4, 0xffffffffu, lat, 128, 0) &&
             upload(&lat.d_ops, flag_ops(c->ops, 4)) == cudaSuccess)
             c->lat[d] = lat;
     }
@@ -909,17 +937,24 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     float best_ms = 1e30f;
     LaunchShape best;
     uint32_t best_w = 0, best_b = 0, best_t = 0;
-    std::vector<std::array<uint32_t, 3>> seen;   // (warps, CTA threads, spill mask) already timed
+    std::vector<std::array<uint32_t, 5>> seen;   // (warps, CTA threads, spill masks, depth) already timed
     int status = POLAR_OK;
+    uint32_t best_vd = 0;
+    // every shape with all stages stored, then the best one with 1 .. vmax
+    // top stages evaluated from the channel
+    for (uint32_t vd = 0; vd <= code->vmax && status == POLAR_OK; ++vd) {
     for (uint32_t w : {4u, 2u, 1u}) {
       for (uint32_t t : {128u, 256u, 512u}) {
         for (uint32_t b : budgets) {
+            if (vd > 0 && (w != best_w || t != best_t || b != best_b)) continue;
             LaunchShape sh;
-            if (!make_shape(code, llr_dtype, w, b, sh, t)) continue;
+            if (!make_shape(code, llr_dtype, w, b, sh, t, (int)vd)) continue;
             bool dup = false;
-            for (auto &pr : seen) dup |= pr[0] == w && pr[1] == t && pr[2] == sh.lay.spill_mask;
+            for (auto &pr : seen)
+                dup |= pr[0] == w && pr[1] == t && pr[2] == sh.lay.spill_mask && pr[3] == sh.lay.flags &&
+                       pr[4] == vd;
             if (dup) continue;
-            seen.push_back({w, t, sh.lay.spill_mask});
+            seen.push_back({w, t, sh.lay.spill_mask, sh.lay.flags, vd});
             std::vector<uint32_t> fl = flag_ops(code->ops, w);
             if (upload(&sh.d_ops, fl) != cudaSuccess) { status = POLAR_ECUDA; break; }
             float ms = 0.f;
@@ -934,11 +969,12 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
             cudaFree(sh.d_ops);
             sh.d_ops = nullptr;
             if (rc != POLAR_OK) continue;
-            if (ms < best_ms) { best_ms = ms; best = sh; best_w = w; best_b = b; best_t = t; }
+            if (ms < best_ms) { best_ms = ms; best = sh; best_w = w; best_b = b; best_t = t; best_vd = vd; }
         }
         if (status != POLAR_OK) break;
       }
       if (status != POLAR_OK) break;
+    }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -950,6 +986,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     if (budget_out) *budget_out = best_b == 0xffffffffu ? 0u : best_b;
     if (cta_out) *cta_out = best_t;
     code->explicit_shape[llr_dtype] = false;
+    code->vdepth[llr_dtype] = best_vd;
     return install_shape(code, llr_dtype, best);
 }
 
@@ -1339,7 +1376,9 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
         info->smem_per_frame[d] = c->shape[d].lay.bytes;
         info->scratch_per_frame[d] = c->shape[d].lay.gbytes;
         info->spill_mask[d] = c->shape[d].lay.spill_mask;
+        info->recomputed_stages[d] = c->shape[d].lay.virt_mask;
     }
+    info->max_recompute_depth = c->vmax;
     return POLAR_OK;
 }
 
@@ -1379,6 +1418,19 @@ int polar_code_op_count(const polar_code_t *c, uint64_t *ops_per_frame) {
     tot += (uint64_t)c->L * c->N * c->n / 32 + (uint64_t)c->L * c->K;
     *ops_per_frame = tot;
     return POLAR_OK;
+}
+
+int polar_code_set_recompute(polar_code_t *c, int llr_dtype, uint32_t depth) {
+    if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
+    if (c->wide) return POLAR_EUNSUPPORTED;
+    if (depth > c->vmax) return POLAR_EINVAL;
+    LaunchShape sh;
+    const LaunchShape &cur = c->shape[llr_dtype];
+    if (!make_shape(c, llr_dtype, (uint32_t)cur.warps, cur.budget, sh, (uint32_t)cur.threads, (int)depth))
+        return POLAR_EINVAL;
+    const int st = install_shape(c, llr_dtype, sh);
+    if (st == POLAR_OK) c->vdepth[llr_dtype] = depth;
+    return st;
 }
 
 int polar_code_set_launch(polar_code_t *c, int llr_dtype, uint32_t warps_per_frame, uint32_t smem_budget,

@@ -46,6 +46,11 @@ __host__ __device__ inline bool op_solo(uint32_t op) { return ((op >> 9) & 1u) !
 __host__ __device__ inline bool op_sync(uint32_t op) { return ((op >> 10) & 1u) != 0; }
 constexpr uint32_t OP_SOLO = 1u << 9;
 constexpr uint32_t OP_SYNC = 1u << 10;
+// OP_F / OP_G only: bits 16..27 = first bit index s of the node. The node at
+// stage j' >= j containing bit s is the right child of its parent iff bit j'
+// of s is set; stages evaluated from the channel (Layout::virt_mask) need it.
+__host__ __device__ inline uint32_t op_with_start(uint32_t op, uint32_t s) { return op | (s << 16); }
+__host__ __device__ inline uint32_t op_start(uint32_t op) { return (op >> 16) & 0xFFFu; }
 // OP_SUB only: bit 11 = the subtree forks paths, bits 12..14 = log2 of the
 // product of its leaves' candidate counts (saturated at 6; the live paths
 // become min(L, L_a * 2^m)), bits 15.. = index of its descriptor.
@@ -76,6 +81,8 @@ struct Layout {
     uint32_t spill_mask;           // bit j: alpha stage j in global scratch
     uint32_t bl_spill;             // bit j: left beta of stage j in global scratch
     uint32_t flags;                // bit 0: BR in global scratch, bit 1: channel in global scratch
+    uint32_t virt_mask;            // bit j: alpha stage j is not stored; F / G reading it evaluate it
+                                   // from the channel (stages n-D .. n-1, every node there inner)
     uint64_t galpha[kMaxLogN];     // global offsets of spilled buffers
     uint64_t gbl[kMaxLogN];
     uint64_t gbr, gchan;
@@ -140,6 +147,7 @@ constexpr int kMaxCtaThreads = 512;
 
 struct LaunchShape {
     int warps;                     // warps per frame group (1, 2, 4)
+    uint32_t budget;               // shared-memory budget per group the layout was built for
     uint32_t *d_ops;               // schedule with this shape's solo / sync flags (device)
     int groups_per_cta;
     int threads;                   // per CTA

@@ -134,6 +134,111 @@ __device__ __forceinline__ T *chan_ptr(const Layout &lay, uint8_t *S, uint8_t *G
                                          : reinterpret_cast<T *>(S + lay.chan);
 }
 
+// ---- stages evaluated from the channel (Layout::virt_mask) -----------------
+// The top D stages of some codes are not stored: alpha_j of the node holding
+// bit s, for path p, is F (Eq. (1)) of alpha_{j+1} when that node is a left
+// child, or G (Eq. (2)) with the path's left-sibling beta BL[j] when it is a
+// right child, down to the channel row. An F / G reading such a stage
+// evaluates its inputs this way (2^D channel loads per element), so those
+// stages take no memory. vload4 returns elements 4v .. 4v+3 of alpha_j (f32),
+// vload16 elements 16v .. 16v+15 (int8); D = n - j.
+template <int D>
+__device__ __forceinline__ float4 vload4(const Layout &lay, uint8_t *S, uint8_t *Gs, const float *chan,
+                                         const uint8_t *bidxc, int j, int p, int v, uint32_t s) {
+    if constexpr (D == 0) {
+        return reinterpret_cast<const float4 *>(chan)[v];
+    } else {
+        const float4 a = vload4<D - 1>(lay, S, Gs, chan, bidxc, j + 1, p, v, s);
+        const float4 b = vload4<D - 1>(lay, S, Gs, chan, bidxc, j + 1, p, v + (1 << (j - 2)), s);
+        float4 r;
+        if ((s >> j) & 1u) {
+            const uint32_t *bl = bl_ptr(lay, S, Gs, j) + (int)bidxc[p * 16 + j] * beta_words(j);
+            const int i = v << 2;
+            const uint32_t nb = bl[i >> 5] >> (i & 31);
+            r.x = g_op(a.x, b.x, nb & 1u); r.y = g_op(a.y, b.y, (nb >> 1) & 1u);
+            r.z = g_op(a.z, b.z, (nb >> 2) & 1u); r.w = g_op(a.w, b.w, (nb >> 3) & 1u);
+        } else {
+            r.x = f_op(a.x, b.x); r.y = f_op(a.y, b.y); r.z = f_op(a.z, b.z); r.w = f_op(a.w, b.w);
+        }
+        return r;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ uint4 vload16(const Layout &lay, uint8_t *S, uint8_t *Gs, const int8_t *chan,
+                                         const uint8_t *bidxc, int j, int p, int v, uint32_t s) {
+    if constexpr (D == 0) {
+        return reinterpret_cast<const uint4 *>(chan)[v];
+    } else {
+        const uint4 a = vload16<D - 1>(lay, S, Gs, chan, bidxc, j + 1, p, v, s);
+        const uint4 b = vload16<D - 1>(lay, S, Gs, chan, bidxc, j + 1, p, v + (1 << (j - 4)), s);
+        uint4 r;
+        if ((s >> j) & 1u) {
+            const uint32_t *bl = bl_ptr(lay, S, Gs, j) + (int)bidxc[p * 16 + j] * beta_words(j);
+            const int i = v << 4;
+            const uint32_t nb = bl[i >> 5] >> (i & 31);
+            r.x = g4(a.x, b.x, nb & 15u); r.y = g4(a.y, b.y, (nb >> 4) & 15u);
+            r.z = g4(a.z, b.z, (nb >> 8) & 15u); r.w = g4(a.w, b.w, (nb >> 12) & 15u);
+        } else {
+            r.x = f4(a.x, b.x); r.y = f4(a.y, b.y); r.z = f4(a.z, b.z); r.w = f4(a.w, b.w);
+        }
+        return r;
+    }
+}
+
+// F / G of one node whose input stage j is evaluated from the channel (D =
+// n - j levels), writing the stored stage j - 1 for every live path.
+template <typename T, int D>
+__device__ __noinline__ void fg_virtual(const Layout &lay, uint8_t *S, uint8_t *Gs, const T *chan,
+                                           uint8_t *idxc, const uint8_t *bidxc, bool isG, int j, uint32_t s, int La,
+                                           int tid, int nthr) {
+    const int jo = j - 1;
+    const int h = 1 << jo;
+    T *outb = alpha_ptr<T>(lay, S, Gs, jo);
+    const uint32_t *blb = bl_ptr(lay, S, Gs, jo);
+    const int bwc = beta_words(jo);
+    if (sizeof(T) == 4) {
+        const int lv = jo - 2;
+        const int total = La << lv;
+        for (int t = tid; t < total; t += nthr) {
+            const int p = t >> lv, v = t & ((1 << lv) - 1);
+            const float *ch = reinterpret_cast<const float *>(chan);
+            const float4 a = vload4<D>(lay, S, Gs, ch, bidxc, j, p, v, s);
+            const float4 b = vload4<D>(lay, S, Gs, ch, bidxc, j, p, v + (h >> 2), s);
+            float4 r;
+            if (isG) {
+                const int i = v << 2;
+                const uint32_t nb = blb[(int)bidxc[p * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
+                r.x = g_op(a.x, b.x, nb & 1u); r.y = g_op(a.y, b.y, (nb >> 1) & 1u);
+                r.z = g_op(a.z, b.z, (nb >> 2) & 1u); r.w = g_op(a.w, b.w, (nb >> 3) & 1u);
+            } else {
+                r.x = f_op(a.x, b.x); r.y = f_op(a.y, b.y); r.z = f_op(a.z, b.z); r.w = f_op(a.w, b.w);
+            }
+            reinterpret_cast<float4 *>(reinterpret_cast<float *>(outb) + (p << jo))[v] = r;
+        }
+    } else {
+        const int lv = jo - 4;
+        const int total = La << lv;
+        for (int t = tid; t < total; t += nthr) {
+            const int p = t >> lv, v = t & ((1 << lv) - 1);
+            const int8_t *ch = reinterpret_cast<const int8_t *>(chan);
+            const uint4 a = vload16<D>(lay, S, Gs, ch, bidxc, j, p, v, s);
+            const uint4 b = vload16<D>(lay, S, Gs, ch, bidxc, j, p, v + (h >> 4), s);
+            uint4 r;
+            if (isG) {
+                const int i = v << 4;
+                const uint32_t nb = blb[(int)bidxc[p * 16 + jo] * bwc + (i >> 5)] >> (i & 31);
+                r.x = g4(a.x, b.x, nb & 15u); r.y = g4(a.y, b.y, (nb >> 4) & 15u);
+                r.z = g4(a.z, b.z, (nb >> 8) & 15u); r.w = g4(a.w, b.w, (nb >> 12) & 15u);
+            } else {
+                r.x = f4(a.x, b.x); r.y = f4(a.y, b.y); r.z = f4(a.z, b.z); r.w = f4(a.w, b.w);
+            }
+            reinterpret_cast<uint4 *>(reinterpret_cast<int8_t *>(outb) + (p << jo))[v] = r;
+        }
+    }
+    for (int t = tid; t < La; t += nthr) idxc[t * 16 + jo] = (uint8_t)t;
+}
+
 // SPC candidate flips over the ranks of the four least reliable bits (bit r
 // = rank r+1), in the candidate order {}, {1,2}, {1,3}, {1,4}, {2,3}, {2,4},
 // {3,4}, {1,2,3,4}.
@@ -1059,7 +1164,18 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
         uint8_t *idxc = S + lay.idx[cur];
         uint8_t *bidxc = S + lay.bidx[cur];
 
-        if (kind == OP_F || kind == OP_G) {
+        if ((kind == OP_F || kind == OP_G) && ((lay.virt_mask >> (j - 1)) & 3u)) {
+            // input stage j is evaluated from the channel; an output stage that is
+            // evaluated too is left to its readers
+            if (!((lay.virt_mask >> (j - 1)) & 1u) && (!solo || wig == 0)) {
+                const uint32_t s0 = op_start(op);
+                const bool isG = kind == OP_G;
+                const int D = n - j;
+                if (D == 1) fg_virtual<T, 1>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
+                else if (D == 2) fg_virtual<T, 2>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
+                else fg_virtual<T, 3>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
+            }
+        } else if (kind == OP_F || kind == OP_G) {
             if (!solo || wig == 0) {
                 // ---------------- F / G: stage j -> stage j-1 ----------------
                 const int jo = j - 1;

@@ -25,6 +25,7 @@ INJECT_ALLOC_FAIL, INJECT_POISON = 1, 2
 EXPORTED = [
     "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror", "polar_sync",
     "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
+    "polar_code_set_recompute",
     "polar_code_autotune", "polar_list_decode_noalloc", "polar_noalloc_scratch_bytes",
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
@@ -48,6 +49,7 @@ class CodeInfo(ctypes.Structure):
         ("n_spc", ctypes.c_uint32), ("warps_per_frame", ctypes.c_uint32 * 2),
         ("frames_per_cta", ctypes.c_uint32 * 2), ("smem_per_frame", ctypes.c_uint32 * 2),
         ("scratch_per_frame", ctypes.c_uint64 * 2), ("spill_mask", ctypes.c_uint32 * 2),
+        ("recomputed_stages", ctypes.c_uint32 * 2), ("max_recompute_depth", ctypes.c_uint32),
     ]
 
 
@@ -109,6 +111,7 @@ def _lib():
         lib.polar_code_schedule.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
         lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
         lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32, u32]
+        lib.polar_code_set_recompute.argtypes = [vp, i32, u32]
         lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32),
                                              ctypes.POINTER(u32)]
         lib.polar_list_decode_noalloc.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
@@ -234,6 +237,10 @@ class PolarCode:
     def set_launch(self, dtype: int, warps_per_frame: int, smem_budget: int = 0, cta_threads: int = 0):
         _check(_lib().polar_code_set_launch(self._h, dtype, warps_per_frame, smem_budget, cta_threads),
                "polar_code_set_launch")
+
+    def set_recompute(self, dtype: int, depth: int):
+        """Evaluate the top ``depth`` alpha stages from the channel instead of storing them."""
+        _check(_lib().polar_code_set_recompute(self._h, dtype, depth), "polar_code_set_recompute")
 
     def autotune(self, llr, stream=None):
         """Time the launch shapes on ``llr`` ([F, N] CUDA tensor) and keep the fastest."""

@@ -119,8 +119,8 @@ def test_code_info_and_op_count(polar):
         assert info["smem_per_frame"][d] * info["frames_per_cta"][d] <= 232448
     assert code.op_count() > 2048 * 11  # at least one path's F/G work
     # a smaller budget moves more alpha stages to global scratch
-    code.set_launch(1, 4, 40000)
-    assert code.info()["smem_per_frame"][1] <= 40000
+    code.set_launch(1, 4, 20000)
+    assert code.info()["smem_per_frame"][1] <= 20000
     assert code.info()["spill_mask"][1] != 0
     with pytest.raises(polar.PolarError):
         code.set_launch(1, 3, 0)
@@ -192,6 +192,7 @@ def test_stage_memory_follows_the_paper_accounting(polar, dtype, es, L):
         fr = I.ga_frozen_mask(N, N // 2, 2.0)
         code = polar.PolarCode(fr, 8, I.CRC8_POLY, L, host_only=True)
         code.set_launch(dtype, 1, 232448, 32)
+        code.set_recompute(dtype, 0)
         info = code.info()
         if info["spill_mask"][dtype] or info["scratch_per_frame"][dtype]:
             pytest.skip("does not fit shared memory")
@@ -210,6 +211,7 @@ def test_stage_memory_follows_the_paper_accounting(polar, dtype, es, L):
     fr = I.ga_frozen_mask(N, N // 2, 2.0)
     code = polar.PolarCode(fr, 8, I.CRC8_POLY, L, host_only=True)
     code.set_launch(dtype, 1, 232448, 32)
+    code.set_recompute(dtype, 0)
     per_path_tables = 2 * 16 + 2 * 16 + 2 * 4 + 8          # alpha/beta index rows, penalties, survivors
     beta_bytes = L * 4 * (sum(max(1, (1 << j) // 32) for j in range(4, 10)) + N // 32) + N // 8
     expect = es * (_paper_alpha_elems(N, L, 1) - 15 * L) + beta_bytes + L * per_path_tables
@@ -235,3 +237,28 @@ def test_l1_codes_report_their_own_kernel(polar):
     assert root.schedule() == [(13, 4096, 0)]
     assert root.info()["smem_per_frame"] == [2 * 4096 * 4 + 512, 2 * 4096 + 512]
     assert root.info()["frames_per_cta"] == [232448 // (2 * 4096 * 4 + 512), 8]
+
+
+def test_recomputed_stages_leave_the_layout(polar):
+    """Top stages evaluated from the channel take no memory: at (2048,1723)
+    L = 32 (stage 8 holds a Rate-1 leaf, so at most stages 9 and 10
+    qualify) depth 2 removes exactly L (1024 + 512) values per frame."""
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    code = polar.PolarCode(fr, 32, I.CRC32_POLY, 32, host_only=True)
+    info = code.info()
+    assert info["max_recompute_depth"] == 2
+    assert info["recomputed_stages"] == [0, 0]                    # every stage stored by default
+    for dt, es in ((0, 4), (1, 1)):
+        code.set_launch(dt, 1, 7000, 512)
+        code.set_recompute(dt, 0)
+        full = code.info()["scratch_per_frame"][dt]
+        code.set_recompute(dt, 2)
+        assert code.info()["recomputed_stages"][dt] == 0x600
+        assert full - code.info()["scratch_per_frame"][dt] == 32 * (1024 + 512) * es
+        with pytest.raises(polar.PolarError):
+            code.set_recompute(dt, 3)
+    # a code whose top stage holds a leaf has nothing to evaluate
+    half = np.zeros(1024, np.uint8)
+    half[:512] = 1                                                 # left half Rate-0, right half Rate-1
+    c2 = polar.PolarCode(half, 0, 0, 8, host_only=True)
+    assert c2.info()["max_recompute_depth"] == 0 and c2.info()["recomputed_stages"] == [0, 0]
