@@ -93,10 +93,12 @@ enum polar_flags {
  *   crc_len      0 (no CRC: the best path wins) or 1..32.
  *   crc_poly     generator polynomial without the x^crc_len term.
  *   L            list size, a power of two, 1 <= L <= 128 (L = 1 is Fast-SSC
- *                decoding, Sec. V). L <= 32 runs the warp-per-frame kernels;
+ *                decoding, Sec. V, with a kernel of its own: one lane per
+ *                frame). 2 <= L <= 32 runs the warp-per-frame kernels;
  *                L = 64 and 128 (the paper's Fig. 3 uses L = 128) run one CTA
  *                of L threads per frame over the fully unrolled schedule, with
- *                every stage in global scratch. Wide codes decode through
+ *                its stages in global scratch (polar_code_set_smem_budget can
+ *                move the smallest on chip). Wide codes decode through
  *                polar_list_decode, polar_list_decode_host and
  *                polar_adaptive_decode; set_launch, the allocation-free entry,
  *                batch plans and servers return POLAR_EUNSUPPORTED for them.
@@ -188,13 +190,31 @@ POLAR_API int polar_code_op_count(const polar_code_t *code, uint64_t *ops_per_fr
  * at most 512; 0 = 128) sets how many frame groups share a CTA and run the
  * schedule in lockstep. Later decodes of that dtype keep this shape even for
  * small batches. A code with L = 1 normally runs a kernel of its own
- * (Fast-SSC decoding, one warp per frame with every stage in shared memory,
- * no scratch); after set_launch it runs the list kernels with this shape
- * instead, until polar_code_autotune hands it back. Errors: POLAR_EINVAL (bad
+ * (Fast-SSC decoding, one lane per frame, see polar_code_set_smem_budget);
+ * after set_launch it runs the list kernels with this shape instead, until
+ * polar_code_autotune or polar_code_set_smem_budget hands it back. Errors: POLAR_EINVAL (bad
  * arguments, or the shape cannot hold the code), POLAR_EUNSUPPORTED (a wide
  * code, L > 32), POLAR_ENOMEM / POLAR_ECUDA (uploading the flagged schedule). */
 POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t warps_per_frame,
                                     uint32_t smem_budget, uint32_t cta_threads);
+
+/* Shared memory for the codes whose kernels place their buffers by a budget
+ * (0 = the default; results do not depend on it):
+ *   - L = 1 (the Fast-SSC kernel: one lane per frame, 32 frames per warp,
+ *     alpha stages interleaved over the lanes): bytes per warp (default 0:
+ *     everything in global scratch, where the accesses are coalesced, the L1
+ *     cache holds the hot low stages, and more warps fit per SM). The beta
+ *     rows, if they fit, and then the lowest alpha stages that fit go to
+ *     shared memory, the rest to global scratch. Also hands an L = 1 code
+ *     back from the list kernels (after polar_code_set_launch).
+ *   - wide codes (L = 64, 128: one CTA per frame): bytes per CTA beyond its
+ *     tables (default 0: every buffer in global scratch, so that more CTAs
+ *     fit per SM), filled with the smallest buffers (low alpha stages, left
+ *     betas, the channel row); the others go to global scratch.
+ * More on chip fits fewer warps or CTAs per SM; polar_code_autotune times the
+ * budgets. Errors: POLAR_EINVAL (bad arguments), POLAR_EUNSUPPORTED (2 <= L
+ * <= 32: those codes take polar_code_set_launch). */
+POLAR_API int polar_code_set_smem_budget(polar_code_t *code, int llr_dtype, uint32_t bytes);
 
 /* Stage memory against recomputation (Sec. IV-E counts one alpha row per
  * path and stage). The top `depth` alpha stages (at most
@@ -247,8 +267,10 @@ POLAR_API int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t
  * and reports it (any out pointer may be NULL; *budget_out = 0 means no cap).
  * Blocks until the timing runs finish. Results of later decodes do not depend
  * on the shape (only speed does). A code with L = 1 gets its own kernel back
- * without timing anything (1 warp per frame, budget 0, 256-thread CTAs), as
- * does a wide code (its one shape). Errors: POLAR_EINVAL, POLAR_ENOMEM,
+ * and its shared-memory budget per warp timed (see polar_code_set_smem_budget;
+ * *warps_out = 1, *budget_out = that budget, *cta_out = the CTA's threads);
+ * a wide code gets its shared-memory budget per CTA timed (*warps_out = L/32,
+ * *budget_out = that budget, *cta_out = L). Errors: POLAR_EINVAL, POLAR_ENOMEM,
  * POLAR_ECUDA. */
 POLAR_API int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, uint32_t n_frames,
                                   polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out,

@@ -34,6 +34,11 @@
 
 using namespace polar;
 
+// Shared memory a wide-list CTA gives its smallest buffers by default: none.
+// Measured at (1024, k=828) L = 128, every byte moved on chip costs more in
+// CTAs per SM than it saves (0.34 M frames/s with none, 0.23 M with 48 KB).
+constexpr uint32_t kWideDefaultBudget = 0u;
+
 struct polar_code {
     uint32_t N, n, K, k, L, crc_len, flags;
     uint64_t crc_poly;
@@ -61,11 +66,14 @@ struct polar_code {
     // L = 64 / 128: the wide kernel over the fully unrolled schedule
     bool wide = false;
     uint32_t *d_xops = nullptr;
-    uint64_t wide_gbytes[2] = {0, 0};
+    uint32_t wide_budget[2] = {kWideDefaultBudget, kWideDefaultBudget};   // shared memory for its buffers
     // L = 1: the Fast-SSC kernel over sc1_op entries (used unless set_launch
     // fixed a shape of the list kernels)
     std::vector<uint32_t> sops;
     uint32_t *d_sops = nullptr;
+    // shared memory per warp (32 frames) the L = 1 kernel may use; the
+    // largest alpha stages above it go to global scratch
+    uint32_t sc1_budget[2] = {0, 0};
     // Top alpha stages that may be evaluated from the channel instead of
     // stored (every node there an inner node of the list schedule, at most
     // three stages, none below stage kSubLog + 2), and the number in use for
@@ -120,9 +128,9 @@ cudaError_t launch_batch_locked(int dtype, int warps, const BatchParams &b, int 
     std::lock_guard<std::mutex> lk(g_launch_mu);
     return launch_batch(dtype, warps, b, grid, smem, threads, st);
 }
-int occupancy_sc1_locked(int dtype, int n, bool root_leaf, int warps) {
+int occupancy_sc1_locked(int dtype, uint32_t warp_bytes, int warps) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
-    return occupancy_sc1(dtype, n, root_leaf, warps);
+    return occupancy_sc1(dtype, warp_bytes, warps);
 }
 cudaError_t launch_sc1_locked(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
@@ -499,20 +507,35 @@ int decode_shape(const polar_code *code, int dtype, const LaunchShape &sh, const
 }
 
 // ---- wide lists ---------------------------------------------------------------
-// Every stage of every path in the CTA's global scratch: alpha stages 0..n-1
-// (L rows of 2^j elements), left betas 0..n-1, the right/root beta, the channel.
-WideView &wide_view(const polar_code *c, int dtype, WideView &v) {
+// The CTA's buffers: alpha stages 0..n-1 (L rows of 2^j elements), left betas
+// 0..n-1, the right/root beta and the channel row. The smallest go to shared
+// memory until `budget` bytes are used (the small stages are the ones the many
+// small nodes of the tree touch), the rest to the CTA's global scratch.
+WideView &wide_view(const polar_code *c, int dtype, WideView &v, uint32_t budget) {
     std::memset(&v, 0, sizeof(v));
     const uint64_t es = dtype == POLAR_LLR_I8 ? 1 : 4;
-    uint64_t off = 0;
-    for (uint32_t j = 0; j < c->n; ++j) { v.galpha[j] = off; off = al256(off + (uint64_t)c->L * (1u << j) * es); }
-    for (uint32_t j = 0; j < c->n; ++j) {
-        v.gbl[j] = off;
-        off = al256(off + (uint64_t)c->L * 4u * (uint64_t)beta_words((int)j));
+    struct Buf { uint64_t *loc; uint64_t bytes; };
+    std::vector<Buf> bufs;
+    for (uint32_t j = 0; j < c->n; ++j) bufs.push_back({&v.galpha[j], (uint64_t)c->L * (1u << j) * es});
+    for (uint32_t j = 0; j < c->n; ++j) bufs.push_back({&v.gbl[j], (uint64_t)c->L * 4u * (uint64_t)beta_words((int)j)});
+    bufs.push_back({&v.gbr, (uint64_t)c->L * 4u * (uint64_t)beta_words((int)c->n)});
+    bufs.push_back({&v.gchan, (uint64_t)c->N * es});
+    std::stable_sort(bufs.begin(), bufs.end(), [](const Buf &a, const Buf &b) { return a.bytes < b.bytes; });
+    uint64_t goff = 0;
+    uint32_t soff = 0;
+    const uint32_t limit = std::min<uint32_t>(budget, kMaxSmemPerCta - wide_smem_bytes((int)c->L, (int)c->n));
+    for (const Buf &b : bufs) {
+        const uint32_t need = (uint32_t)((b.bytes + 15u) & ~uint64_t(15));
+        if (b.bytes <= limit && soff + need <= limit) {
+            *b.loc = kWideInSmem | soff;
+            soff += need;
+        } else {
+            *b.loc = goff;
+            goff = al256(goff + b.bytes);
+        }
     }
-    v.gbr = off; off = al256(off + (uint64_t)c->L * 4u * (uint64_t)beta_words((int)c->n));
-    v.gchan = off; off = al256(off + (uint64_t)c->N * es);
-    v.gbytes = off;
+    v.sbytes = soff;
+    v.gbytes = goff;
     v.xops = c->d_xops;
     v.syn = c->d_syn;
     v.info = c->d_info;
@@ -529,11 +552,12 @@ WideView &wide_view(const polar_code *c, int dtype, WideView &v) {
 }
 
 int decode_wide(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
-                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx, const uint32_t *frame_cnt) {
+                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx, const uint32_t *frame_cnt,
+                uint32_t budget = 0) {
     WideParams p;
     std::memset(&p, 0, sizeof(p));
-    wide_view(code, dtype, p.v);
-    const int occ = occupancy_wide(dtype, (int)code->L, (int)code->n);
+    wide_view(code, dtype, p.v, budget ? budget : code->wide_budget[dtype]);
+    const int occ = occupancy_wide(dtype, (int)code->L, wide_smem_bytes((int)code->L, (int)code->n) + p.v.sbytes);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
     if (grid > n_frames) grid = n_frames;
@@ -546,20 +570,36 @@ int decode_wide(const polar_code *code, int dtype, const void *llr, uint32_t n_f
     p.frame_idx = frame_idx;
     p.frame_cnt = frame_cnt;
     void *scratch = nullptr;
-    if (scratch_alloc(&scratch, (size_t)(grid * p.v.gbytes), st) != cudaSuccess) return POLAR_ENOMEM;
-    scratch_poison(scratch, (size_t)(grid * p.v.gbytes), dtype, st);
-    p.scratch = (uint8_t *)scratch;
+    if (p.v.gbytes > 0) {
+        if (scratch_alloc(&scratch, (size_t)(grid * p.v.gbytes), st) != cudaSuccess) return POLAR_ENOMEM;
+        scratch_poison(scratch, (size_t)(grid * p.v.gbytes), dtype, st);
+        p.scratch = (uint8_t *)scratch;
+    }
     cudaError_t e = launch_wide(dtype, p, (int)grid, st);
-    cudaFreeAsync(scratch, st);
+    if (scratch) cudaFreeAsync(scratch, st);
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 // ---- L = 1 ----------------------------------------------------------------------
 bool use_sc1(const polar_code *c, int dtype) { return c->L == 1 && c->d_sops && !c->explicit_shape[dtype]; }
 
-// Needs no scratch: every stage of a frame sits in its warp's shared memory.
-int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
-               uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx, const uint32_t *frame_cnt) {
+// The L = 1 kernel: 32 frames per warp, one lane each; warps per CTA as many
+// as the shared memory takes (at most kSc1Threads / 32).
+struct Sc1Shape : Sc1Layout {
+    int warps;
+};
+
+Sc1Shape sc1_shape(const polar_code *code, int dtype, uint32_t budget) {
+    Sc1Shape sh;
+    const int es = dtype == POLAR_LLR_I8 ? 1 : 4;
+    sc1_layout((int)code->n, es, std::min(budget, kMaxSmemPerCta), &sh);
+    sh.warps = sh.warp_bytes == 0 ? kSc1Threads / 32
+                                  : std::max(1, std::min<int>(kSc1Threads / 32, (int)(kMaxSmemPerCta / sh.warp_bytes)));
+    return sh;
+}
+
+Sc1Params sc1_params(const polar_code *code, const Sc1Shape &sh, const void *llr, uint32_t n_frames, uint8_t *bits,
+                     float *pm, uint8_t *ok, int32_t *slot, const uint32_t *frame_idx, const uint32_t *frame_cnt) {
     Sc1Params p;
     std::memset(&p, 0, sizeof(p));
     p.ops = code->d_sops;
@@ -571,8 +611,11 @@ int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
     p.kb = (int)((code->k + 7) / 8);
     p.crc_len = (int)code->crc_len;
     p.systematic = (code->flags & POLAR_SYSTEMATIC) ? 1 : 0;
-    p.root_leaf = code->sops.size() == 1 ? 1 : 0;
-    p.warp_bytes = sc1_warp_bytes((int)code->n, dtype == POLAR_LLR_I8 ? 1 : 4, p.root_leaf != 0, &p.beta_off);
+    p.split = sh.split;
+    p.beta_smem = sh.beta_smem;
+    p.warp_bytes = sh.warp_bytes;
+    p.beta_off = sh.beta_off;
+    p.warp_gbytes = sh.warp_gbytes;
     p.llr = llr;
     p.bits = bits;
     p.pm = pm;
@@ -581,13 +624,38 @@ int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
     p.n_frames = n_frames;
     p.frame_idx = frame_idx;
     p.frame_cnt = frame_cnt;
-    const int warps = std::min<int>(kSc1Threads / 32, (int)(kMaxSmemPerCta / (uint32_t)p.warp_bytes));
-    const int occ = occupancy_sc1_locked(dtype, (int)code->n, p.root_leaf != 0, warps);
+    return p;
+}
+
+// Grid of the L = 1 kernel: resident CTAs, no more than the frames need.
+int sc1_grid(const polar_code *code, int dtype, const Sc1Shape &sh, uint32_t n_frames, uint64_t *grid) {
+    const int occ = occupancy_sc1_locked(dtype, sh.warp_bytes, sh.warps);
     if (occ <= 0) return POLAR_ECUDA;
-    uint64_t grid = (uint64_t)occ * (uint64_t)code->sm_count;
-    const uint64_t need = ((uint64_t)n_frames + warps - 1) / warps;
-    if (grid > need) grid = need;
-    return launch_sc1_locked(dtype, p, (int)grid, warps, st) == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+    uint64_t g = (uint64_t)occ * (uint64_t)code->sm_count;
+    const uint64_t need = ((uint64_t)n_frames + 32u * sh.warps - 1) / (32u * sh.warps);
+    if (g > need) g = need;
+    *grid = std::max<uint64_t>(g, 1);
+    return POLAR_OK;
+}
+
+int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
+               uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx, const uint32_t *frame_cnt,
+               uint32_t budget = 0) {
+    const Sc1Shape sh = sc1_shape(code, dtype, budget ? budget : code->sc1_budget[dtype]);
+    Sc1Params p = sc1_params(code, sh, llr, n_frames, bits, pm, ok, slot, frame_idx, frame_cnt);
+    uint64_t grid = 0;
+    const int rc = sc1_grid(code, dtype, sh, n_frames, &grid);
+    if (rc != POLAR_OK) return rc;
+    void *scratch = nullptr;
+    if (sh.warp_gbytes > 0) {
+        const size_t bytes = (size_t)grid * sh.warps * sh.warp_gbytes;
+        if (scratch_alloc(&scratch, bytes, st) != cudaSuccess) return POLAR_ENOMEM;
+        scratch_poison(scratch, bytes, dtype, st);
+        p.scratch = (uint8_t *)scratch;
+    }
+    const cudaError_t e = launch_sc1_locked(dtype, p, (int)grid, sh.warps, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
 // The installed shape of the narrow kernels, the L = 1 kernel or the wide kernel.
@@ -736,10 +804,6 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     }
     if (L > (uint32_t)kMaxL) {
         c->wide = true;
-        for (int d = 0; d < 2; ++d) {
-            WideView v;
-            c->wide_gbytes[d] = wide_view(c, d, v).gbytes;
-        }
         *out = c;
         return POLAR_OK;
     }
@@ -907,17 +971,104 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
                         polar_stream_t stream, uint32_t *warps_out, uint32_t *budget_out, uint32_t *cta_out) {
     if (!code || code->host_only || !llr_dev || n_frames == 0) return POLAR_EINVAL;
     if (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8) return POLAR_EINVAL;
-    if (code->wide) {   // one shape only: a CTA of L threads per frame
+    if (code->wide) {
+        // a CTA of L threads per frame: time how much shared memory its
+        // smallest buffers get (more on chip against fewer CTAs per SM)
+        static const uint32_t wide_budgets[] = {1u, 8000u, 16000u, 24000u, 36000u, 48000u, 64000u, 96000u,
+                                                140000u, kMaxSmemPerCta};
+        cudaStream_t stw = reinterpret_cast<cudaStream_t>(stream);
+        const size_t kbw = (code->k + 7) / 8;
+        uint8_t *bw = nullptr;
+        float *pmw = nullptr;
+        if (cudaMalloc(&bw, std::max<size_t>(kbw, 1) * n_frames) != cudaSuccess) return POLAR_ENOMEM;
+        if (cudaMalloc(&pmw, sizeof(float) * n_frames) != cudaSuccess) {
+            cudaFree(bw);
+            return POLAR_ENOMEM;
+        }
+        cudaEvent_t aw, zw;
+        cudaEventCreate(&aw);
+        cudaEventCreate(&zw);
+        float bestw = 1e30f;
+        uint32_t bestb = code->wide_budget[llr_dtype];
+        uint32_t last_sbytes = 0xffffffffu;
+        int statusw = POLAR_OK;
+        for (uint32_t b : wide_budgets) {
+            WideView wv;
+            wide_view(code, llr_dtype, wv, b);
+            if (wv.sbytes == last_sbytes) continue;               // the same placement as the last budget
+            last_sbytes = wv.sbytes;
+            int rc = decode_wide(code, llr_dtype, llr_dev, n_frames, bw, pmw, nullptr, nullptr, stw, nullptr, nullptr, b);
+            float ms = 0.f;
+            if (rc == POLAR_OK) {
+                cudaEventRecord(aw, stw);
+                rc = decode_wide(code, llr_dtype, llr_dev, n_frames, bw, pmw, nullptr, nullptr, stw, nullptr, nullptr, b);
+                cudaEventRecord(zw, stw);
+                if (cudaEventSynchronize(zw) != cudaSuccess) { statusw = POLAR_ECUDA; break; }
+                cudaEventElapsedTime(&ms, aw, zw);
+            }
+            if (rc == POLAR_ENOMEM) { statusw = rc; break; }
+            if (rc == POLAR_OK && ms < bestw) { bestw = ms; bestb = b; }
+        }
+        cudaEventDestroy(aw);
+        cudaEventDestroy(zw);
+        cudaFree(bw);
+        cudaFree(pmw);
+        if (statusw != POLAR_OK) return statusw;
+        code->wide_budget[llr_dtype] = bestb;
         if (warps_out) *warps_out = code->L / 32;
-        if (budget_out) *budget_out = 0;
+        if (budget_out) *budget_out = bestb;
         if (cta_out) *cta_out = code->L;
         return POLAR_OK;
     }
-    if (code->L == 1 && code->d_sops) {   // the L = 1 kernel: one warp per frame, no budget
+    if (code->L == 1 && code->d_sops) {
+        // the L = 1 kernel: time the shared-memory budgets per warp (how many
+        // alpha stages stay on chip against how many warps fit) and keep the fastest
+        static const uint32_t sc1_budgets[] = {0u, 9000u, 17000u, 25000u, 33000u, 46000u, 57000u, 76000u,
+                                               112000u, kMaxSmemPerCta};
+        cudaStream_t st1 = reinterpret_cast<cudaStream_t>(stream);
+        const size_t kb1 = (code->k + 7) / 8;
+        uint8_t *b1 = nullptr;
+        float *pm1 = nullptr;
+        if (cudaMalloc(&b1, std::max<size_t>(kb1, 1) * n_frames) != cudaSuccess) return POLAR_ENOMEM;
+        if (cudaMalloc(&pm1, sizeof(float) * n_frames) != cudaSuccess) {
+            cudaFree(b1);
+            return POLAR_ENOMEM;
+        }
+        cudaEvent_t a1, z1;
+        cudaEventCreate(&a1);
+        cudaEventCreate(&z1);
+        float best1 = 1e30f;
+        uint32_t bestb = 0;
+        int seen_split = -2;
+        int status1 = POLAR_OK;
+        for (uint32_t b : sc1_budgets) {
+            const Sc1Shape shp = sc1_shape(code, llr_dtype, b);
+            const int key = shp.beta_smem ? shp.split : -1;
+            if (key == seen_split) continue;                // the same layout as the last budget
+            seen_split = key;
+            int rc = decode_sc1(code, llr_dtype, llr_dev, n_frames, b1, pm1, nullptr, nullptr, st1, nullptr, nullptr, b);
+            float ms = 0.f;
+            if (rc == POLAR_OK) {
+                cudaEventRecord(a1, st1);
+                rc = decode_sc1(code, llr_dtype, llr_dev, n_frames, b1, pm1, nullptr, nullptr, st1, nullptr, nullptr, b);
+                cudaEventRecord(z1, st1);
+                if (cudaEventSynchronize(z1) != cudaSuccess) { status1 = POLAR_ECUDA; break; }
+                cudaEventElapsedTime(&ms, a1, z1);
+            }
+            if (rc == POLAR_ENOMEM) { status1 = rc; break; }
+            if (rc == POLAR_OK && ms < best1) { best1 = ms; bestb = b; }
+        }
+        cudaEventDestroy(a1);
+        cudaEventDestroy(z1);
+        cudaFree(b1);
+        cudaFree(pm1);
+        if (status1 != POLAR_OK) return status1;
+        code->sc1_budget[llr_dtype] = bestb;
         code->explicit_shape[llr_dtype] = false;
+        const Sc1Shape fin = sc1_shape(code, llr_dtype, bestb);
         if (warps_out) *warps_out = 1;
-        if (budget_out) *budget_out = 0;
-        if (cta_out) *cta_out = kSc1Threads;
+        if (budget_out) *budget_out = bestb;
+        if (cta_out) *cta_out = 32u * (uint32_t)fin.warps;
         return POLAR_OK;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1001,9 +1152,29 @@ int polar_list_decode_noalloc(const polar_code_t *code, const void *llr_dev, int
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return POLAR_ECUDA;
     if (dev != code->device) return POLAR_EINVAL;
-    if (use_sc1(code, llr_dtype))
-        return decode_sc1(code, llr_dtype, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev,
-                          winner_slot_dev, reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr);
+    if (use_sc1(code, llr_dtype)) {
+        // the L = 1 kernel: its spilled stages go to the fixed array too, the
+        // persistent grid cut to what the array holds
+        const Sc1Shape s1 = sc1_shape(code, llr_dtype, code->sc1_budget[llr_dtype]);
+        Sc1Params p1 = sc1_params(code, s1, llr_dev, n_frames, info_bits_dev, path_metric_dev, crc_ok_dev,
+                                  winner_slot_dev, nullptr, nullptr);
+        uint64_t g1 = 0;
+        const int rc1 = sc1_grid(code, llr_dtype, s1, n_frames, &g1);
+        if (rc1 != POLAR_OK) return rc1;
+        const uint64_t per_cta1 = (uint64_t)s1.warps * s1.warp_gbytes;
+        if (per_cta1 > 0) {
+            if (per_cta1 > kNoAllocScratchBytes) return POLAR_EUNSUPPORTED;
+            g1 = std::min<uint64_t>(g1, kNoAllocScratchBytes / per_cta1);
+            uint8_t *scr = nullptr;
+            const int st1 = noalloc_scratch(dev, &scr);
+            if (st1 != POLAR_OK) return st1;
+            scratch_poison(scr, (size_t)(g1 * per_cta1), llr_dtype, reinterpret_cast<cudaStream_t>(stream));
+            p1.scratch = scr;
+        }
+        const cudaError_t e1 = launch_sc1_locked(llr_dtype, p1, (int)g1, s1.warps,
+                                                 reinterpret_cast<cudaStream_t>(stream));
+        return e1 == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
+    }
     const LaunchShape &sh = code->shape[llr_dtype];
     const int occ = occupancy_locked(llr_dtype, sh);
     if (occ <= 0) return POLAR_ECUDA;
@@ -1358,17 +1529,25 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
         if (c->wide) {
             info->warps_per_frame[d] = c->L / 32;
             info->frames_per_cta[d] = 1;
-            info->smem_per_frame[d] = wide_smem_bytes((int)c->L, (int)c->n);
-            info->scratch_per_frame[d] = c->wide_gbytes[d];
-            info->spill_mask[d] = (1u << c->n) - 1u;
+            WideView wv;
+            wide_view(c, d, wv, c->wide_budget[d]);
+            info->smem_per_frame[d] = wide_smem_bytes((int)c->L, (int)c->n) + wv.sbytes;
+            info->scratch_per_frame[d] = wv.gbytes;
+            uint32_t sm = 0;
+            for (uint32_t j = 0; j < c->n; ++j)
+                if (!(wv.galpha[j] & kWideInSmem)) sm |= 1u << j;
+            info->spill_mask[d] = sm;
             continue;
         }
         if (c->L == 1 && !c->explicit_shape[d]) {
-            const uint32_t wb =
-                (uint32_t)sc1_warp_bytes((int)c->n, d == POLAR_LLR_I8 ? 1 : 4, c->sops.size() == 1, nullptr);
+            // one lane per frame: a warp decodes 32 frames
+            const Sc1Shape s1 = sc1_shape(c, d, c->sc1_budget[d]);
             info->warps_per_frame[d] = 1;
-            info->frames_per_cta[d] = std::min<uint32_t>((uint32_t)kSc1Threads / 32, kMaxSmemPerCta / wb);
-            info->smem_per_frame[d] = wb;
+            info->frames_per_cta[d] = 32u * (uint32_t)s1.warps;
+            info->smem_per_frame[d] = s1.warp_bytes / 32u;
+            info->scratch_per_frame[d] = s1.warp_gbytes / 32u;
+            info->spill_mask[d] = ((1u << c->n) - 1u) & ~((1u << s1.split) - 1u);
+            info->smem_per_frame[d] = s1.warp_bytes / 32u;
             continue;
         }
         info->warps_per_frame[d] = (uint32_t)c->shape[d].warps;
@@ -1417,6 +1596,18 @@ int polar_code_op_count(const polar_code_t *c, uint64_t *ops_per_frame) {
     }
     tot += (uint64_t)c->L * c->N * c->n / 32 + (uint64_t)c->L * c->K;
     *ops_per_frame = tot;
+    return POLAR_OK;
+}
+
+int polar_code_set_smem_budget(polar_code_t *c, int llr_dtype, uint32_t bytes) {
+    if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
+    if (c->wide) {
+        c->wide_budget[llr_dtype] = bytes ? bytes : kWideDefaultBudget;
+        return POLAR_OK;
+    }
+    if (c->L != 1) return POLAR_EUNSUPPORTED;
+    c->sc1_budget[llr_dtype] = bytes;
+    c->explicit_shape[llr_dtype] = false;
     return POLAR_OK;
 }
 

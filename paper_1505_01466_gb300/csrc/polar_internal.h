@@ -176,11 +176,15 @@ struct WideView {
     const uint16_t *info;          // [K] information positions
     int n_xops;
     int N, n, L, K, k, kb, crc_len, systematic;
+    // Buffer locations: a global scratch offset, or, with kWideInSmem set, an
+    // offset into the CTA's shared memory after its tables.
     uint64_t galpha[kMaxLogN];     // stage j: L rows of 2^j elements
     uint64_t gbl[kMaxLogN];        // left beta of stage j: L rows of beta_words(j) words
     uint64_t gbr, gchan;           // right/root beta, channel row
     uint64_t gbytes;               // global scratch per CTA
+    uint32_t sbytes;               // shared memory of the buffers kept on chip
 };
+constexpr uint64_t kWideInSmem = 1ull << 63;
 
 struct WideParams {
     WideView v;
@@ -195,12 +199,12 @@ struct WideParams {
     const uint32_t *frame_cnt;
 };
 
-uint32_t wide_smem_bytes(int L, int n);
-int occupancy_wide(int dtype, int L, int n);
+uint32_t wide_smem_bytes(int L, int n);   // the CTA's tables; the launch adds WideView::sbytes
+int occupancy_wide(int dtype, int L, uint32_t smem);
 cudaError_t launch_wide(int dtype, const WideParams &p, int grid, cudaStream_t stream);
 
-// ---- L = 1 (Fast-SSC): one warp per frame, lanes over the elements of a node ----
-constexpr int kSc1Threads = 256;   // CTA size, unless 8 warps' shared memory does not fit
+// ---- L = 1 (Fast-SSC): one lane per frame, 32 frames per warp in lockstep ----
+constexpr int kSc1Threads = 256;   // CTA size, unless fewer warps' shared memory fits
 
 // Schedule entry of the L = 1 kernel: kind | stage j << 4 | first bit s << 8.
 __host__ __device__ inline uint32_t sc1_op(uint32_t kind, uint32_t j, uint32_t s) {
@@ -213,8 +217,11 @@ struct Sc1Params {
     const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
     const uint16_t *info;          // [K] information positions, ascending
     int n, k, kb, crc_len, systematic;
-    int root_leaf;                 // the root is a leaf: its input (the channel) is copied to stage n
-    int warp_bytes, beta_off;      // shared memory of one warp; offset of its beta row
+    int split;                     // alpha stages below it in shared memory, the rest in global scratch
+    int beta_smem;                 // beta rows in shared memory (else in global scratch)
+    uint32_t warp_bytes, beta_off; // shared memory of one warp (32 frames); offset of its beta rows
+    uint64_t warp_gbytes;          // global scratch of one warp
+    uint8_t *scratch;              // warp_gbytes per warp of the grid (when split < n)
     const void *llr;               // [n_frames][N]
     uint8_t *bits;                 // [n_frames][kb]
     float *pm;
@@ -225,8 +232,14 @@ struct Sc1Params {
     const uint32_t *frame_cnt;
 };
 
-int sc1_warp_bytes(int n, int es, bool root_leaf, int *beta_off);
-int occupancy_sc1(int dtype, int n, bool root_leaf, int warps);
+// Per-warp shared memory and global scratch of the L = 1 kernel for a budget.
+struct Sc1Layout {
+    int split, beta_smem;
+    uint32_t warp_bytes, beta_off;
+    uint64_t warp_gbytes;
+};
+void sc1_layout(int n, int es, uint32_t budget, Sc1Layout *lay);
+int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps);
 cudaError_t launch_sc1(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t stream);
 
 }  // namespace polar

@@ -12,25 +12,34 @@
 //    (smallest |alpha|, then lowest index) is flipped and penalty += its
 //    |alpha|                                                    (Sec. III-D)
 //
-// One warp decodes one frame, and the warps of a CTA take frames in turn
-// (persistent). The lanes run over the elements of a node.
-//  * Alpha stages 6..n-1 sit in the warp's shared memory (stage j at element
-//    offset 2^j); the channel row is read from global memory by the two
-//    operations at the root (a code whose root is itself a leaf copies it to
-//    shared memory first).
-//  * Every node of at most 32 bits runs in registers: stage 5 in one register
-//    (element e in lane e), stages 0..4 together in another (stage j in lanes
-//    2^j .. 2^(j+1)-1), F and G by two warp shuffles each, and the node's 32
-//    beta bits in one word.
-//  * Beta is one bit-packed row of N bits in shared memory: a leaf writes its
-//    bits at its own position and Combine (Eq. (3)) xors the right half into
-//    the left in place, so at the end the row holds the codeword x.
+// One lane decodes one frame: a warp takes 32 frames and walks the unrolled
+// schedule (Listing 2) once for all of them, every lane doing its own frame's
+// work for each operation. There is no data-dependent control flow at L = 1,
+// so the lanes never diverge, and the cost of interpreting an operation is
+// shared by 32 frames. Storage is interleaved by lane:
+//  * alpha stage j holds 2^j values per frame; value e of lane l sits in
+//    32-bit word e * 32 + l of the stage (float32), or, for int8, four values
+//    per word (value e in byte e & 3 of word (e >> 2) * 32 + l), so F and G
+//    run four lanes of SIMD at a time. Every access of a warp touches 32
+//    consecutive words: no bank conflicts in shared memory, one 128-byte line
+//    in global memory.
+//  * the stages go to the warp's shared memory up to a budget, the largest
+//    ones to a per-warp region of global scratch (by default all of them:
+//    the accesses are coalesced and the L1 cache keeps the hot low stages,
+//    and without shared memory more warps fit per SM);
+//  * beta is one bit-packed row of N bits per frame (word w of lane l at
+//    w * 32 + l), in shared memory if the budget holds it: a leaf writes its bits at its position and
+//    Combine (Eq. (3)) xors the right half into the left in place, so at the
+//    end the row holds the codeword x;
+//  * the channel row (stage n) is read from the caller's buffer.
 //
-// Float sums follow the pairwise tree s[i] = x[i] + x[i + n/2]; int8 LLRs use
-// saturated G and exact integer penalties. These are the conventions of the
-// list kernels, so the results equal theirs at L = 1.
+// Float sums follow the pairwise tree s[i] = x[i] + x[i + n/2] (computed in
+// the dead stage below the leaf); int8 LLRs use saturated G and exact
+// integer penalties. These are the conventions of the list kernels, so the
+// results equal theirs at L = 1.
 
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/polar.h"
 #include "polar_internal.h"
@@ -38,52 +47,12 @@
 namespace polar {
 namespace {
 
-constexpr uint32_t FULL = 0xffffffffu;
-
-template <typename T> struct A1;
-
-template <> struct A1<float> {
-    typedef float V;
-    static __device__ __forceinline__ float ld(const float *p) { return *p; }
-    static __device__ __forceinline__ float ldch(const float *p) { return __ldg(p); }
-    // Eq. (1), min-sum, sign by comparison
-    static __device__ __forceinline__ float f(float a, float b) {
-        const float m = fminf(fabsf(a), fabsf(b));
-        return ((a < 0.f) != (b < 0.f)) ? -m : m;
-    }
-    // Eq. (2)
-    static __device__ __forceinline__ float g(float a, float b, uint32_t beta) { return beta ? b - a : b + a; }
-    static __device__ __forceinline__ float st(float v) { return v; }
-    static __device__ __forceinline__ uint32_t absbits(float a) { return __float_as_uint(fabsf(a)); }
-    static __device__ __forceinline__ float absv(float a) { return fabsf(a); }
-    static __device__ __forceinline__ float unabs(uint32_t b) { return __uint_as_float(b); }
-    static __device__ __forceinline__ float negpart(float a) { return a < 0.f ? -a : 0.f; }
-    static __device__ __forceinline__ float pospart(float a) { return a > 0.f ? a : 0.f; }
-};
-
-template <> struct A1<int8_t> {
-    typedef int V;
-    static __device__ __forceinline__ int ld(const int8_t *p) { return *p; }
-    // -128 is read as -127
-    static __device__ __forceinline__ int ldch(const int8_t *p) {
-        const int v = __ldg(reinterpret_cast<const signed char *>(p));
-        return v < -127 ? -127 : v;
-    }
-    static __device__ __forceinline__ int f(int a, int b) {
-        const int m = min(abs(a), abs(b));
-        return ((a < 0) != (b < 0)) ? -m : m;
-    }
-    static __device__ __forceinline__ int g(int a, int b, uint32_t beta) {
-        const int r = beta ? b - a : b + a;
-        return max(-127, min(127, r));
-    }
-    static __device__ __forceinline__ int8_t st(int v) { return (int8_t)v; }
-    static __device__ __forceinline__ uint32_t absbits(int a) { return (uint32_t)abs(a); }
-    static __device__ __forceinline__ int absv(int a) { return abs(a); }
-    static __device__ __forceinline__ int unabs(uint32_t b) { return (int)b; }
-    static __device__ __forceinline__ int negpart(int a) { return a < 0 ? -a : 0; }
-    static __device__ __forceinline__ int pospart(int a) { return a > 0 ? a : 0; }
-};
+// Eq. (1), min-sum, and Eq. (2) on float32
+__device__ __forceinline__ float f1(float a, float b) {
+    const float m = fminf(fabsf(a), fabsf(b));
+    return ((a < 0.f) != (b < 0.f)) ? -m : m;
+}
+__device__ __forceinline__ float g1(float a, float b, uint32_t beta) { return beta ? b - a : b + a; }
 
 // Four int8 LLRs in one word: F = max(min(a, b), -max(a, b)); G with the four
 // beta bits in nib (bit e -> byte e), saturated to [-127, 127].
@@ -95,349 +64,393 @@ __device__ __forceinline__ uint32_t g4(uint32_t a, uint32_t b, uint32_t nib) {
     const uint32_t sa = (a & ~m) | (__vneg4(a) & m);
     return __vmaxs4(__vaddss4(b, sa), 0x81818181u);
 }
+__device__ __forceinline__ int byte_of(uint32_t w, int e) { return (int)(int8_t)((w >> (8 * (e & 3))) & 0xFFu); }
 
-__device__ __forceinline__ uint32_t beta_bit(const uint32_t *bw, int pos) {
-    return (bw[pos >> 5] >> (pos & 31)) & 1u;
+// Words of stages 0 .. j-1 a lane holds: stage j has 2^j values, one per
+// word (float32) or four per word (int8, at least one word).
+__host__ __device__ __forceinline__ int words_below(int j, int es) {
+    if (es == 4) return (1 << j) - 1;
+    return j <= 2 ? j : (1 << (j - 2)) + 1;
 }
 
-// Write the bits of a node of nv bits at position s; lane l holds element
-// l + 32 c of chunk c in its predicate.
-__device__ __forceinline__ void put_chunk(uint32_t *bw, int s, int nv, int c, bool bit, int lane) {
-    const uint32_t b = __ballot_sync(FULL, bit);
-    if (lane == 0) {
-        if (nv >= 32) {
-            bw[(s >> 5) + c] = b;
+// Per-lane view of one warp's storage: stages below `split` in the warp's
+// shared memory, the others in its global scratch, both interleaved by lane.
+struct Lane {
+    uint8_t *smem, *gmem;          // the warp's regions, offset to this lane (4 * lane)
+    uint32_t *beta;                // beta row, offset to this lane (word w at beta[w * 32])
+    int n, N, split, es;
+    __device__ __forceinline__ uint8_t *stage(int j) const {
+        return j < split ? smem + (size_t)words_below(j, es) * 128
+                         : gmem + (size_t)(words_below(j, es) - words_below(split, es)) * 128;
+    }
+};
+
+// The frame's channel row (stage n) and its alignment.
+struct Chan {
+    const uint8_t *row;
+    bool vec;                      // 16-byte aligned rows: vector loads
+};
+
+// ---- float32 element access ----
+__device__ __forceinline__ float ldf(const Lane &ln, const Chan &ch, int j, int e) {
+    if (j == ln.n) return __ldg(reinterpret_cast<const float *>(ch.row) + e);
+    return reinterpret_cast<const float *>(ln.stage(j))[e * 32];
+}
+__device__ __forceinline__ float4 ldf4(const Lane &ln, const Chan &ch, int j, int e) {   // values e .. e+3
+    if (j == ln.n && ch.vec) return __ldg(reinterpret_cast<const float4 *>(ch.row + 4 * e));
+    float4 r;
+    r.x = ldf(ln, ch, j, e);
+    r.y = ldf(ln, ch, j, e + 1);
+    r.z = ldf(ln, ch, j, e + 2);
+    r.w = ldf(ln, ch, j, e + 3);
+    return r;
+}
+
+// ---- int8 word access: word w = values 4w .. 4w+3 (a stage of fewer than
+// four values uses the low bytes of word 0); the channel reads -128 as -127 ----
+__device__ __forceinline__ uint32_t ldw(const Lane &ln, const Chan &ch, int j, int w) {
+    if (j == ln.n) {
+        uint32_t v;
+        if (ch.vec) {
+            v = __ldg(reinterpret_cast<const uint32_t *>(ch.row) + w);
         } else {
-            const uint32_t m = ((1u << nv) - 1u) << (s & 31);
-            uint32_t &w = bw[s >> 5];
-            w = (w & ~m) | ((b << (s & 31)) & m);
+            const uint8_t *p = ch.row + 4 * w;
+            v = (uint32_t)__ldg(p) | ((uint32_t)__ldg(p + 1) << 8) | ((uint32_t)__ldg(p + 2) << 16) |
+                ((uint32_t)__ldg(p + 3) << 24);
         }
+        return __vmaxs4(v, 0x81818181u);
     }
+    return reinterpret_cast<const uint32_t *>(ln.stage(j))[w * 32];
 }
 
-// Pairwise tree sum of |min(a,0)| (neg) or max(a,0) (!neg) over a[0..nv),
-// returned to every lane. Sums of more than 32 terms use scr (nv/2 floats).
-__device__ float tree_sum(const float *a, int nv, bool neg, float *scr, int lane) {
-    auto t = [neg](float x) { return neg ? (x < 0.f ? -x : 0.f) : (x > 0.f ? x : 0.f); };
-    float v;
-    if (nv > 32) {
-        const int h = nv >> 1;
-        for (int i = lane; i < h; i += 32) scr[i] = t(a[i]) + t(a[i + h]);
-        __syncwarp();
-        for (int m = h; m > 32; m >>= 1) {
-            const int hh = m >> 1;
-            for (int i = lane; i < hh; i += 32) scr[i] = scr[i] + scr[i + hh];
-            __syncwarp();
-        }
-        v = scr[lane];
-        __syncwarp();
-        nv = 32;
+__device__ __forceinline__ uint32_t beta_bits(const Lane &ln, int pos) {   // bits pos .. pos+31 (pos % 32 + span <= 32)
+    return ln.beta[(pos >> 5) * 32] >> (pos & 31);
+}
+// Write nb (< 32) bits at position s (within one word) or whole words.
+__device__ __forceinline__ void put_bits(const Lane &ln, int s, int nb, uint32_t bits) {
+    if (nb >= 32) {
+        ln.beta[(s >> 5) * 32] = bits;
     } else {
-        v = lane < nv ? t(a[lane]) : 0.f;
+        const uint32_t m = ((1u << nb) - 1u) << (s & 31);
+        uint32_t &w = ln.beta[(s >> 5) * 32];
+        w = (w & ~m) | ((bits << (s & 31)) & m);
     }
-    for (int h = nv >> 1; h >= 1; h >>= 1) v = v + __shfl_down_sync(FULL, v, h);
-    return __shfl_sync(FULL, v, 0);
 }
 
-// Integer sums are exact in any order.
-__device__ int tree_sum(const int8_t *a, int nv, bool neg, int8_t *, int lane) {
-    int v = 0;
-    for (int i = lane; i < nv; i += 32) {
-        const int x = a[i];
-        v += neg ? (x < 0 ? -x : 0) : (x > 0 ? x : 0);
-    }
-    return __reduce_add_sync(FULL, v);
-}
-
-template <typename T>
-__device__ __forceinline__ T *stage(T *alpha, int j) { return alpha + (1 << j); }
-
-// F or G of a node of stage j starting at bit s: stage j (or the channel
-// row when j = n) -> stage j - 1.
-template <typename T, bool IS_G>
-__device__ __forceinline__ void fg(const Sc1Params &p, T *alpha, const uint32_t *bw, const T *ch, bool vec_ch,
-                                   int j, int s, int lane) {
-    typedef A1<T> A;
+// ---- F / G (Eq. (1), (2)) of a node of stage j starting at bit s ----------
+template <bool IS_G>
+__device__ __forceinline__ void fg_f32(const Lane &ln, const Chan &ch, int j, int s) {
     const int h = 1 << (j - 1);
-    const bool root = j == p.n;
-    const T *in = root ? ch : stage(alpha, j);
-    T *out = stage(alpha, j - 1);
-    if (sizeof(T) == 1 && h >= 128 && (!root || vec_ch)) {
-        const uint32_t *in4 = reinterpret_cast<const uint32_t *>(in);
-        uint32_t *out4 = reinterpret_cast<uint32_t *>(out);
-        const int h4 = h >> 2;
-        for (int w = lane; w < h4; w += 32) {
-            uint32_t a = root ? __ldg(in4 + w) : in4[w];
-            uint32_t b = root ? __ldg(in4 + w + h4) : in4[w + h4];
-            if (root) { a = __vmaxs4(a, 0x81818181u); b = __vmaxs4(b, 0x81818181u); }
+    float *out = reinterpret_cast<float *>(ln.stage(j - 1));
+    if (h >= 4) {
+#pragma unroll 2
+        for (int e = 0; e < h; e += 4) {
+            const float4 a = ldf4(ln, ch, j, e), b = ldf4(ln, ch, j, e + h);
             if (IS_G) {
-                const int pos = s + 4 * w;
-                out4[w] = g4(a, b, (bw[pos >> 5] >> (pos & 31)) & 0xFu);
+                const uint32_t nib = beta_bits(ln, s + e);
+                out[e * 32] = g1(a.x, b.x, nib & 1u);
+                out[(e + 1) * 32] = g1(a.y, b.y, (nib >> 1) & 1u);
+                out[(e + 2) * 32] = g1(a.z, b.z, (nib >> 2) & 1u);
+                out[(e + 3) * 32] = g1(a.w, b.w, (nib >> 3) & 1u);
             } else {
-                out4[w] = f4(a, b);
+                out[e * 32] = f1(a.x, b.x);
+                out[(e + 1) * 32] = f1(a.y, b.y);
+                out[(e + 2) * 32] = f1(a.z, b.z);
+                out[(e + 3) * 32] = f1(a.w, b.w);
             }
         }
-        return;
-    }
-    if (sizeof(T) == 4 && h >= 128 && (!root || vec_ch)) {
-        const float4 *in4 = reinterpret_cast<const float4 *>(in);
-        float4 *out4 = reinterpret_cast<float4 *>(out);
-        const int h4 = h >> 2;
-        for (int w = lane; w < h4; w += 32) {
-            const float4 a = root ? __ldg(in4 + w) : in4[w];
-            const float4 b = root ? __ldg(in4 + w + h4) : in4[w + h4];
-            float4 r;
-            if (IS_G) {
-                const int pos = s + 4 * w;
-                const uint32_t nib = (bw[pos >> 5] >> (pos & 31)) & 0xFu;
-                r.x = A1<float>::g(a.x, b.x, nib & 1u);
-                r.y = A1<float>::g(a.y, b.y, (nib >> 1) & 1u);
-                r.z = A1<float>::g(a.z, b.z, (nib >> 2) & 1u);
-                r.w = A1<float>::g(a.w, b.w, (nib >> 3) & 1u);
-            } else {
-                r.x = A1<float>::f(a.x, b.x);
-                r.y = A1<float>::f(a.y, b.y);
-                r.z = A1<float>::f(a.z, b.z);
-                r.w = A1<float>::f(a.w, b.w);
-            }
-            out4[w] = r;
+    } else {
+        const uint32_t nib = IS_G ? beta_bits(ln, s) : 0u;
+        for (int e = 0; e < h; ++e) {
+            const float a = ldf(ln, ch, j, e), b = ldf(ln, ch, j, e + h);
+            out[e * 32] = IS_G ? g1(a, b, (nib >> e) & 1u) : f1(a, b);
         }
-        return;
-    }
-    for (int e = lane; e < h; e += 32) {
-        const typename A::V a = root ? A::ldch(in + e) : A::ld(in + e);
-        const typename A::V b = root ? A::ldch(in + e + h) : A::ld(in + e + h);
-        out[e] = A::st(IS_G ? A::g(a, b, beta_bit(bw, s + e)) : A::f(a, b));
     }
 }
 
-// Pairwise tree sum over lanes [base, base + nv) of t (zero elsewhere),
-// returned to every lane: lane base + e adds lane base + e + h, h = nv/2, ...
-template <typename V>
-__device__ __forceinline__ V wsum(V t, int nv, int base) {
-    for (int h = nv >> 1; h >= 1; h >>= 1) t = t + __shfl_down_sync(FULL, t, h);
-    return __shfl_sync(FULL, t, base);
+template <bool IS_G>
+__device__ __forceinline__ void fg_i8(const Lane &ln, const Chan &ch, int j, int s) {
+    const int h = 1 << (j - 1);
+    uint32_t *out = reinterpret_cast<uint32_t *>(ln.stage(j - 1));
+    if (h >= 4) {
+        const int hw = h >> 2;
+#pragma unroll 4
+        for (int w = 0; w < hw; ++w) {
+            const uint32_t a = ldw(ln, ch, j, w), b = ldw(ln, ch, j, w + hw);
+            out[w * 32] = IS_G ? g4(a, b, beta_bits(ln, s + 4 * w) & 15u) : f4(a, b);
+        }
+    } else {
+        // two values (j = 2) or one (j = 1) in the low bytes of one word
+        const uint32_t x = ldw(ln, ch, j, 0);
+        const uint32_t b = x >> (8 * h);
+        const uint32_t keep = h == 2 ? 0xFFFFu : 0xFFu;
+        out[0] = (IS_G ? g4(x, b, beta_bits(ln, s) & ((1u << h) - 1u)) : f4(x, b)) & keep;
+    }
 }
 
-// A leaf of 64 or more bits, read from its stage in shared memory (a: its
-// input, scr: the dead stage below it, scratch for float sums).
+// ---- Combine (Eq. (3)) in place on the beta row ----
+__device__ __forceinline__ void comb(const Lane &ln, int j, int s) {
+    const int h = 1 << (j - 1);
+    if (h >= 32) {
+        for (int w = 0; w < (h >> 5); ++w) ln.beta[((s >> 5) + w) * 32] ^= ln.beta[(((s + h) >> 5) + w) * 32];
+    } else {
+        uint32_t &W = ln.beta[(s >> 5) * 32];
+        W ^= (W >> h) & (((1u << h) - 1u) << (s & 31));
+    }
+}
+
+// ---- leaves ----------------------------------------------------------------
+// Pairwise tree sum of |min(a, 0)| (neg) or max(a, 0) (!neg) over the nv =
+// 2^j values of stage j, in the dead stage j - 1 (float32).
+__device__ float tsum_f32(const Lane &ln, const Chan &ch, int j, bool neg) {
+    auto t = [neg](float x) { return neg ? (x < 0.f ? -x : 0.f) : (x > 0.f ? x : 0.f); };
+    if (j == 0) return t(ldf(ln, ch, 0, 0));
+    const int h = 1 << (j - 1);
+    float *scr = reinterpret_cast<float *>(ln.stage(j - 1));
+    for (int i = 0; i < h; ++i) scr[i * 32] = t(ldf(ln, ch, j, i)) + t(ldf(ln, ch, j, i + h));
+    for (int m = h; m > 1; m >>= 1) {
+        const int hh = m >> 1;
+        for (int i = 0; i < hh; ++i) scr[i * 32] = scr[i * 32] + scr[(i + hh) * 32];
+    }
+    return scr[0];
+}
+
+// Integer sums are exact in any order (int8): sums of |min(a,0)| and max(a,0).
+__device__ void isums(const Lane &ln, const Chan &ch, int j, int &s0, int &s1) {
+    const int nv = 1 << j;
+    int a0 = 0, a1 = 0;
+    for (int w = 0; w < (nv + 3) / 4; ++w) {
+        const uint32_t x = ldw(ln, ch, j, w);
+        const int cnt = nv < 4 ? nv : 4;
+        for (int b = 0; b < cnt; ++b) {
+            const int v = byte_of(x, b);
+            a0 += v < 0 ? -v : 0;
+            a1 += v > 0 ? v : 0;
+        }
+    }
+    s0 = a0;
+    s1 = a1;
+}
+
+// Hard decisions of values c*32 .. c*32 + cnt - 1 of stage j as one word.
 template <typename T>
-__device__ void leaf_smem(int kind, const T *a, T *scr, uint32_t *bw, int nv, int s, typename A1<T>::V &pen,
-                          int lane) {
-    typedef A1<T> A;
-    typedef typename A::V V;
+__device__ __forceinline__ uint32_t hd_chunk(const Lane &ln, const Chan &ch, int j, int c, int cnt) {
+    uint32_t bits = 0;
+    if (sizeof(T) == 4) {
+        if (cnt >= 4) {
+            for (int e = 0; e < cnt; e += 4) {
+                const float4 v = ldf4(ln, ch, j, 32 * c + e);
+                bits |= ((uint32_t)(v.x < 0.f) | ((uint32_t)(v.y < 0.f) << 1) | ((uint32_t)(v.z < 0.f) << 2) |
+                         ((uint32_t)(v.w < 0.f) << 3)) << e;
+            }
+        } else {
+            for (int e = 0; e < cnt; ++e) bits |= (uint32_t)(ldf(ln, ch, j, 32 * c + e) < 0.f) << e;
+        }
+    } else {
+        for (int w = 0; w < (cnt + 3) / 4; ++w) {
+            const uint32_t t = (ldw(ln, ch, j, 8 * c + w) >> 7) & 0x01010101u;     // sign bit of each byte
+            bits |= (((t * 0x01020408u) >> 24) & 0xFu) << (4 * w);
+        }
+        if (cnt < 32) bits &= (1u << cnt) - 1u;
+    }
+    return bits;
+}
+
+// |value| and position of the least reliable value (smallest |a|, lowest index).
+template <typename T>
+__device__ __forceinline__ void lrb1(const Lane &ln, const Chan &ch, int j, uint32_t &best_abs, int &best_e) {
+    const int nv = 1 << j;
+    uint32_t ba = 0xffffffffu;
+    int be = 0;
+    if (sizeof(T) == 4) {
+        for (int e = 0; e < nv; e += 4) {
+            const float4 v = ldf4(ln, ch, j, e);
+            const uint32_t x0 = __float_as_uint(fabsf(v.x)), x1 = __float_as_uint(fabsf(v.y));
+            const uint32_t x2 = __float_as_uint(fabsf(v.z)), x3 = __float_as_uint(fabsf(v.w));
+            if (x0 < ba) { ba = x0; be = e; }
+            if (x1 < ba) { ba = x1; be = e + 1; }
+            if (x2 < ba) { ba = x2; be = e + 2; }
+            if (x3 < ba) { ba = x3; be = e + 3; }
+        }
+    } else {
+        for (int w = 0; w < nv / 4; ++w) {
+            const uint32_t x = ldw(ln, ch, j, w);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int v = byte_of(x, b);
+                const uint32_t a = (uint32_t)(v < 0 ? -v : v);
+                if (a < ba) { ba = a; be = 4 * w + b; }
+            }
+        }
+    }
+    best_abs = ba;
+    best_e = be;
+}
+
+template <typename T, typename PT>
+__device__ __forceinline__ void leaf(const Lane &ln, const Chan &ch, int kind, int j, int s, PT &pen) {
+    const int nv = 1 << j;
+    const int nch = nv >= 32 ? nv >> 5 : 1;
+    const int cnt = nv >= 32 ? 32 : nv;
     if (kind == OP_R0) {                                               // Eq. (10)
-        pen = pen + tree_sum(a, nv, true, scr, lane);
-        for (int c = 0; c < nv / 32; ++c) put_chunk(bw, s, nv, c, false, lane);
-    } else if (kind == OP_R1) {
-        for (int c = 0; c < nv / 32; ++c) put_chunk(bw, s, nv, c, A::ld(a + 32 * c + lane) < 0, lane);
+        if (sizeof(T) == 4) {
+            pen = pen + (PT)tsum_f32(ln, ch, j, true);
+        } else {
+            int s0, s1;
+            isums(ln, ch, j, s0, s1);
+            pen = pen + (PT)s0;
+        }
+        for (int c = 0; c < nch; ++c) put_bits(ln, s + 32 * c, cnt, 0u);
+    } else if (kind == OP_R1) {                                        // Sec. III-C
+        for (int c = 0; c < nch; ++c) put_bits(ln, s + 32 * c, cnt, hd_chunk<T>(ln, ch, j, c, cnt));
     } else if (kind == OP_REP) {                                       // Eq. (5), ties to all zero
-        const V p0 = tree_sum(a, nv, true, scr, lane);
-        const V p1 = tree_sum(a, nv, false, scr, lane);
-        const bool one = !(p0 <= p1);
-        pen = pen + (one ? p1 : p0);
-        for (int c = 0; c < nv / 32; ++c) put_chunk(bw, s, nv, c, one, lane);
+        bool one;
+        if (sizeof(T) == 4) {
+            const float p0 = tsum_f32(ln, ch, j, true);
+            const float p1 = tsum_f32(ln, ch, j, false);
+            one = !(p0 <= p1);
+            pen = pen + (PT)(one ? p1 : p0);
+        } else {
+            int s0, s1;
+            isums(ln, ch, j, s0, s1);
+            one = !(s0 <= s1);
+            pen = pen + (PT)(one ? s1 : s0);
+        }
+        for (int c = 0; c < nch; ++c) put_bits(ln, s + 32 * c, cnt, one ? 0xffffffffu : 0u);
     } else {                                                           // SPC, Sec. III-D
         uint32_t par = 0;
-        unsigned long long best = ~0ull;
-        for (int c = 0; c < nv / 32; ++c) {
-            const int e = 32 * c + lane;
-            const V x = A::ld(a + e);
-            const unsigned long long key = ((unsigned long long)A::absbits(x) << 32) | (uint32_t)e;
-            best = key < best ? key : best;
-            par ^= (uint32_t)__popc(__ballot_sync(FULL, x < 0)) & 1u;
-            put_chunk(bw, s, nv, c, x < 0, lane);
+        for (int c = 0; c < nch; ++c) {
+            const uint32_t b = hd_chunk<T>(ln, ch, j, c, cnt);
+            par ^= (uint32_t)__popc(b);
+            put_bits(ln, s + 32 * c, cnt, b);
         }
-        for (int off = 16; off >= 1; off >>= 1) {
-            const unsigned long long o2 = __shfl_xor_sync(FULL, best, off);
-            best = o2 < best ? o2 : best;
-        }
-        if (par) {
-            const int e = (int)(uint32_t)best;
-            __syncwarp();
-            if (lane == 0) bw[(s + e) >> 5] ^= 1u << ((s + e) & 31);
-            pen = pen + A::unabs((uint32_t)(best >> 32));
+        if (par & 1u) {
+            uint32_t ba;
+            int be;
+            lrb1<T>(ln, ch, j, ba, be);
+            ln.beta[((s + be) >> 5) * 32] ^= 1u << ((s + be) & 31);
+            if (sizeof(T) == 4) pen = pen + (PT)__uint_as_float(ba);
+            else pen = pen + (PT)ba;
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSc1Threads, 6) sc1_kernel(const Sc1Params p) {
-    typedef A1<T> A;
-    typedef typename A::V V;                        // an LLR in arithmetic: float, or int for int8
-    typedef V PT;                                   // penalty: float, or exact int for int8
+__global__ void __launch_bounds__(kSc1Threads) sc1_kernel(const Sc1Params p) {
+    typedef typename std::conditional<sizeof(T) == 4, float, int>::type PT;   // penalty: exact int for int8
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int N = 1 << p.n;
-    const int bwn = N >= 32 ? N >> 5 : 1;
-    uint8_t *mine = smem_raw + (size_t)warp * p.warp_bytes;
-    T *alpha = reinterpret_cast<T *>(mine);
-    uint32_t *bw = reinterpret_cast<uint32_t *>(mine + p.beta_off);
-    const uint32_t count = p.frame_idx ? *p.frame_cnt : p.n_frames;
-    const bool vec_ch = (reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0;
     const uint32_t wpc = blockDim.x >> 5;
-    for (uint32_t i = blockIdx.x * wpc + warp; i < count; i += gridDim.x * wpc) {
-        const uint32_t f = p.frame_idx ? p.frame_idx[i] : i;
-        const T *ch = reinterpret_cast<const T *>(p.llr) + (size_t)f * N;
+    const int es = sizeof(T);
+    Lane ln;
+    ln.n = p.n;
+    ln.N = 1 << p.n;
+    ln.es = es;
+    ln.split = p.split;
+    ln.smem = smem_raw + (size_t)warp * p.warp_bytes + 4 * lane;
+    uint8_t *gwarp = p.scratch ? p.scratch + (size_t)(blockIdx.x * wpc + warp) * p.warp_gbytes : nullptr;
+    ln.gmem = gwarp ? gwarp + 4 * lane : nullptr;
+    ln.beta = reinterpret_cast<uint32_t *>((p.beta_smem ? smem_raw + (size_t)warp * p.warp_bytes : gwarp) +
+                                           p.beta_off) + lane;
+    const int N = ln.N;
+    const int bwn = N >= 32 ? N >> 5 : 1;
+    const uint32_t count = p.frame_idx ? *p.frame_cnt : p.n_frames;
+    const bool vec = (reinterpret_cast<uintptr_t>(p.llr) & (es == 4 ? 15u : 3u)) == 0;
+    for (uint32_t base = (blockIdx.x * wpc + warp) * 32u; base < count; base += gridDim.x * wpc * 32u) {
+        const uint32_t i = base + (uint32_t)lane;
+        const bool valid = i < count;
+        const uint32_t ic = valid ? i : count - 1u;                  // idle lanes redo the last frame, unwritten
+        const uint32_t f = p.frame_idx ? p.frame_idx[ic] : ic;
+        Chan ch;
+        ch.row = reinterpret_cast<const uint8_t *>(p.llr) + (size_t)f * N * es;
+        ch.vec = vec;
         PT pen = 0;
-        // The 32-bit window in registers: R holds alpha stages 0..4, stage j
-        // in lanes [2^j, 2^(j+1)); R5 holds stage 5, element e in lane e; W
-        // holds the window's 32 beta bits (lane 0 stores it after each change).
-        V R = 0, R5 = 0;
-        uint32_t W = 0;
-        if (p.n <= 5) {
-            if (p.n == 5) R5 = A::ldch(ch + lane);
-            else if (lane >= N && lane < 2 * N) R = A::ldch(ch + lane - N);
-        } else if (p.root_leaf) {
-            T *top = stage(alpha, p.n);
-            for (int e = lane; e < N; e += 32) top[e] = A::st(A::ldch(ch + e));
-            __syncwarp();
-        }
-        // Only operations on shared memory synchronise the warp: the window
-        // operations touch registers, and lane 0 alone stores W.
-        uint32_t op = __ldg(p.ops);
+        for (int w = 0; w < bwn; ++w) ln.beta[w * 32] = 0u;
         for (int o = 0; o < p.n_ops; ++o) {
-            const uint32_t next = o + 1 < p.n_ops ? __ldg(p.ops + o + 1) : 0u;
+            const uint32_t op = __ldg(p.ops + o);                     // the same for every lane
             const int kind = (int)(op & 15u), j = (int)((op >> 4) & 15u), s = (int)(op >> 8);
-            const int nv = 1 << j;
-            if (kind == OP_F || kind == OP_G) {                        // Eq. (1), (2)
-                const bool isg = kind == OP_G;
-                if (j >= 7) {
-                    __syncwarp();
-                    if (isg) fg<T, true>(p, alpha, bw, ch, vec_ch, j, s, lane);
-                    else fg<T, false>(p, alpha, bw, ch, vec_ch, j, s, lane);
-                    __syncwarp();
-                } else if (j == 6) {                                   // stage 6 -> R5
-                    __syncwarp();
-                    const bool root = p.n == 6;
-                    const T *in = root ? ch : stage(alpha, 6);
-                    const V a = root ? A::ldch(in + lane) : A::ld(in + lane);
-                    const V b = root ? A::ldch(in + lane + 32) : A::ld(in + lane + 32);
-                    R5 = isg ? A::g(a, b, (W >> lane) & 1u) : A::f(a, b);
-                } else {                                               // inside the window
-                    const int h = nv >> 1, e = lane & (h - 1);
-                    const V src = j == 5 ? R5 : R;
-                    const int base = j == 5 ? 0 : nv;
-                    const V a = __shfl_sync(FULL, src, base + e);
-                    const V b = __shfl_sync(FULL, src, base + e + h);
-                    const V r = isg ? A::g(a, b, (W >> ((s & 31) + e)) & 1u) : A::f(a, b);
-                    if (lane >= h && lane < nv) R = r;
-                }
-            } else if (kind == OP_COMB) {                              // Eq. (3), in place
-                const int h = nv >> 1;
-                if (h >= 32) {
-                    __syncwarp();
-                    for (int w = lane; w < (h >> 5); w += 32) bw[(s >> 5) + w] ^= bw[((s + h) >> 5) + w];
-                    __syncwarp();
-                } else {
-                    W ^= (W >> h) & (((1u << h) - 1u) << (s & 31));
-                    if (lane == 0) bw[s >> 5] = W;
-                }
-            } else if (j >= 6) {
-                __syncwarp();
-                leaf_smem<T>(kind, stage(alpha, j), stage(alpha, j - 1), bw, nv, s, pen, lane);
-                __syncwarp();
-            } else {                                                   // a leaf inside the window
-                const V v = j == 5 ? R5 : R;
-                const int base = j == 5 ? 0 : nv;
-                const bool in = lane >= base && lane < base + nv;
-                const uint32_t mask = j == 5 ? FULL : ((1u << nv) - 1u);
-                uint32_t bits = 0;
-                if (kind == OP_R0) {                                   // Eq. (10)
-                    pen = pen + wsum<V>(in ? A::negpart(v) : V(0), nv, base);
-                } else if (kind == OP_R1) {
-                    bits = (__ballot_sync(FULL, in && v < 0) >> base) & mask;
-                } else if (kind == OP_REP) {                           // Eq. (5), ties to all zero
-                    const V p0 = wsum<V>(in ? A::negpart(v) : V(0), nv, base);
-                    const V p1 = wsum<V>(in ? A::pospart(v) : V(0), nv, base);
-                    const bool one = !(p0 <= p1);
-                    pen = pen + (one ? p1 : p0);
-                    bits = one ? mask : 0u;
-                } else {                                               // SPC, Sec. III-D
-                    bits = (__ballot_sync(FULL, in && v < 0) >> base) & mask;
-                    unsigned long long key =
-                        in ? (((unsigned long long)A::absbits(v) << 32) | (uint32_t)(lane - base)) : ~0ull;
-                    for (int off = nv >> 1; off >= 1; off >>= 1) {
-                        const unsigned long long o2 = __shfl_xor_sync(FULL, key, off);
-                        key = o2 < key ? o2 : key;
-                    }
-                    key = __shfl_sync(FULL, key, base);
-                    if (__popc(bits) & 1) {
-                        bits ^= 1u << (uint32_t)key;
-                        pen = pen + A::unabs((uint32_t)(key >> 32));
-                    }
-                }
-                if (j == 5) {
-                    W = bits;
-                } else {
-                    const int sh = s & 31;
-                    W = (W & ~(mask << sh)) | (bits << sh);
-                }
-                if (lane == 0) bw[s >> 5] = W;
+            if (kind == OP_F) {
+                if (es == 4) fg_f32<false>(ln, ch, j, s); else fg_i8<false>(ln, ch, j, s);
+            } else if (kind == OP_G) {
+                if (es == 4) fg_f32<true>(ln, ch, j, s); else fg_i8<true>(ln, ch, j, s);
+            } else if (kind == OP_COMB) {
+                comb(ln, j, s);
+            } else {
+                leaf<T, PT>(ln, ch, kind, j, s, pen);
             }
-            op = next;
         }
-        __syncwarp();
 
         // ---------------- final pick (Sec. II-B) ----------------
+        // CRC: the syndrome of the codeword x (the beta row), byte by byte
         uint32_t acc = 0;
         if (p.crc_len > 0) {
-            const uint8_t *xb = reinterpret_cast<const uint8_t *>(bw);
-            for (int b = lane; b < (N >> 3); b += 32) acc ^= __ldg(p.syn + ((b << 8) | xb[b]));
-            for (int off = 16; off >= 1; off >>= 1) acc ^= __shfl_xor_sync(FULL, acc, off);
+            for (int w = 0; w < (N >> 5 ? N >> 5 : 1); ++w) {
+                const uint32_t x = ln.beta[w * 32];
+                const int nb = N >= 32 ? 4 : N / 8;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (b < nb) acc ^= __ldg(p.syn + (((4 * w + b) << 8) | ((x >> (8 * b)) & 0xFFu)));
+            }
         }
-        __syncwarp();
-        if (!p.systematic) {                                           // u = x G_N, in place
+        // u = x G_N (natural-order butterflies) unless the code is systematic
+        if (!p.systematic) {
             const uint32_t M[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
-            for (int w = lane; w < bwn; w += 32) {
-                uint32_t u = bw[w];
+            for (int w = 0; w < bwn; ++w) {
+                uint32_t u = ln.beta[w * 32];
 #pragma unroll
                 for (int e = 0; e < 5; ++e)
                     if ((1 << e) < N) u ^= (u >> (1 << e)) & M[e];
-                bw[w] = u;
+                ln.beta[w * 32] = u;
             }
-            __syncwarp();
-            for (int d = 1; d < bwn; d <<= 1) {
-                for (int w = lane; w < bwn; w += 32)
-                    if (!(w & d)) bw[w] ^= bw[w + d];
-                __syncwarp();
-            }
+            for (int d = 1; d < bwn; d <<= 1)
+                for (int w = 0; w < bwn; ++w)
+                    if (!(w & d)) ln.beta[w * 32] ^= ln.beta[(w + d) * 32];
         }
-        uint8_t *row = p.bits + (size_t)f * p.kb;
-        for (int b = lane; b < p.kb; b += 32) {
-            uint32_t byte = 0;
+        if (valid) {
+            uint8_t *row = p.bits + (size_t)f * p.kb;
+            for (int b = 0; b < p.kb; ++b) {
+                uint32_t byte = 0;
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int pos = 8 * b + t;
-                if (pos < p.k) {
-                    const uint32_t u = __ldg(p.info + pos);
-                    byte |= ((bw[u >> 5] >> (u & 31u)) & 1u) << t;
+                for (int t = 0; t < 8; ++t) {
+                    const int pos = 8 * b + t;
+                    if (pos < p.k) {
+                        const uint32_t u = __ldg(p.info + pos);
+                        byte |= ((ln.beta[(u >> 5) * 32] >> (u & 31u)) & 1u) << t;
+                    }
                 }
+                row[b] = (uint8_t)byte;
             }
-            row[b] = (uint8_t)byte;
-        }
-        if (lane == 0) {
             p.pm[f] = (float)pen;
             if (p.ok) p.ok[f] = (uint8_t)(p.crc_len == 0 || acc == 0u);
             if (p.slot) p.slot[f] = 0;
         }
-        __syncwarp();
     }
 }
 
 }  // namespace
 
-int sc1_warp_bytes(int n, int es, bool root_leaf, int *beta_off) {
+// Layout of one warp (32 frames) for a shared-memory budget: the beta rows
+// go to shared memory if they fit, then alpha stages 0 .. split-1 while the
+// total fits; everything else (higher stages, and the beta rows if they did
+// not fit) to the warp's global scratch, stages first.
+void sc1_layout(int n, int es, uint32_t budget, Sc1Layout *lay) {
     const int N = 1 << n;
-    const int a = ((root_leaf ? 2 * N : N) * es + 15) & ~15;
-    const int b = ((N >= 32 ? N / 8 : 4) + 15) & ~15;
-    if (beta_off) *beta_off = a;
-    return a + b;
+    const uint32_t beta_bytes = (uint32_t)(N >= 32 ? N / 32 : 1) * 128u;
+    lay->beta_smem = beta_bytes <= budget ? 1 : 0;
+    int split = 0;
+    if (lay->beta_smem)
+        while (split < n && (uint32_t)words_below(split + 1, es) * 128u + beta_bytes <= budget) ++split;
+    lay->split = split;
+    const uint32_t sb = (uint32_t)words_below(split, es) * 128u;
+    const uint64_t gb = (uint64_t)(words_below(n, es) - words_below(split, es)) * 128u;
+    lay->warp_bytes = sb + (lay->beta_smem ? beta_bytes : 0u);
+    lay->beta_off = lay->beta_smem ? sb : (uint32_t)gb;     // in shared memory, or in scratch after the stages
+    lay->warp_gbytes = gb + (lay->beta_smem ? 0u : beta_bytes);
 }
 
-int occupancy_sc1(int dtype, int n, bool root_leaf, int warps) {
-    const int smem = warps * sc1_warp_bytes(n, dtype == POLAR_LLR_I8 ? 1 : 4, root_leaf, nullptr);
+int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps) {
+    const int smem = warps * (int)warp_bytes;
     const void *fn = dtype == POLAR_LLR_I8 ? (const void *)sc1_kernel<int8_t> : (const void *)sc1_kernel<float>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
     int blocks = 0;
@@ -446,7 +459,7 @@ int occupancy_sc1(int dtype, int n, bool root_leaf, int warps) {
 }
 
 cudaError_t launch_sc1(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t st) {
-    const int smem = warps * p.warp_bytes;
+    const int smem = warps * (int)p.warp_bytes;
     if (dtype == POLAR_LLR_I8) {
         cudaFuncSetAttribute(sc1_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         sc1_kernel<int8_t><<<grid, 32 * warps, smem, st>>>(p);

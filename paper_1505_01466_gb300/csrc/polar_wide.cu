@@ -6,7 +6,8 @@
 // threads per frame, thread p owning path p for leaves, all threads sharing
 // the element-wise F / G / Combine work. The schedule is the fully unrolled
 // one (every F, G, Combine and leaf of the decoding tree, Sec. II-D,
-// Listing 2); every stage lives in the CTA's global scratch behind per-path
+// Listing 2); every stage lives in the CTA's global scratch (or, up to a
+// shared-memory budget, the smallest buffers on chip) behind per-path
 // stage-index rows (the lazy copy of Sec. IV-A/B). Selection (Algorithm 1)
 // sorts all candidate keys of the CTA in shared memory and keeps the L
 // smallest; survivors take slots in (source, candidate) order.
@@ -76,6 +77,13 @@ struct WideSmem {
     unsigned long long *red;       // [L / 32] reduction scratch
 };
 
+// Bytes of the CTA's tables (index rows, penalties, keys, sort buffer, ...), a multiple of 16.
+__host__ __device__ __forceinline__ uint32_t tables_bytes(int L, int n) {
+    const uint32_t b = (uint32_t)(4 * L * 16 + 2 * L * 4 + 2 * L * 8 * 8 + L * 4 + L * 16 + 2 * L * 4 +
+                                  beta_words(n) * 4);
+    return ((((b + 15u) & ~15u) + 8u * (uint32_t)(L / 32)) + 15u) & ~15u;
+}
+
 __device__ __forceinline__ WideSmem carve(uint8_t *base, int L, int nbw) {
     WideSmem s;
     uint8_t *p = base;
@@ -94,10 +102,16 @@ __device__ __forceinline__ WideSmem carve(uint8_t *base, int L, int nbw) {
     return s;
 }
 
+// A buffer in the CTA's shared memory (SX: after its tables) or global scratch (G).
+__device__ __forceinline__ uint8_t *wbuf(uint64_t loc, uint8_t *SX, uint8_t *G) {
+    return (loc & kWideInSmem) ? SX + (uint32_t)loc : G + loc;
+}
+
 template <typename T>
-__device__ __forceinline__ T *wrow(const WideView &v, uint8_t *G, const WideSmem &s, int cur, int p, int j) {
-    if (j == v.n) return reinterpret_cast<T *>(G + v.gchan);
-    return reinterpret_cast<T *>(G + v.galpha[j]) + ((size_t)s.idx[cur][p * 16 + j] << j);
+__device__ __forceinline__ T *wrow(const WideView &v, uint8_t *SX, uint8_t *G, const WideSmem &s, int cur, int p,
+                                   int j) {
+    if (j == v.n) return reinterpret_cast<T *>(wbuf(v.gchan, SX, G));
+    return reinterpret_cast<T *>(wbuf(v.galpha[j], SX, G)) + ((size_t)s.idx[cur][p * 16 + j] << j);
 }
 
 // CTA-wide exclusive scan of one int per thread; returns the prefix, *total the sum.
@@ -212,14 +226,15 @@ __device__ __forceinline__ void wide_sums(T *row, int nv, bool want1, typename W
 }
 
 template <typename T>
-__device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, const uint8_t *src, uint8_t *bits_row,
+__device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const WideSmem &s, const uint8_t *src,
+                           uint8_t *bits_row,
                            float *pm_out, uint8_t *ok_out, int32_t *slot_out) {
     typedef typename WA<T>::P P;
     const int t = threadIdx.x, nt = blockDim.x, lane = t & 31;
     const int n = v.n, N = v.N, L = v.L;
     const int nbw = beta_words(n);
-    T *chan = reinterpret_cast<T *>(G + v.gchan);
-    uint32_t *br = reinterpret_cast<uint32_t *>(G + v.gbr);
+    T *chan = reinterpret_cast<T *>(wbuf(v.gchan, SX, G));
+    uint32_t *br = reinterpret_cast<uint32_t *>(wbuf(v.gbr, SX, G));
 
     for (int i = t; i < N; i += nt) {
         T x = reinterpret_cast<const T *>(src)[i];
@@ -241,14 +256,14 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
         if (kind == OP_F || kind == OP_G) {
             const int jo = j - 1, h = 1 << jo;
             const int bwc = beta_words(jo);
-            const uint32_t *blb = reinterpret_cast<const uint32_t *>(G + v.gbl[jo]);
-            T *outb = reinterpret_cast<T *>(G + v.galpha[jo]);
+            const uint32_t *blb = reinterpret_cast<const uint32_t *>(wbuf(v.gbl[jo], SX, G));
+            T *outb = reinterpret_cast<T *>(wbuf(v.galpha[jo], SX, G));
             if (h >= 4) {
                 // four consecutive elements per item (16-byte float / 4-byte int8 vectors)
                 const int lq = jo - 2;
                 for (int e = t; e < (La << lq); e += nt) {
                     const int p = e >> lq, i = (e & ((h >> 2) - 1)) << 2;
-                    const T *in = wrow<T>(v, G, s, cur, p, j);
+                    const T *in = wrow<T>(v, SX, G, s, cur, p, j);
                     uint32_t bits4 = 0u;
                     if (kind == OP_G)
                         bits4 = (blb[(int)s.bidx[cur][p * 16 + jo] * bwc + (i >> 5)] >> (i & 31)) & 15u;
@@ -280,7 +295,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
             } else {
                 for (int e = t; e < (La << jo); e += nt) {
                     const int p = e >> jo, i = e & (h - 1);
-                    const T *in = wrow<T>(v, G, s, cur, p, j);
+                    const T *in = wrow<T>(v, SX, G, s, cur, p, j);
                     T r;
                     if (kind == OP_F) {
                         r = WA<T>::f(in[i], in[i + h]);
@@ -296,8 +311,8 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
             __syncthreads();
         } else if (kind == OP_COMB) {
             const int jc = j - 1, bwc = beta_words(jc);
-            const uint32_t *blb = reinterpret_cast<const uint32_t *>(G + v.gbl[jc]);
-            uint32_t *out = dest ? br : reinterpret_cast<uint32_t *>(G + v.gbl[j]);
+            const uint32_t *blb = reinterpret_cast<const uint32_t *>(wbuf(v.gbl[jc], SX, G));
+            uint32_t *out = dest ? br : reinterpret_cast<uint32_t *>(wbuf(v.gbl[j], SX, G));
             const int ostride = dest ? nbw : beta_words(j);
             if (jc >= 5) {
                 for (int e = t; e < La * bwc; e += nt) {
@@ -323,14 +338,14 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
             // ---------------- leaf of 2^j bits: thread p = path p ----------------
             const int nv = 1 << j;
             const int bw = beta_words(j);
-            uint32_t *bout = dest ? br : reinterpret_cast<uint32_t *>(G + v.gbl[j]);
+            uint32_t *bout = dest ? br : reinterpret_cast<uint32_t *>(wbuf(v.gbl[j], SX, G));
             const int ostride = dest ? nbw : bw;
             const uint32_t wmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
             const bool act = t < La;
             if (kind == OP_R0) {
                 // Rate-0 (Sec. III-B): penalty += sum |min(a, 0)|, beta = 0, no fork.
                 if (act) {
-                    T *row = wrow<T>(v, G, s, cur, t, j);
+                    T *row = wrow<T>(v, SX, G, s, cur, t, j);
                     P v0, v1;
                     wide_sums<T>(row, nv, false, v0, v1);
                     s.pen[cur][t] = WA<T>::pbits(WA<T>::frombits(s.pen[cur][t]) + v0);
@@ -344,7 +359,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
             if (kind == OP_R1) C = nv == 1 ? 2 : 4;
             else if (kind == OP_SPC) C = L == 2 ? 2 : 8;
             if (act) {
-                T *row = wrow<T>(v, G, s, cur, t, j);
+                T *row = wrow<T>(v, SX, G, s, cur, t, j);
                 const P ps = WA<T>::frombits(s.pen[cur][t]);
                 unsigned long long *kk = s.keys + t * C;
                 if (kind == OP_REP) {
@@ -442,7 +457,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *G, const WideSmem &s, con
                     for (int w = 0; w < bw; ++w) ob[w] = word;
                 } else {
                     const uint32_t dm = kind == OP_R1 ? (uint32_t)c : (spc_mask(c) ^ (s.flag[sp] ? 0u : 1u));
-                    const T *srow = wrow<T>(v, G, s, cur, sp, j);
+                    const T *srow = wrow<T>(v, SX, G, s, cur, sp, j);
                     for (int w = 0; w < bw; ++w) {
                         uint32_t word = 0;
                         const int lim = nv < 32 ? nv : 32;
@@ -552,36 +567,38 @@ __global__ void __launch_bounds__(128) wide_kernel(const WideParams P) {
     extern __shared__ __align__(16) uint8_t smem_w[];
     const WideView &v = P.v;
     const WideSmem s = carve(smem_w, v.L, beta_words(v.n));
-    uint8_t *G = P.scratch + (size_t)blockIdx.x * v.gbytes;
+    uint8_t *SX = smem_w + tables_bytes(v.L, v.n);
+    uint8_t *G = P.scratch ? P.scratch + (size_t)blockIdx.x * v.gbytes : nullptr;
     const size_t nbytes = (size_t)v.N * sizeof(T);
     const uint32_t nf = P.frame_idx ? *P.frame_cnt : P.n_frames;
     for (uint32_t i = blockIdx.x; i < nf; i += gridDim.x) {
         const uint32_t f = P.frame_idx ? P.frame_idx[i] : i;
-        wide_frame<T>(v, G, s, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
+        wide_frame<T>(v, SX, G, s, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
                       P.bits + (size_t)f * v.kb, P.pm + f, P.ok ? P.ok + f : nullptr, P.slot ? P.slot + f : nullptr);
     }
 }
 
 }  // namespace
 
-uint32_t wide_smem_bytes(int L, int n) {
-    const uint32_t b = (uint32_t)(4 * L * 16 + 2 * L * 4 + 2 * L * 8 * 8 + L * 4 + L * 16 + 2 * L * 4 +
-                                  beta_words(n) * 4);
-    return ((b + 15u) & ~15u) + 8u * (uint32_t)(L / 32);
-}
+uint32_t wide_smem_bytes(int L, int n) { return tables_bytes(L, n); }
 
-int occupancy_wide(int dtype, int L, int n) {
-    const uint32_t sm = wide_smem_bytes(L, n);
+int occupancy_wide(int dtype, int L, uint32_t sm) {
     int nb = 0;
-    cudaError_t e = dtype == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wide_kernel<float>, L, sm)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wide_kernel<int8_t>, L, sm);
+    const void *fn = dtype == 0 ? (const void *)wide_kernel<float> : (const void *)wide_kernel<int8_t>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, L, sm);
     return e == cudaSuccess ? nb : 0;
 }
 
 cudaError_t launch_wide(int dtype, const WideParams &p, int grid, cudaStream_t st) {
-    const uint32_t sm = wide_smem_bytes(p.v.L, p.v.n);
-    if (dtype == 0) wide_kernel<float><<<grid, p.v.L, sm, st>>>(p);
-    else wide_kernel<int8_t><<<grid, p.v.L, sm, st>>>(p);
+    const uint32_t sm = wide_smem_bytes(p.v.L, p.v.n) + p.v.sbytes;
+    if (dtype == 0) {
+        cudaFuncSetAttribute(wide_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        wide_kernel<float><<<grid, p.v.L, sm, st>>>(p);
+    } else {
+        cudaFuncSetAttribute(wide_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        wide_kernel<int8_t><<<grid, p.v.L, sm, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

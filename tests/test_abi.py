@@ -219,24 +219,39 @@ def test_stage_memory_follows_the_paper_accounting(polar, dtype, es, L):
 
 
 def test_l1_codes_report_their_own_kernel(polar):
-    """L = 1 codes run the Fast-SSC kernel: one warp per frame, every stage in
-    shared memory, no scratch; set_launch hands them to the list kernels."""
+    """L = 1 codes run the Fast-SSC kernel: one lane per frame, 32 frames per
+    warp, alpha stages and beta rows interleaved over the lanes. By default all
+    of it sits in global scratch (coalesced, L1-cached); a shared-memory budget
+    per warp takes the beta rows first, then the lowest stages that fit;
+    set_launch hands the code to the list kernels."""
     fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
     code = polar.PolarCode(fr, 32, I.CRC32_POLY, 1, host_only=True)
+    below = {4: lambda j: (1 << j) - 1, 1: lambda j: j if j <= 2 else (1 << (j - 2)) + 1}
+    beta = 64 * 128                                                 # N / 32 words of 32 lanes
+
     info = code.info()
-    assert info["warps_per_frame"] == [1, 1] and info["frames_per_cta"] == [8, 8]
-    assert info["smem_per_frame"] == [2048 * 4 + 256, 2048 + 256]     # alpha row + beta row
-    assert info["scratch_per_frame"] == [0, 0] and info["spill_mask"] == [0, 0]
+    for d, es in ((0, 4), (1, 1)):
+        assert info["warps_per_frame"][d] == 1 and info["frames_per_cta"][d] == 256
+        assert info["smem_per_frame"][d] == 0
+        assert info["scratch_per_frame"][d] == (below[es](11) * 128 + beta) // 32
+        assert info["spill_mask"][d] == (1 << 11) - 1
+    code.set_smem_budget(0, 48 * 1024)                              # f32: beta rows and stages 0..7
+    smem = below[4](8) * 128 + beta
+    assert smem <= 48 * 1024 < below[4](9) * 128 + beta
+    info = code.info()
+    assert info["smem_per_frame"][0] == smem // 32 and info["frames_per_cta"][0] == 32 * min(8, 232448 // smem)
+    assert info["scratch_per_frame"][0] == (below[4](11) - below[4](8)) * 128 // 32
+    assert info["spill_mask"][0] == ((1 << 11) - 1) & ~0xFF
+    code.set_smem_budget(1, 232448)                                 # int8: every stage on chip
+    smem = below[1](11) * 128 + beta
+    assert code.info()["smem_per_frame"][1] == smem // 32 and code.info()["scratch_per_frame"][1] == 0
+    assert code.info()["frames_per_cta"][1] == 32 * (232448 // smem)
     code.set_launch(0, 1, 7000, 512)
     assert code.info()["frames_per_cta"][0] == 16 and code.info()["scratch_per_frame"][0] > 0
-    assert code.info()["frames_per_cta"][1] == 8                        # the other dtype keeps it
-    # a code whose root is a leaf keeps a copy of the channel row as well
-    rep = np.ones(4096, np.uint8)
-    rep[-1] = 0
-    root = polar.PolarCode(rep, 0, 0, 1, host_only=True)
-    assert root.schedule() == [(13, 4096, 0)]
-    assert root.info()["smem_per_frame"] == [2 * 4096 * 4 + 512, 2 * 4096 + 512]
-    assert root.info()["frames_per_cta"] == [232448 // (2 * 4096 * 4 + 512), 8]
+    code.set_smem_budget(0, 0)                                      # back to the L = 1 kernel
+    assert code.info()["frames_per_cta"][0] == 256
+    with pytest.raises(polar.PolarError):
+        polar.PolarCode(fr, 32, I.CRC32_POLY, 4, host_only=True).set_smem_budget(0, 0)
 
 
 def test_recomputed_stages_leave_the_layout(polar):

@@ -1,7 +1,7 @@
 """GPU parity of the L = 1 (Fast-SSC) kernel against the oracle.
 
-A code with L = 1 runs its own kernel (one warp per frame, lanes over the
-elements of a node) unless set_launch fixes a shape of the list kernels. Both
+A code with L = 1 runs its own kernel (one lane per frame, 32 frames per
+warp) unless set_launch fixes a shape of the list kernels. Both
 must give the oracle's results bit for bit (payload, CRC flag, slot 0) with the
 penalty exact for int8 and within 1e-5 relative for float32.
 """
@@ -56,7 +56,7 @@ def _both_kernels(torch, oracle_mod, fr, crc, poly, llr, mode=0, systematic=Fals
     o = oracle_mod.decode(fr, 1, llr, crc, poly, mode | (oracle_mod.SYSTEMATIC if systematic else 0), n_threads=NT)
     code = PolarCode(fr, crc, poly, 1, mode=mode, systematic=systematic)
     info = code.info()
-    assert info["warps_per_frame"] == [1, 1] and info["scratch_per_frame"] == [0, 0]
+    assert info["warps_per_frame"] == [1, 1] and info["frames_per_cta"][0] % 32 == 0
     g = _decode(torch, code, llr, offset)
     _check(g, o, dtype, f"L=1 kernel N={fr.size} mode={mode} sys={systematic} offset={offset}")
     code.set_launch(1 if dtype == "i8" else 0, 1, 0, 128)          # the list kernel at L = 1
@@ -165,4 +165,52 @@ def test_sync_waits_for_the_stream(torch_cuda, oracle_mod):
     g = tuple(t.cpu().numpy() for t in (bits, pm, ok, slot))
     _check(g, o, "f32", "after polar_sync")
     polar.sync()                                        # the current stream: nothing pending
+    code.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+def test_every_shared_memory_budget(torch_cuda, oracle_mod, dtype):
+    """The L = 1 kernel keeps the lowest alpha stages of its 32 frames per warp
+    in shared memory up to a budget and the others in global scratch: from
+    every stage on chip (int8) down to none (budget 1), the results are the
+    oracle's. The scratch is poisoned, so a value read before it is written
+    would show up."""
+    from paper_1505_01466_gb300 import polar
+    torch = torch_cuda
+    lib = polar.load_library()
+    dt = polar.LLR_I8 if dtype == "i8" else polar.LLR_F32
+    rng = np.random.default_rng(5)
+    for N, K, crc in ((2048, 1723, 32), (4096, 2500, 8), (64, 40, 8)):
+        poly = I.CRC32_POLY if crc == 32 else I.CRC8_POLY
+        fr = I.ga_frozen_mask(N, K, 3.0, (K - crc) / N)
+        f = I.make_frames(fr, crc, poly, float(rng.uniform(2.0, 3.5)), 200, seed=N)
+        llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+        o = oracle_mod.decode(fr, 1, llr, crc, poly, 0, n_threads=NT)
+        code = polar.PolarCode(fr, crc, poly, 1)
+        splits = set()
+        lib.polar_debug_inject(polar.INJECT_POISON, 1)
+        try:
+            for budget in (0, 232448, 100000, 60000, 30000, 12000, 1):
+                code.set_smem_budget(dt, budget)
+                info = code.info()
+                splits.add(info["spill_mask"][dt])
+                g = _decode(torch, code, llr)
+                _check(g, o, dtype, f"N={N} budget={budget}")
+        finally:
+            lib.polar_debug_inject(polar.INJECT_POISON, 0)
+        assert ((1 << fr.size.bit_length() - 1) - 1) in splits          # every stage in scratch once
+        assert len(splits) >= (3 if N >= 1024 else 2)
+        code.close()
+
+
+def test_autotune_keeps_results(torch_cuda, oracle_mod):
+    from paper_1505_01466_gb300 import polar
+    torch = torch_cuda
+    fr = I.ga_frozen_mask(2048, 1723, 4.0, 1691 / 2048)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 3.5, 1000, seed=3)
+    o = oracle_mod.decode(fr, 1, f.llr_f32, 32, I.CRC32_POLY, 0, n_threads=NT)
+    code = polar.PolarCode(fr, 32, I.CRC32_POLY, 1)
+    w, b, t = code.autotune(torch.from_numpy(f.llr_f32).cuda())
+    assert w == 1 and t % 32 == 0 and b > 0
+    _check(_decode(torch, code, f.llr_f32), o, "f32", "after autotune")
     code.close()

@@ -96,3 +96,49 @@ def test_wide_systematic_and_adaptive(env, oracle_mod):
             wide.set_launch(0, 1, 0)
     fast.close()
     wide.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i8"])
+@pytest.mark.parametrize("L", [64, 128])
+def test_every_shared_memory_budget(env, oracle_mod, dtype, L):
+    """The wide CTA keeps its smallest buffers (low alpha stages, left betas,
+    the channel row) in shared memory up to a budget and the rest in global
+    scratch: from nothing on chip (budget 1) to as much as a CTA holds, with
+    the scratch poisoned, the results are the oracle's."""
+    torch, polar = env
+    lib = polar.load_library()
+    dt = polar.LLR_I8 if dtype == "i8" else polar.LLR_F32
+    for N, K, crc, poly, snr in ((1024, 836, 8, I.CRC8_POLY, 3.0), (256, 128, 8, I.CRC8_POLY, 1.5),
+                                 (4096, 3000, 32, I.CRC32_POLY, 3.0)):
+        fr = I.ga_frozen_mask(N, K, 3.0, (K - crc) / N)
+        f = I.make_frames(fr, crc, poly, snr, 24 if N == 4096 else 64, seed=N + L)
+        llr = f.llr_i8 if dtype == "i8" else f.llr_f32
+        o = oracle_mod.decode(fr, L, llr, crc, poly, 0, n_threads=NT)
+        code = polar.PolarCode(fr, crc, poly, L)
+        masks = set()
+        lib.polar_debug_inject(polar.INJECT_POISON, 1)
+        try:
+            for budget in (1, 6000, 20000, 0, 100000, 232448):
+                code.set_smem_budget(dt, budget)
+                masks.add(code.info()["spill_mask"][dt])
+                g = code.decode(torch.from_numpy(np.ascontiguousarray(llr)).cuda())
+                torch.cuda.synchronize()
+                _parity(g, o, dtype, f"N={N} L={L} budget={budget}")
+        finally:
+            lib.polar_debug_inject(polar.INJECT_POISON, 0)
+        assert ((1 << (N.bit_length() - 1)) - 1) in masks and len(masks) >= 3
+        code.close()
+
+
+def test_wide_autotune_keeps_results(env, oracle_mod):
+    torch, polar = env
+    fr = I.ga_frozen_mask(1024, 836, 4.0, 828 / 1024)
+    f = I.make_frames(fr, 8, I.CRC8_POLY, 3.0, 600, seed=8)
+    llr = torch.from_numpy(f.llr_f32).cuda()
+    code = polar.PolarCode(fr, 8, I.CRC8_POLY, 128)
+    w, b, t = code.autotune(llr)
+    assert w == 4 and t == 128 and b > 0
+    g = code.decode(llr)
+    torch.cuda.synchronize()
+    _parity(g, oracle_mod.decode(fr, 128, f.llr_f32, 8, I.CRC8_POLY, 0, n_threads=NT), "f32", "after autotune")
+    code.close()
