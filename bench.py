@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--fer-points", default="3.5,3.75,4.0,4.25,4.5", help="Eb/N0 points (dB) of the FER sweep")
     ap.add_argument("--fer-codes", default="c2,c3", help="FER sweep codes: c2 = (1024,860), c3 = (2048,1723)")
     ap.add_argument("--details", default="", help="also write every measured block in full to this JSON file")
+    ap.add_argument("--case", default="", choices=["", "sc1", "list", "wide", "batch"],
+                    help="run one small decode case for a profiler and exit: each dtype (or plan) once as warm-up, "
+                         "then once more")
     return ap.parse_args()
 
 
@@ -965,8 +968,65 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_case(name):
+    """Small cases for ncu captures (inputs above L2, a few GB at most):
+    sc1   (2048,1723) L = 1, 2^16 frames, f32 then int8 (launches 1 and 3 of sc1_kernel);
+    list  (2048,1723) L = 32, 2^15 frames, 1 warp per frame, 7000-byte budget, 512-thread CTAs,
+          f32 then int8 (launches 1 and 3 of decode_kernel);
+    wide  (1024,860) L = 128, 2^13 frames, f32 (launch 1 of wide_kernel);
+    batch the 125-class int8 mix, 2^16 frames, 1 warp per frame, 7000-byte budget, 512-thread CTAs
+          (launch 1 of batch_kernel)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1505_01466_gb300 import inputs as I, workloads as WL
+    from paper_1505_01466_gb300.polar import PolarCode, PolarBatch, LLR_I8
+    torch.cuda.set_device(0)
+    if name in ("sc1", "list"):
+        Lc, F = (1, 1 << 16) if name == "sc1" else (L, 1 << 15)
+        frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
+        _, f32, i8 = I.make_frames_torch(frozen, CRC_LEN, I.CRC32_POLY, EBN0_DB, F, seed=5, device="cuda")
+        code = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, Lc)
+        for dt, llr in ((0, f32), (1, i8)):
+            if name == "list":
+                code.set_launch(dt, 1, 7000, 512)
+            code.decode(llr[:4096])
+            code.decode(llr)
+    elif name == "wide":
+        frozen = I.ga_frozen_mask(1024, 860, DESIGN_DB, 828 / 1024)
+        _, f32, _ = I.make_frames_torch(frozen, CRC_LEN, I.CRC32_POLY, 3.5, 1 << 13, seed=5, device="cuda")
+        code = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, 128)
+        code.decode(f32[:512])
+        code.decode(f32)
+    else:
+        pools = WL.class_pools(pool_frames=64, seed=11)
+        codes = [PolarCode(p.frozen, p.crc_len, I.CRC32_POLY, p.L) for p in pools]
+        F = 1 << 16
+        fc = I.frame_order(I.zipf_class_counts(F, len(pools), seed=1), seed=1)
+        plan = PolarBatch(codes, fc, LLR_I8)
+        llr_bytes, bits_bytes, lo, _ = plan.layout()
+        packed = torch.zeros(llr_bytes, dtype=torch.int8, device="cuda")
+        for c, p in enumerate(pools):
+            sel = np.flatnonzero(fc == c)
+            if sel.size:
+                rows = torch.from_numpy(p.llr_i8[np.arange(sel.size) % p.llr_i8.shape[0]]).cuda()
+                idx = torch.from_numpy(lo[sel].astype(np.int64)).cuda()[:, None] + torch.arange(p.N, device="cuda")
+                packed[idx] = rows
+        bits = torch.empty(bits_bytes, dtype=torch.uint8, device="cuda")
+        pm = torch.empty(F, dtype=torch.float32, device="cuda")
+        plan.set_launch(1, 7000, 512)
+        plan.run(packed, bits, pm)
+        plan.run(packed, bits, pm)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

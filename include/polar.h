@@ -133,7 +133,8 @@ POLAR_API int polar_code_destroy(polar_code_t *code);
  * its own scratch from the stream-ordered allocator when the code needs any).
  * A call with no more frames than the device has SMs runs them with a
  * latency shape (four warps and a CTA's shared memory per frame) unless
- * polar_code_set_launch fixed the shape; results do not depend on the shape.
+ * polar_code_set_launch fixed the shape, L = 1 codes included; results do not
+ * depend on the shape.
  * The call is asynchronous: it reports launch errors; an error raised while
  * its kernels run shows up in polar_sync (or the next CUDA call).
  * Errors: POLAR_EINVAL (NULL code/required pointer, bad dtype, host-only
@@ -267,7 +268,8 @@ POLAR_API int polar_adaptive_decode(const polar_code_t *fast, const polar_code_t
  * and reports it (any out pointer may be NULL; *budget_out = 0 means no cap).
  * Blocks until the timing runs finish. Results of later decodes do not depend
  * on the shape (only speed does). A code with L = 1 gets its own kernel back
- * and its shared-memory budget per warp timed (see polar_code_set_smem_budget;
+ * and its shared-memory budget per warp timed when the sample fills every SM
+ * (otherwise the default is kept; see polar_code_set_smem_budget;
  * *warps_out = 1, *budget_out = that budget, *cta_out = the CTA's threads);
  * a wide code gets its shared-memory budget per CTA timed (*warps_out = L/32,
  * *budget_out = that budget, *cta_out = L). Errors: POLAR_EINVAL, POLAR_ENOMEM,

@@ -663,10 +663,13 @@ int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx = nullptr,
                const uint32_t *frame_cnt = nullptr) {
     if (code->wide) return decode_wide(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
-    if (use_sc1(code, dtype)) return decode_sc1(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
     // a batch no larger than the SM count is latency-bound: give each frame a
-    // CTA of its own with everything on chip (unless the shape was fixed)
+    // CTA of its own with everything on chip (unless the shape was fixed).
+    // That holds at L = 1 too, where one lane would otherwise walk a whole
+    // frame alone.
     const bool small = n_frames <= (uint32_t)code->sm_count && !frame_idx;
+    if (use_sc1(code, dtype) && !(small && code->lat[dtype].d_ops))
+        return decode_sc1(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
     const LaunchShape &sh = (small && !code->explicit_shape[dtype] && code->lat[dtype].d_ops) ? code->lat[dtype]
                                                                                                 : code->shape[dtype];
     return decode_shape(code, dtype, sh, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
@@ -1025,6 +1028,21 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
         // alpha stages stay on chip against how many warps fit) and keep the fastest
         static const uint32_t sc1_budgets[] = {0u, 9000u, 17000u, 25000u, 33000u, 46000u, 57000u, 76000u,
                                                112000u, kMaxSmemPerCta};
+        // A sample that does not fill every SM at the default layout would
+        // favour layouts with fewer resident warps; keep the default then.
+        {
+            const Sc1Shape d0 = sc1_shape(code, llr_dtype, 0);
+            const int occ0 = occupancy_sc1_locked(llr_dtype, d0.warp_bytes, d0.warps);
+            if (occ0 <= 0) return POLAR_ECUDA;
+            if ((uint64_t)n_frames < (uint64_t)occ0 * code->sm_count * 32u * (uint64_t)d0.warps) {
+                code->sc1_budget[llr_dtype] = 0;
+                code->explicit_shape[llr_dtype] = false;
+                if (warps_out) *warps_out = 1;
+                if (budget_out) *budget_out = 0;
+                if (cta_out) *cta_out = 32u * (uint32_t)d0.warps;
+                return POLAR_OK;
+            }
+        }
         cudaStream_t st1 = reinterpret_cast<cudaStream_t>(stream);
         const size_t kb1 = (code->k + 7) / 8;
         uint8_t *b1 = nullptr;

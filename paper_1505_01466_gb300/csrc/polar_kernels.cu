@@ -905,6 +905,7 @@ __device__ __forceinline__ void lane_lrb(const T *row, int nv, typename LrbKey<T
     int cnt = 0;
     if (sizeof(T) == 4) {
         const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll 4
         for (int q = 0; q < (nv >> 2); ++q) {
             const float4 v = r4[q];
             cnt += (v.x < 0.f) + (v.y < 0.f) + (v.z < 0.f) + (v.w < 0.f);
@@ -1186,14 +1187,14 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                 const uint32_t *blb = bl_ptr(lay, S, Gs, jo);
                 const int bwc = beta_words(jo);
                 if (sizeof(T) == 4) {
-                    const int lv = jo - 2;             // h >= 16 here: float4 items
+                    const int lv = jo - 2;             // h >= 16 here: float4 items, eight in flight per thread
                     const int total = La << lv;
-                    for (int t0 = tid; t0 < total; t0 += 4 * nthr) {
-                        float4 a[4], b[4];
-                        uint32_t nb[4] = {0u, 0u, 0u, 0u};
-                        int pp[4], vv[4];
+                    for (int t0 = tid; t0 < total; t0 += 8 * nthr) {
+                        float4 a[8], b[8];
+                        uint32_t nb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                        int pp[8], vv[8];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < 8; ++u) {
                             const int t = t0 + u * nthr;
                             pp[u] = t < total ? t >> lv : 0;
                             vv[u] = t < total ? t & ((1 << lv) - 1) : 0;
@@ -1207,7 +1208,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < 8; ++u) {
                             if (t0 + u * nthr >= total) break;
                             float4 r;
                             if (isG) {

@@ -68,7 +68,8 @@ __device__ __forceinline__ uint32_t spc_mask(int c) { return (0xFCA69530u >> (4 
 struct WideSmem {
     uint8_t *idx[2], *bidx[2];     // [L][16] stage -> physical row
     uint32_t *pen[2];              // penalty bits per slot
-    unsigned long long *keys;      // [L * 8] candidate keys in (source, candidate) order
+    unsigned long long *keys;      // [8][L] candidate keys, candidate-major: (source t, candidate c) at c * L + t,
+                                   // so a warp's lanes touch consecutive words
     unsigned long long *sortb;     // [pow2 >= L * 8] sort buffer
     uint32_t *flag, *mpos;         // per source: SPC parity / repetition ML flag, [L][4] positions
     int *nsrc;                     // per new slot: index into keys[]
@@ -135,8 +136,8 @@ __device__ __forceinline__ int cta_excl_scan(int x, int *scan, int *total) {
     return base + v - x;
 }
 
-// Exact L-th smallest of keys[0, M) (M = La * C > L), source t owning
-// keys[t*C, t*C + C). With a full list (La = L) the answer is at most t0, the
+// Exact L-th smallest of the M = La * C > L candidate keys, source t owning
+// keys[c * L + t] for c < C. With a full list (La = L) the answer is at most t0, the
 // largest of the sources' best keys, so only keys <= t0 are sorted: the L
 // best keys plus the few later candidates below t0. Otherwise all M keys are.
 __device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, int L, int La, int C) {
@@ -146,7 +147,7 @@ __device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, 
         unsigned long long m = 0ull;
         if (t < La) {
             m = KINF64;
-            for (int c = 0; c < C; ++c) m = s.keys[t * C + c] < m ? s.keys[t * C + c] : m;
+            for (int c = 0; c < C; ++c) m = s.keys[c * L + t] < m ? s.keys[c * L + t] : m;
         }
         for (int d = 16; d > 0; d >>= 1) {
             const unsigned long long o = __shfl_xor_sync(FULLW, m, d);
@@ -161,13 +162,13 @@ __device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, 
     // compact the keys <= t0 (all of them without a full list)
     int cnt = 0;
     if (t < La)
-        for (int c = 0; c < C; ++c) cnt += s.keys[t * C + c] <= t0 ? 1 : 0;
+        for (int c = 0; c < C; ++c) cnt += s.keys[c * L + t] <= t0 ? 1 : 0;
     int S = 0;
     int off = cta_excl_scan(cnt, s.scan, &S);
     if (S == L) return t0;               // no later candidate below t0
     if (t < La)
         for (int c = 0; c < C; ++c)
-            if (s.keys[t * C + c] <= t0) s.sortb[off++] = s.keys[t * C + c];
+            if (s.keys[c * L + t] <= t0) s.sortb[off++] = s.keys[c * L + t];
     int P = 1;
     while (P < S) P <<= 1;
     for (int i = S + t; i < P; i += blockDim.x) s.sortb[i] = KINF64;
@@ -361,7 +362,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
             if (act) {
                 T *row = wrow<T>(v, SX, G, s, cur, t, j);
                 const P ps = WA<T>::frombits(s.pen[cur][t]);
-                unsigned long long *kk = s.keys + t * C;
+                unsigned long long *kk = s.keys + t;        // candidate c at kk[c * L]
                 if (kind == OP_REP) {
                     // Repetition (Sec. III-E): the ML word listed first.
                     P x0, x1;
@@ -369,7 +370,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
                     const uint32_t fl = (x0 <= x1) ? 0u : 1u;
                     s.flag[t] = fl;
                     kk[0] = ((unsigned long long)WA<T>::pbits(ps + (fl ? x1 : x0)) << 32) | (unsigned)(t * C);
-                    kk[1] = ((unsigned long long)WA<T>::pbits(ps + (fl ? x0 : x1)) << 32) | (unsigned)(t * C + 1);
+                    kk[L] = ((unsigned long long)WA<T>::pbits(ps + (fl ? x0 : x1)) << 32) | (unsigned)(t * C + 1);
                 } else {
                     // least reliable positions by (|a|, index), and the parity of the hard decision
                     const int R = kind == OP_R1 ? 2 : 4;
@@ -405,10 +406,10 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
                     if (kind == OP_R1) {
                         // Rate-1 (Sec. III-C): HD, HD^m1, HD^m2, HD^m1^m2.
                         kk[0] = ((unsigned long long)WA<T>::pbits(ps) << 32) | (unsigned)(t * C);
-                        kk[1] = ((unsigned long long)WA<T>::pbits(ps + ar[0]) << 32) | (unsigned)(t * C + 1);
+                        kk[L] = ((unsigned long long)WA<T>::pbits(ps + ar[0]) << 32) | (unsigned)(t * C + 1);
                         if (C == 4) {
-                            kk[2] = ((unsigned long long)WA<T>::pbits(ps + ar[1]) << 32) | (unsigned)(t * C + 2);
-                            kk[3] = ((unsigned long long)WA<T>::pbits(ps + (ar[0] + ar[1])) << 32) | (unsigned)(t * C + 3);
+                            kk[2 * L] = ((unsigned long long)WA<T>::pbits(ps + ar[1]) << 32) | (unsigned)(t * C + 2);
+                            kk[3 * L] = ((unsigned long long)WA<T>::pbits(ps + (ar[0] + ar[1])) << 32) | (unsigned)(t * C + 3);
                         }
                     } else {
                         // SPC (Sec. III-D): ML = HD or HD^m1 by the parity q; ML ^ T, penalty Eq. (9).
@@ -420,7 +421,7 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
                             bool first = true;
                             for (int r = 0; r < 4; ++r)
                                 if ((dm >> r) & 1u) { inc = first ? ar[r] : inc + ar[r]; first = false; }
-                            kk[c] = ((unsigned long long)WA<T>::pbits(ps + inc) << 32) | (unsigned)(t * C + c);
+                            kk[c * L] = ((unsigned long long)WA<T>::pbits(ps + inc) << 32) | (unsigned)(t * C + c);
                         }
                     }
                 }
@@ -433,18 +434,18 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
             // survivors in (source, candidate) order: thread t scans items [t*q, t*q + q)
             const int q = (M + nt - 1) / nt;
             int cnt = 0;
-            for (int i = t * q; i < M && i < t * q + q; ++i) cnt += s.keys[i] <= tau ? 1 : 0;
+            for (int i = t * q; i < M && i < t * q + q; ++i) cnt += s.keys[(i & (C - 1)) * L + i / C] <= tau ? 1 : 0;
             int tot = 0;
             int off = cta_excl_scan(cnt, s.scan, &tot);
             for (int i = t * q; i < M && i < t * q + q; ++i)
-                if (s.keys[i] <= tau) s.nsrc[off++] = i;
+                if (s.keys[(i & (C - 1)) * L + i / C] <= tau) s.nsrc[off++] = i;
             __syncthreads();
             // ---------------- commit: slot t takes its source's rows and its word ----------------
             const int nxt = cur ^ 1;
             if (t < keep) {
                 const int ki = s.nsrc[t];
                 const int sp = ki / C, c = ki - sp * C;
-                const unsigned long long key = s.keys[ki];
+                const unsigned long long key = s.keys[(ki & (C - 1)) * L + ki / C];
                 s.pen[nxt][t] = (uint32_t)(key >> 32);
                 for (int b = 0; b < 16; ++b) {
                     s.idx[nxt][t * 16 + b] = s.idx[cur][sp * 16 + b];

@@ -211,6 +211,6 @@ def test_autotune_keeps_results(torch_cuda, oracle_mod):
     o = oracle_mod.decode(fr, 1, f.llr_f32, 32, I.CRC32_POLY, 0, n_threads=NT)
     code = polar.PolarCode(fr, 32, I.CRC32_POLY, 1)
     w, b, t = code.autotune(torch.from_numpy(f.llr_f32).cuda())
-    assert w == 1 and t % 32 == 0 and b > 0
+    assert w == 1 and t % 32 == 0 and b == 0          # a 1000-frame sample keeps the default
     _check(_decode(torch, code, f.llr_f32), o, "f32", "after autotune")
     code.close()
