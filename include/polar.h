@@ -217,6 +217,19 @@ POLAR_API int polar_code_set_launch(polar_code_t *code, int llr_dtype, uint32_t 
  * <= 32: those codes take polar_code_set_launch). */
 POLAR_API int polar_code_set_smem_budget(polar_code_t *code, int llr_dtype, uint32_t bytes);
 
+/* List sizes L <= 16 with one warp per frame: in rounds where every frame
+ * group of a CTA holds a frame, run the register subtrees (Sec. III leaves of
+ * up to 32 bits and their selection, Algorithm 1) of 32 / L frames in one
+ * warp, L lanes each, while the other warps of those frames wait (on != 0),
+ * or each frame in its own warp (on = 0, the default). Either way the
+ * selection of a frame sorts and scans inside its own L lanes. Needs a shape
+ * with one warp per frame and at least 32 / L frames per CTA; keeps the rest
+ * of the current shape; polar_code_autotune also tries it. Results do not
+ * depend on it. Errors: POLAR_EINVAL (bad arguments or shape),
+ * POLAR_EUNSUPPORTED (a wide code), POLAR_ENOMEM / POLAR_ECUDA (uploading the
+ * schedule). */
+POLAR_API int polar_code_set_packing(polar_code_t *code, int llr_dtype, int on);
+
 /* Stage memory against recomputation (Sec. IV-E counts one alpha row per
  * path and stage). The top `depth` alpha stages (at most
  * max_recompute_depth, at most 3) are not stored: an F or G that reads one

@@ -393,6 +393,7 @@ bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget,
     if (!build_layout(c->n, c->L, es, budget, lay, virt_mask_of(c->n, vd))) return false;
     sh.d_ops = nullptr;
     sh.budget = budget;
+    sh.pack = 0;
     sh.warps = (int)warps;
     sh.groups_per_cta = (int)gpc;
     sh.threads = (int)cta_threads;
@@ -469,6 +470,7 @@ CodeView make_view(const polar_code *code, const LaunchShape &sh) {
     v.kb = (int)((code->k + 7) / 8);
     v.crc_len = (int)code->crc_len;
     v.systematic = (code->flags & POLAR_SYSTEMATIC) ? 1 : 0;
+    v.pack = sh.pack;
     v.lay = sh.lay;
     return v;
 }
@@ -1145,6 +1147,27 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
       if (status != POLAR_OK) break;
     }
     }
+    // several frames' register subtrees to a warp (L <= 16, one warp per frame,
+    // 32 / L frame groups to a CTA) on the best shape
+    if (status == POLAR_OK && best_w == 1 && code->L <= 16 && (uint32_t)(32 / code->L) <= best_t / 32) {
+        LaunchShape sh = best;
+        sh.pack = 1;
+        std::vector<uint32_t> fl = flag_ops(code->ops, 1);
+        if (upload(&sh.d_ops, fl) == cudaSuccess) {
+            float ms = 0.f;
+            int rc = decode_shape(code, llr_dtype, sh, llr_dev, n_frames, bits, pm, nullptr, nullptr, st);
+            if (rc == POLAR_OK) {
+                cudaEventRecord(e0, st);
+                rc = decode_shape(code, llr_dtype, sh, llr_dev, n_frames, bits, pm, nullptr, nullptr, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = POLAR_ECUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            cudaFree(sh.d_ops);
+            sh.d_ops = nullptr;
+            if (rc == POLAR_OK && ms < best_ms) { best_ms = ms; best = sh; }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(bits);
@@ -1627,6 +1650,19 @@ int polar_code_set_smem_budget(polar_code_t *c, int llr_dtype, uint32_t bytes) {
     c->sc1_budget[llr_dtype] = bytes;
     c->explicit_shape[llr_dtype] = false;
     return POLAR_OK;
+}
+
+int polar_code_set_packing(polar_code_t *c, int llr_dtype, int on) {
+    if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
+    if (c->wide) return POLAR_EUNSUPPORTED;
+    LaunchShape sh = c->shape[llr_dtype];
+    if (on && (sh.warps != 1 || c->L > 16 || 32 / (int)c->L > sh.groups_per_cta)) return POLAR_EINVAL;
+    sh.pack = on ? 1 : 0;
+    sh.d_ops = nullptr;
+    const bool fixed = c->explicit_shape[llr_dtype];
+    const int st = install_shape(c, llr_dtype, sh);
+    c->explicit_shape[llr_dtype] = fixed;
+    return st;
 }
 
 int polar_code_set_recompute(polar_code_t *c, int llr_dtype, uint32_t depth) {

@@ -100,6 +100,7 @@ struct CodeView {
     int n_ops;
     int N, n, L, K, k, kb, crc_len;
     int systematic;                // payload read from x, not from u = x G_N
+    int pack;                      // L <= 16: run register subtrees 32 / L frames to a warp in lockstep rounds
     Layout lay;
 };
 
@@ -152,6 +153,7 @@ struct LaunchShape {
     int groups_per_cta;
     int threads;                   // per CTA
     uint32_t smem;                 // dynamic shared memory per CTA
+    int pack;                      // CodeView::pack
     Layout lay;
 };
 

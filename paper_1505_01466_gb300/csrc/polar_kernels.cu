@@ -379,6 +379,146 @@ __device__ __forceinline__ K warp_kth(const K (&k)[8], int C, int L, int La, int
     return tau;
 }
 
+// ---- segmented selection: several frames' paths in one warp ----------------
+// With L <= 16 paths a warp holds P = 32 / L frames' subtrees at once: lane
+// sb + s is path s of the frame whose segment starts at lane sb, and every
+// sort, scan and reduction stays inside an aligned segment of sn = L lanes
+// (xor partners below sn never leave it). Branches that depend on the data of
+// one segment are taken warp-uniformly (on the warp's maximum), so every
+// shuffle sees the whole warp.
+template <typename K>
+__device__ __forceinline__ K bsort_seg(K x, int ls, int sn) {   // ascending inside each segment
+    for (int k = 2; k <= sn; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const K o = __shfl_xor_sync(FULL, x, j);
+            const bool up = (ls & k) == 0;
+            const bool lo = (ls & j) == 0;
+            x = (lo == up) ? kmin(x, o) : kmax(x, o);
+        }
+    }
+    return x;
+}
+
+template <typename K>
+__device__ __forceinline__ K bmerge_seg(K x, int ls, int sn) {  // bitonic -> ascending inside each segment
+    for (int j = sn >> 1; j > 0; j >>= 1) {
+        const K o = __shfl_xor_sync(FULL, x, j);
+        x = ((ls & j) == 0) ? kmin(x, o) : kmax(x, o);
+    }
+    return x;
+}
+
+__device__ __forceinline__ int seg_excl_scan(int v, int ls, int sn) {
+    int x = v;
+    for (int d = 1; d < sn; d <<= 1) {
+        const int o = __shfl_up_sync(FULL, x, d);
+        if (ls >= d) x += o;
+    }
+    return x - v;
+}
+
+template <typename K>
+__device__ __forceinline__ K seg_max(K x, int sn) {
+    for (int m = sn >> 1; m > 0; m >>= 1) x = kmax(x, __shfl_xor_sync(FULL, x, m));
+    return x;
+}
+template <typename K>
+__device__ __forceinline__ K seg_min(K x, int sn) {
+    for (int m = sn >> 1; m > 0; m >>= 1) x = kmin(x, __shfl_xor_sync(FULL, x, m));
+    return x;
+}
+
+// warp_kth for segments of sn = L lanes (tmp: the segment's frame's scratch).
+template <typename K>
+__device__ __forceinline__ K warp_kth_seg(const K (&k)[8], int C, int L, int La, int sb, int ls, K *tmp) {
+    const int sn = L;
+    if (C >= 4 && La == L) {
+        const K t0 = seg_max<K>(k[0], sn);
+        int t = 0;
+#pragma unroll
+        for (int r = 1; r < 8; ++r) t += k[r] < t0 ? 1 : 0;
+        const int base = seg_excl_scan(t, ls, sn);
+        const int tot = __shfl_sync(FULL, base + t, sb + sn - 1);
+        int tmax = tot;
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) tmax = max(tmax, __shfl_xor_sync(FULL, tmax, m));
+        if (tmax == 0) return t0;
+        if (tmax <= 3 && tmax <= sn) {      // one extra key per lane of the segment
+            if (t > 0) {
+#pragma unroll
+                for (int r = 1; r < 8; ++r)
+                    if (r <= t) tmp[base + r - 1] = k[r];
+            }
+            __syncwarp();
+            K c0 = k[0];
+            K c1 = ls < tot ? tmp[ls] : (K)0;
+            __syncwarp();
+            K res = t0;
+            for (int r = 0; r <= tmax; ++r) {
+                const K m = seg_max<K>(kmax(c0, c1), sn);
+                if (r == tot) res = m;
+                if (c0 == m) c0 = (K)0;
+                else if (c1 == m) c1 = (K)0;
+            }
+            return res;
+        }
+        if (tmax <= L) {
+#pragma unroll
+            for (int r = 1; r < 8; ++r)
+                if (r <= t) tmp[base + r - 1] = k[r];
+            __syncwarp();
+            K y = ls < tot ? tmp[ls] : ~(K)0;
+            __syncwarp();
+            K B = bsort_seg(k[0], ls, sn);
+            y = bsort_seg(y, ls, sn);
+            y = __shfl_sync(FULL, y, sb + sn - 1 - ls);      // descending
+            B = bmerge_seg(kmin(B, y), ls, sn);
+            return __shfl_sync(FULL, B, sb + L - 1);
+        }
+    }
+    K B = bsort_seg(k[0], ls, sn);
+    K tau = __shfl_sync(FULL, B, sb + L - 1);
+    K q[7];
+#pragma unroll
+    for (int r = 0; r < 7; ++r) q[r] = k[r + 1];
+#pragma unroll 1
+    for (int r = 1; r < C; ++r) {
+        K col = q[0];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) q[t] = q[t + 1];
+        const K mn = seg_min<K>(col, sn);
+        // a column above every segment's threshold changes no segment (merging it
+        // into one below its threshold would not either)
+        if (__all_sync(FULL, mn > tau)) break;
+        col = bsort_seg(col, ls, sn);
+        col = __shfl_sync(FULL, col, sb + sn - 1 - ls);      // descending
+        B = bmerge_seg(kmin(B, col), ls, sn);
+        tau = __shfl_sync(FULL, B, sb + L - 1);
+    }
+    return tau;
+}
+
+template <typename KT>
+__device__ __noinline__ KT select_keys_seg(KT k0, KT k1, KT k2, KT k3, KT k4, KT k5, KT k6, KT k7, int C, int nc,
+                                           int L, int sb, int ls, KT *tab) {
+    const KT KINF = (KT)~(KT)0;
+    KT k[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
+    const KT tau = (nc > L) ? warp_kth_seg(k, C, L, nc / C, sb, ls, tab) : KINF;
+    const uint32_t cm = (uint32_t)(C - 1);
+    uint32_t sm = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        if (k[r] != KINF && k[r] <= tau) sm |= 1u << ((uint32_t)k[r] & cm);
+    const int base = seg_excl_scan(__popc(sm), ls, L);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (k[r] != KINF && k[r] <= tau) tab[base + __popc(sm & ((1u << ((uint32_t)k[r] & cm)) - 1u))] = k[r];
+    }
+    __syncwarp();
+    const int La2 = nc < L ? nc : L;
+    return ls < La2 ? tab[ls] : (KT)0;
+}
+
 // ---- register-resident subtrees (OP_SUB) ----------------------------------
 // A subtree of at most 16 bits runs on warp 0, lane s = path s. The alpha of
 // stage j (j <= 4) lives in registers a[(1 << j) - 1 ...], left-child betas in
@@ -412,6 +552,7 @@ template <typename T>
 struct SubCtx {
     typename Arith<T>::K *tab;     // survivor keys in new-slot order (shared memory)
     int lane, La, L;
+    bool live;                     // the lane's segment holds a frame (segmented mode)
 };
 
 struct Desc {
@@ -447,7 +588,7 @@ __device__ __noinline__ KT select_keys(KT k0, KT k1, KT k2, KT k3, KT k4, KT k5,
     return lane < La2 ? tab[lane] : (KT)0;
 }
 
-template <typename T, int J>
+template <typename T, int J, bool SEGD>
 __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, SubCtx<T> &cx) {
     typedef typename Arith<T>::P P;
     typedef typename Arith<T>::K KT;
@@ -456,7 +597,11 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
     constexpr int o = aoff<J>();
     constexpr uint32_t wmask = (nv >= 32) ? 0xffffffffu : ((1u << nv) - 1u);
     const int lane = cx.lane;
-    const bool act = lane < cx.La;
+    // path index inside the frame and first lane of the frame (packed frames: segments of L lanes)
+    const int ls = SEGD ? (lane & (cx.L - 1)) : lane;
+    const int sb = SEGD ? (lane & ~(cx.L - 1)) : 0;
+    const bool live = SEGD ? cx.live : true;
+    const bool act = live && ls < cx.La;
     if (type == OP_R0) {
         // Rate-0 (Sec. III-B): penalty += sum |min(a, 0)| (pairwise tree), beta = 0.
         P x[nv];
@@ -479,7 +624,7 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
     for (int c = 0; c < 8; ++c) k[c] = KINF;
     uint32_t mpos = 0, flag = 0;
     int C, lc;
-    const int s = lane;
+    const int s = ls;
     const P ps = st.pen;
     // a leaf of one bit is Rate-0 or Rate-1; SPC needs at least four bits
     if (J >= 1 && type == OP_REP) {
@@ -572,11 +717,12 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
         for (int c = 0; c < 8; ++c) k[c] = KINF;
     }
     const int nc = cx.La * C;
-    const KT kt = select_keys<KT>(k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], C, nc, cx.L, lane, cx.tab);
+    const KT kt = SEGD ? select_keys_seg<KT>(k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], C, nc, cx.L, sb, ls, cx.tab)
+                       : select_keys<KT>(k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], C, nc, cx.L, lane, cx.tab);
     const int La2 = nc < cx.L ? nc : cx.L;
-    const bool act2 = lane < La2;
+    const bool act2 = live && ls < La2;
     const uint32_t ci = Arith<T>::kidx(kt);
-    const int src = act2 ? (int)(ci >> lc) : 0;
+    const int src = sb + (act2 ? (int)(ci >> lc) : 0);
     const int c = (int)(ci & (uint32_t)(C - 1));
     const uint32_t hd_s = __shfl_sync(FULL, hd, src);
     const uint32_t mp_s = __shfl_sync(FULL, mpos, src);
@@ -602,11 +748,11 @@ __device__ __forceinline__ void sub_leaf(uint32_t type, Sub<T> &st, int side, Su
     __syncwarp();
 }
 
-template <typename T, int J>
+template <typename T, int J, bool SEGD>
 __device__ __forceinline__ void sub_node(Sub<T> &st, Desc &d, int side, SubCtx<T> &cx) {
     const uint32_t type = d.next();
     if (J == 0 || type != 0u) {
-        sub_leaf<T, J>(type, st, side, cx);
+        sub_leaf<T, J, SEGD>(type, st, side, cx);
         return;
     }
     if constexpr (J > 0) {
@@ -622,7 +768,7 @@ __device__ __forceinline__ void sub_node(Sub<T> &st, Desc &d, int side, SubCtx<T
                     st.a[aoff<J - 1>() + i] =
                         gv(st.a[aoff<J>() + i], st.a[aoff<J>() + i + h], (st.bl[J - 1] >> i) & 1u);
             }
-            sub_node<T, J - 1>(st, d, sd, cx);
+            sub_node<T, J - 1, SEGD>(st, d, sd, cx);
         }
         constexpr uint32_t m = (1u << h) - 1u;
         const uint32_t v = ((st.bl[J - 1] ^ st.br) & m) | ((st.br & m) << h);
@@ -632,22 +778,32 @@ __device__ __forceinline__ void sub_node(Sub<T> &st, Desc &d, int side, SubCtx<T
 
 // ---- run one register subtree -------------------------------------------
 // Warp 0: load the paths' alpha rows of stage JR, walk the subtree, then write
-// the root's beta, penalties and index rows.
-template <typename T, int JR>
+// the root's beta, penalties and index rows. With SEGD the warp holds
+// 32 / L frames of L paths each (lane f * L + s = path s of frame f, whose
+// memory starts sstride bytes of shared memory and gstride bytes of scratch
+// after frame f - 1's).
+template <typename T, int JR, bool SEGD>
 __device__ __forceinline__ void run_sub(const CodeView &cv, uint8_t *S, uint8_t *Gs, uint32_t op, int La, int cur,
-                                        int lane) {
+                                        int lane, int P = 1, uint32_t sstride = 0, uint64_t gstride = 0) {
     typedef typename Arith<T>::P PT;
     typedef typename Arith<T>::K KT;
     const Layout &lay = cv.lay;
+    const int me = SEGD ? (lane & (cv.L - 1)) : lane;           // path index inside the frame
+    const int fseg = SEGD ? lane / cv.L : 0;                     // the lane's frame (segment)
+    const bool live = fseg < P;                                  // segments past the P frames idle
+    if (SEGD && live) {
+        S += (size_t)fseg * sstride;
+        if (Gs) Gs += (size_t)fseg * gstride;
+    }
     const int n = cv.n;
     const int dest = op_dest(op);
     uint8_t *idxc = S + lay.idx[cur];
     uint8_t *bidxc = S + lay.bidx[cur];
     PT *penc = reinterpret_cast<PT *>(S + lay.pen[cur]);
     Sub<T> st;
-    const bool act = lane < La;
+    const bool act = live && me < La;
     const T *row = (JR == n) ? chan_ptr<T>(lay, S, Gs)
-                             : alpha_ptr<T>(lay, S, Gs, JR) + ((int)idxc[(act ? lane : 0) * 16 + JR] << JR);
+                             : alpha_ptr<T>(lay, S, Gs, JR) + ((int)idxc[(act ? me : 0) * 16 + JR] << JR);
     constexpr int o = aoff<JR>();
 #pragma unroll
     for (int i = 0; i < 31; ++i) st.a[i] = 0;
@@ -668,14 +824,14 @@ __device__ __forceinline__ void run_sub(const CodeView &cv, uint8_t *S, uint8_t 
                 st.a[o + 4 * q + 3] = (int)(int8_t)(v >> 24);
             }
         }
-        st.pen = penc[lane];
+        st.pen = penc[me];
     } else {
         st.pen = (PT)0;
     }
 #pragma unroll
     for (int jj = 0; jj < 5; ++jj) st.bl[jj] = 0u;
     st.br = 0u;
-    st.orig = lane;
+    st.orig = me;
     const uint32_t di = op_sub_desc(op);
     Desc d;
     d.w0 = __ldg(cv.desc + 2 * di);
@@ -686,8 +842,9 @@ __device__ __forceinline__ void run_sub(const CodeView &cv, uint8_t *S, uint8_t 
     cx.lane = lane;
     cx.La = La;
     cx.L = cv.L;
-    sub_node<T, JR>(st, d, dest, cx);
-    const bool act2 = lane < cx.La;
+    cx.live = live;
+    sub_node<T, JR, SEGD>(st, d, dest, cx);
+    const bool act2 = live && me < cx.La;
     const uint32_t beta = dest ? st.br : st.bl[JR];
     uint32_t *bout = dest ? br_ptr(lay, S, Gs) : bl_ptr(lay, S, Gs, JR);
     const int ostride = dest ? beta_words(n) : beta_words(JR);
@@ -696,15 +853,15 @@ __device__ __forceinline__ void run_sub(const CodeView &cv, uint8_t *S, uint8_t 
             const int nxt = cur ^ 1;
             uint8_t *idxn = S + lay.idx[nxt];
             uint8_t *bidxn = S + lay.bidx[nxt];
-            reinterpret_cast<PT *>(S + lay.pen[nxt])[lane] = st.pen;
-            reinterpret_cast<uint4 *>(idxn)[lane] = reinterpret_cast<const uint4 *>(idxc)[st.orig];
-            reinterpret_cast<uint4 *>(bidxn)[lane] = reinterpret_cast<const uint4 *>(bidxc)[st.orig];
-            if (!dest) bidxn[lane * 16 + JR] = (uint8_t)lane;
+            reinterpret_cast<PT *>(S + lay.pen[nxt])[me] = st.pen;
+            reinterpret_cast<uint4 *>(idxn)[me] = reinterpret_cast<const uint4 *>(idxc)[st.orig];
+            reinterpret_cast<uint4 *>(bidxn)[me] = reinterpret_cast<const uint4 *>(bidxc)[st.orig];
+            if (!dest) bidxn[me * 16 + JR] = (uint8_t)me;
         } else {
-            penc[lane] = st.pen;
-            if (!dest) bidxc[lane * 16 + JR] = (uint8_t)lane;
+            penc[me] = st.pen;
+            if (!dest) bidxc[me * 16 + JR] = (uint8_t)me;
         }
-        bout[lane * ostride] = beta;
+        bout[me * ostride] = beta;
     }
 }
 
@@ -743,13 +900,20 @@ __device__ __forceinline__ void node32_in(const T *row, Sub<T> &st, int side) {
     }
 }
 
-template <typename T>
+template <typename T, bool SEGD>
 __device__ __forceinline__ void run_sub32(const CodeView &cv, uint8_t *S, uint8_t *Gs, uint32_t op, int La, int cur,
-                                          int lane) {
+                                          int lane, int P = 1, uint32_t sstride = 0, uint64_t gstride = 0) {
     typedef typename Arith<T>::P PT;
     typedef typename Arith<T>::K KT;
     constexpr int JN = kSubLog + 1;
     const Layout &lay = cv.lay;
+    const int me = SEGD ? (lane & (cv.L - 1)) : lane;           // path index inside the frame
+    const int fseg = SEGD ? lane / cv.L : 0;                     // the lane's frame (segment)
+    const bool live = fseg < P;                                  // segments past the P frames idle
+    if (SEGD && live) {
+        S += (size_t)fseg * sstride;
+        if (Gs) Gs += (size_t)fseg * gstride;
+    }
     const int n = cv.n;
     const int dest = op_dest(op);
     uint8_t *idxc = S + lay.idx[cur];
@@ -759,27 +923,28 @@ __device__ __forceinline__ void run_sub32(const CodeView &cv, uint8_t *S, uint8_
     Sub<T> st;
 #pragma unroll
     for (int i = 0; i < 31; ++i) st.a[i] = 0;
-    st.pen = lane < La ? penc[lane] : (PT)0;
+    st.pen = (live && me < La) ? penc[me] : (PT)0;
 #pragma unroll
     for (int jj = 0; jj < 5; ++jj) st.bl[jj] = 0u;
     st.br = 0u;
-    st.orig = lane;
+    st.orig = me;
     SubCtx<T> cx;
     cx.tab = reinterpret_cast<KT *>(S + lay.surv);
     cx.lane = lane;
     cx.La = La;
     cx.L = cv.L;
+    cx.live = live;
     const uint32_t di = op_sub_desc(op);
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
-        if (lane < cx.La) node32_in<T>(stj + ((int)idxc[st.orig * 16 + JN] << JN), st, side);
+        if (live && me < cx.La) node32_in<T>(stj + ((int)idxc[st.orig * 16 + JN] << JN), st, side);
         Desc d;
         d.w0 = __ldg(cv.desc + 2 * (di + side));
         d.w1 = __ldg(cv.desc + 2 * (di + side) + 1);
         d.pos = 0;
-        sub_node<T, kSubLog>(st, d, side, cx);
+        sub_node<T, kSubLog, SEGD>(st, d, side, cx);
     }
-    const bool act2 = lane < cx.La;
+    const bool act2 = live && me < cx.La;
     const uint32_t beta = ((st.bl[kSubLog] ^ st.br) & 0xFFFFu) | ((st.br & 0xFFFFu) << 16);
     uint32_t *bout = dest ? br_ptr(lay, S, Gs) : bl_ptr(lay, S, Gs, JN);
     const int ostride = dest ? beta_words(n) : beta_words(JN);
@@ -788,15 +953,15 @@ __device__ __forceinline__ void run_sub32(const CodeView &cv, uint8_t *S, uint8_
             const int nxt = cur ^ 1;
             uint8_t *idxn = S + lay.idx[nxt];
             uint8_t *bidxn = S + lay.bidx[nxt];
-            reinterpret_cast<PT *>(S + lay.pen[nxt])[lane] = st.pen;
-            reinterpret_cast<uint4 *>(idxn)[lane] = reinterpret_cast<const uint4 *>(idxc)[st.orig];
-            reinterpret_cast<uint4 *>(bidxn)[lane] = reinterpret_cast<const uint4 *>(bidxc)[st.orig];
-            if (!dest) bidxn[lane * 16 + JN] = (uint8_t)lane;
+            reinterpret_cast<PT *>(S + lay.pen[nxt])[me] = st.pen;
+            reinterpret_cast<uint4 *>(idxn)[me] = reinterpret_cast<const uint4 *>(idxc)[st.orig];
+            reinterpret_cast<uint4 *>(bidxn)[me] = reinterpret_cast<const uint4 *>(bidxc)[st.orig];
+            if (!dest) bidxn[me * 16 + JN] = (uint8_t)me;
         } else {
-            penc[lane] = st.pen;
-            if (!dest) bidxc[lane * 16 + JN] = (uint8_t)lane;
+            penc[me] = st.pen;
+            if (!dest) bidxc[me * 16 + JN] = (uint8_t)me;
         }
-        bout[lane * ostride] = beta;
+        bout[me * ostride] = beta;
     }
 }
 
@@ -1047,15 +1212,19 @@ __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t
 #pragma unroll
         for (int c = 0; c < 8; ++c) k[c] = KINF;
     }
-    // selection (Algorithm 1)
+    // selection (Algorithm 1); with L <= 16 inside an L-lane segment (shorter
+    // sorting networks; the lanes past L hold no keys)
     const int nc = La * C;
     KT *tab = reinterpret_cast<KT *>(S + lay.surv);
-    const KT tau = (nc > L) ? warp_kth(k, C, L, La, lane, tab) : KINF;
+    const bool seg = L <= 16;
+    const int ls = lane & (L - 1);
+    const KT tau = (nc > L) ? (seg ? warp_kth_seg(k, C, L, La, lane & ~(L - 1), ls, tab) : warp_kth(k, C, L, La, lane, tab))
+                            : KINF;
     uint32_t sm = 0;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
         if (k[r] != KINF && k[r] <= tau) sm |= 1u << (Arith<T>::kidx(k[r]) & (uint32_t)(C - 1));
-    const int base = warp_excl_scan(__popc(sm), lane);
+    const int base = seg ? seg_excl_scan(__popc(sm), ls, L) : warp_excl_scan(__popc(sm), lane);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         if (k[r] != KINF && k[r] <= tau) {
@@ -1108,13 +1277,17 @@ __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t
 template <typename T, int W>
 __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uint8_t *Gs, const uint8_t *src,
                                              uint8_t *bits_row, float *pm_out, uint8_t *ok_out, int32_t *slot_out,
-                                             int gidx, int gtid, bool lockstep) {
+                                             int gidx, int gtid, bool lockstep, uint32_t sstride, uint64_t gstride,
+                                             int gpc) {
     typedef typename Arith<T>::P PT;
     constexpr int GT = W * 32;
     const Layout &lay = cv.lay;
     const int lane = gtid & 31;
     const int wig = gtid >> 5;
     const int n = cv.n, N = cv.N, L = cv.L;
+    // register subtrees of several frames in one warp (lockstep rounds, one warp
+    // per frame, L <= 16, and 32 / L frame groups to a CTA)
+    const bool pack = cv.pack && W == 1 && lockstep && L <= 16 && 32 / L <= gpc;
     const int bwn = beta_words(n);
     T *chan = chan_ptr<T>(lay, S, Gs);
     uint32_t *br = br_ptr(lay, S, Gs);
@@ -1292,10 +1465,27 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
             }
         } else if (kind == OP_SUB) {
             // ---------------- a small subtree in registers (warp 0) ----------------
-            if (wig == 0) {
-                if (j == kSubLog) run_sub<T, 4>(cv, S, Gs, op, La, cur, lane);
-                else if (j == kSubLog + 1) run_sub32<T>(cv, S, Gs, op, La, cur, lane);
-                else run_sub<T, 3>(cv, S, Gs, op, La, cur, lane);
+            if (pack) {
+                // L <= 16 in lockstep: the first warp of every run of P = 32 / L
+                // groups runs the subtree for all P frames, L lanes each, and
+                // the others wait at the CTA barrier below
+                if ((gidx & (32 / L - 1)) == 0) {
+                    const int P = 32 / L;
+                    if (j == kSubLog) run_sub<T, 4, true>(cv, S, Gs, op, La, cur, lane, P, sstride, gstride);
+                    else if (j == kSubLog + 1) run_sub32<T, true>(cv, S, Gs, op, La, cur, lane, P, sstride, gstride);
+                    else run_sub<T, 3, true>(cv, S, Gs, op, La, cur, lane, P, sstride, gstride);
+                }
+                asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
+            } else if (wig == 0 && L <= 16) {
+                // one frame, its selection in an L-lane segment (shorter sorting
+                // networks); the other lanes idle
+                if (j == kSubLog) run_sub<T, 4, true>(cv, S, Gs, op, La, cur, lane);
+                else if (j == kSubLog + 1) run_sub32<T, true>(cv, S, Gs, op, La, cur, lane);
+                else run_sub<T, 3, true>(cv, S, Gs, op, La, cur, lane);
+            } else if (wig == 0) {
+                if (j == kSubLog) run_sub<T, 4, false>(cv, S, Gs, op, La, cur, lane);
+                else if (j == kSubLog + 1) run_sub32<T, false>(cv, S, Gs, op, La, cur, lane);
+                else run_sub<T, 3, false>(cv, S, Gs, op, La, cur, lane);
             }
             const int lm = op_sub_logmult(op);
             La = (lm >= 6 || (La << lm) > L) ? L : (La << lm);
@@ -1429,7 +1619,8 @@ __global__ void __launch_bounds__(kMaxCtaThreads) decode_kernel(const Params P) 
         const bool full = P.groups_per_cta > 1 && (i - (uint32_t)gidx) + (uint32_t)P.groups_per_cta <= nf;
         decode_frame<T, W>(P.cv, S, Gs, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
                            P.bits + (size_t)f * P.cv.kb, P.pm + f, P.ok ? P.ok + f : nullptr,
-                           P.slot ? P.slot + f : nullptr, gidx, gtid, full);
+                           P.slot ? P.slot + f : nullptr, gidx, gtid, full, P.cv.lay.bytes, P.cv.lay.gbytes,
+                           P.groups_per_cta);
     }
 }
 
@@ -1493,7 +1684,7 @@ __global__ void __launch_bounds__(kMaxCtaThreads) batch_kernel(const BatchParams
         }
         decode_frame<T, W>(*cvs, S, Gs, B.llr + item.llr_off, B.bits + item.bits_off, B.pm + item.frame,
                            B.ok ? B.ok + item.frame : nullptr, B.slot ? B.slot + item.frame : nullptr, gidx, gtid,
-                           lock);
+                           lock, B.group_bytes, B.gbytes, B.groups_per_cta);
     }
 }
 

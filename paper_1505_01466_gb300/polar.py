@@ -25,7 +25,7 @@ INJECT_ALLOC_FAIL, INJECT_POISON = 1, 2
 EXPORTED = [
     "polar_code_create", "polar_code_destroy", "polar_list_decode", "polar_strerror", "polar_sync",
     "polar_code_get_info", "polar_code_schedule", "polar_code_op_count", "polar_code_set_launch",
-    "polar_code_set_recompute", "polar_code_set_smem_budget",
+    "polar_code_set_recompute", "polar_code_set_smem_budget", "polar_code_set_packing",
     "polar_code_autotune", "polar_list_decode_noalloc", "polar_noalloc_scratch_bytes",
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
@@ -112,6 +112,7 @@ def _lib():
         lib.polar_code_op_count.argtypes = [vp, ctypes.POINTER(u64)]
         lib.polar_code_set_launch.argtypes = [vp, i32, u32, u32, u32]
         lib.polar_code_set_recompute.argtypes = [vp, i32, u32]
+        lib.polar_code_set_packing.argtypes = [vp, i32, i32]
         lib.polar_code_set_smem_budget.argtypes = [vp, i32, u32]
         lib.polar_code_autotune.argtypes = [vp, i32, vp, u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32),
                                              ctypes.POINTER(u32)]
@@ -242,6 +243,10 @@ class PolarCode:
     def set_smem_budget(self, dtype: int, smem_per_warp: int):
         """Shared memory of the L = 1 kernel (per warp of 32 frames) or of a wide code (per CTA)."""
         _check(_lib().polar_code_set_smem_budget(self._h, dtype, smem_per_warp), "polar_code_set_smem_budget")
+
+    def set_packing(self, dtype: int, on: bool):
+        """L <= 16: register subtrees of 32 / L frames in one warp (lockstep rounds)."""
+        _check(_lib().polar_code_set_packing(self._h, dtype, 1 if on else 0), "polar_code_set_packing")
 
     def set_recompute(self, dtype: int, depth: int):
         """Evaluate the top ``depth`` alpha stages from the channel instead of storing them."""

@@ -277,3 +277,23 @@ def test_recomputed_stages_leave_the_layout(polar):
     half[:512] = 1                                                 # left half Rate-0, right half Rate-1
     c2 = polar.PolarCode(half, 0, 0, 8, host_only=True)
     assert c2.info()["max_recompute_depth"] == 0 and c2.info()["recomputed_stages"] == [0, 0]
+
+
+def test_packing_needs_a_packable_shape(polar):
+    fr = I.ga_frozen_mask(1024, 860, 4.0, 828 / 1024)
+    c8 = polar.PolarCode(fr, 32, I.CRC32_POLY, 8, host_only=True)
+    c8.set_launch(0, 1, 7000, 128)                 # 4 frame groups per CTA: 32 / 8 = 4 frames to a warp
+    c8.set_packing(0, True)
+    c8.set_packing(0, False)
+    c8.set_launch(0, 2, 7000, 128)                 # two warps per frame: no packing
+    with pytest.raises(polar.PolarError):
+        c8.set_packing(0, True)
+    c4 = polar.PolarCode(fr, 32, I.CRC32_POLY, 4, host_only=True)
+    c4.set_launch(1, 1, 7000, 128)                 # 8 frames to a warp need 8 groups per CTA
+    with pytest.raises(polar.PolarError):
+        c4.set_packing(1, True)
+    c4.set_launch(1, 1, 7000, 256)
+    c4.set_packing(1, True)
+    c32 = polar.PolarCode(fr, 32, I.CRC32_POLY, 32, host_only=True)
+    with pytest.raises(polar.PolarError):
+        c32.set_packing(0, True)
