@@ -166,6 +166,7 @@ typedef struct {
     uint32_t spill_mask[2];          /* alpha stages kept in global scratch */
     uint32_t recomputed_stages[2];   /* alpha stages not stored: evaluated from the channel */
     uint32_t max_recompute_depth;    /* how many top stages may be (see polar_code_set_recompute) */
+    uint32_t packed[2];              /* 1: the shape packs register subtrees (polar_code_set_packing) */
 } polar_code_info_t;
 
 /* Fill *info (host memory, caller-owned). Errors: POLAR_EINVAL (NULL). */
@@ -220,12 +221,17 @@ POLAR_API int polar_code_set_smem_budget(polar_code_t *code, int llr_dtype, uint
 /* List sizes L <= 16 with one warp per frame: in rounds where every frame
  * group of a CTA holds a frame, run the register subtrees (Sec. III leaves of
  * up to 32 bits and their selection, Algorithm 1) of 32 / L frames in one
- * warp, L lanes each, while the other warps of those frames wait (on != 0),
- * or each frame in its own warp (on = 0, the default). Either way the
- * selection of a frame sorts and scans inside its own L lanes. Needs a shape
- * with one warp per frame and at least 32 / L frames per CTA; keeps the rest
- * of the current shape; polar_code_autotune also tries it. Results do not
- * depend on it. Errors: POLAR_EINVAL (bad arguments or shape),
+ * warp, L lanes each, while the other warps of those frames wait, and sort
+ * and scan each frame's selection inside its own L lanes (on != 0); or run
+ * each frame in its own warp with lane-per-path selection over the whole warp
+ * (on = 0). Default: on for L <= 4, off for L = 8 and 16 (measured faster
+ * each way). The choice is kept per LLR type: later shapes from
+ * polar_code_set_launch use it where they allow it (one warp per frame), and
+ * the batched and serving forms follow the code's choice for its frames.
+ * Turning it on needs a shape with one warp per frame and at least 32 / L
+ * frames per CTA; the rest of the current shape is kept. polar_code_autotune
+ * and polar_batch_autotune (all classes on or off) try both settings. Results
+ * do not depend on it. Errors: POLAR_EINVAL (bad arguments or shape),
  * POLAR_EUNSUPPORTED (a wide code), POLAR_ENOMEM / POLAR_ECUDA (uploading the
  * schedule). */
 POLAR_API int polar_code_set_packing(polar_code_t *code, int llr_dtype, int on);

@@ -1,9 +1,10 @@
 """Build ``libpolar_gb300.so`` in-tree with nvcc for sm_103a.
 
-The four translation units (host runtime, list kernels, wide-list kernel and the L = 1
-kernel) compile in parallel and
-are linked into one shared library next to this file. No CMake, no torch
-extension machinery: the library has a plain C ABI (include/polar.h).
+Seven objects compile in parallel: the host runtime, the list kernels in four
+parts (float / int8 x plain / batched form, one source compiled with
+-DPOLAR_KPART=0..3), the wide-list kernel and the L = 1 kernel. They are linked
+into one shared library next to this file. No CMake, no torch extension
+machinery: the library has a plain C ABI (include/polar.h).
 """
 from __future__ import annotations
 
@@ -15,6 +16,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpolar_gb300.so")
 SOURCES = ["polar_capi.cu", "polar_kernels.cu", "polar_wide.cu", "polar_sc1.cu"]
+# (source, object, extra flags): the list kernels compile once per part
+UNITS = [("polar_capi.cu", "polar_capi.o", []),
+         *[("polar_kernels.cu", f"polar_kernels_p{p}.o", [f"-DPOLAR_KPART={p}", "-diag-suppress", "177"])
+           for p in range(4)],   # a part leaves the other parts' helpers unused
+         ("polar_wide.cu", "polar_wide.o", []),
+         ("polar_sc1.cu", "polar_sc1.o", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -36,9 +43,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
     procs, objs = [], []
-    for src in SOURCES:
-        obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    for src, o, extra in UNITS:
+        obj = os.path.join(bdir, o)
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((subprocess.Popen(cmd), src))

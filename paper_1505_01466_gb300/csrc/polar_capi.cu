@@ -38,6 +38,11 @@ using namespace polar;
 // Measured at (1024, k=828) L = 128, every byte moved on chip costs more in
 // CTAs per SM than it saves (0.34 M frames/s with none, 0.23 M with 48 KB).
 constexpr uint32_t kWideDefaultBudget = 0u;
+// Codes with at most this many paths pack their register subtrees (several
+// frames to a warp, selection in L-lane segments) unless told otherwise:
+// measured faster at L = 2 and 4 and slower at L = 8 and 16, where a frame's
+// lane-per-path code on its own warp wins.
+constexpr uint32_t kPackDefaultMaxL = 4u;
 
 struct polar_code {
     uint32_t N, n, K, k, L, crc_len, flags;
@@ -80,7 +85,16 @@ struct polar_code {
     // each LLR type.
     uint32_t vmax = 0;
     uint32_t vdepth[2] = {0, 0};
+    // Pack register subtrees (L <= 16) wherever the launch shape allows it
+    // (one warp per frame), per LLR type: the plain, batched and serving forms
+    // follow it; set_packing and the autotuner change it.
+    bool pack_pref[2] = {false, false};
 };
+
+// Whether a shape of `warps` warps per frame runs the packed design.
+bool packs(const polar_code *c, int dtype, uint32_t warps) {
+    return warps == 1 && c->L <= 16 && c->pack_pref[dtype];
+}
 
 namespace {
 
@@ -119,14 +133,14 @@ cudaError_t launch_decode_locked(int dtype, const LaunchShape &sh, const Params 
     std::lock_guard<std::mutex> lk(g_launch_mu);
     return launch_decode(dtype, sh, p, grid, st);
 }
-int occupancy_batch_locked(int dtype, int warps, uint32_t smem, int threads) {
+int occupancy_batch_locked(int dtype, int warps, bool seg, uint32_t smem, int threads) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
-    return occupancy_batch(dtype, warps, smem, threads);
+    return occupancy_batch(dtype, warps, seg, smem, threads);
 }
-cudaError_t launch_batch_locked(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
-                                cudaStream_t st) {
+cudaError_t launch_batch_locked(int dtype, int warps, bool seg, const BatchParams &b, int grid, uint32_t smem,
+                                int threads, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
-    return launch_batch(dtype, warps, b, grid, smem, threads, st);
+    return launch_batch(dtype, warps, seg, b, grid, smem, threads, st);
 }
 int occupancy_sc1_locked(int dtype, uint32_t warp_bytes, int warps) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
@@ -393,7 +407,7 @@ bool make_shape(const polar_code *c, int dtype, uint32_t warps, uint32_t budget,
     if (!build_layout(c->n, c->L, es, budget, lay, virt_mask_of(c->n, vd))) return false;
     sh.d_ops = nullptr;
     sh.budget = budget;
-    sh.pack = 0;
+    sh.pack = packs(c, dtype, warps) ? 1 : 0;
     sh.warps = (int)warps;
     sh.groups_per_cta = (int)gpc;
     sh.threads = (int)cta_threads;
@@ -783,6 +797,7 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
     }
     // stored by default: measured, evaluating them costs more than it saves
     for (int d = 0; d < 2; ++d) c->vdepth[d] = 0;
+    for (int d = 0; d < 2; ++d) c->pack_pref[d] = L <= kPackDefaultMaxL;
     c->n_leaves = tb.leaves;
     c->n_r0 = tb.r0;
     c->n_r1 = tb.r1;
@@ -1151,7 +1166,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     // 32 / L frame groups to a CTA) on the best shape
     if (status == POLAR_OK && best_w == 1 && code->L <= 16 && (uint32_t)(32 / code->L) <= best_t / 32) {
         LaunchShape sh = best;
-        sh.pack = 1;
+        sh.pack = best.pack ^ 1;
         std::vector<uint32_t> fl = flag_ops(code->ops, 1);
         if (upload(&sh.d_ops, fl) == cudaSuccess) {
             float ms = 0.f;
@@ -1168,6 +1183,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
             if (rc == POLAR_OK && ms < best_ms) { best_ms = ms; best = sh; }
         }
     }
+    if (status == POLAR_OK && best_w == 1 && code->L <= 16) code->pack_pref[llr_dtype] = best.pack != 0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(bits);
@@ -1281,6 +1297,8 @@ struct polar_batch {
     uint32_t group_bytes = 0, view_bytes = 0, cta_smem = 0;
     uint64_t gbytes = 0;
     int grid = 0;
+    int pack = 1;                      // classes follow their codes' packing choice (0: none packs)
+    bool seg = false;                  // some class packs: launch the kernels that hold that code
     // device state
     std::vector<uint32_t *> d_ops;     // per class, flagged for `warps`
     CodeView *d_classes = nullptr;
@@ -1319,12 +1337,15 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget, uint32_t cta_threads
     std::vector<CodeView> views(b->codes.size());
     uint32_t gb = 0;
     uint64_t gs = 0;
+    bool seg = false;
     for (size_t c = 0; c < b->codes.size(); ++c) {
         Layout lay;
         if (!build_layout(b->codes[c]->n, b->codes[c]->L, es, budget, lay)) return POLAR_EINVAL;
         LaunchShape sh;
         std::memset(&sh, 0, sizeof(sh));
         sh.lay = lay;
+        sh.pack = b->pack && packs(b->codes[c], b->dtype, (uint32_t)warps) ? 1 : 0;
+        seg |= sh.pack != 0;
         views[c] = make_view(b->codes[c], sh);
         gb = std::max(gb, lay.bytes);
         gs = std::max<uint64_t>(gs, lay.gbytes);
@@ -1332,7 +1353,7 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget, uint32_t cta_threads
     const uint32_t group_bytes = view_bytes + gb;
     const uint32_t cta_smem = group_bytes * (uint32_t)gpc;
     if (cta_smem > kMaxSmemPerCta) return POLAR_EINVAL;
-    const int occ = occupancy_batch_locked(b->dtype, warps, cta_smem, (int)cta_threads);
+    const int occ = occupancy_batch_locked(b->dtype, warps, seg, cta_smem, (int)cta_threads);
     if (occ <= 0) return POLAR_ECUDA;
     batch_free_shape(b);
     for (size_t c = 0; c < b->codes.size(); ++c) {
@@ -1351,6 +1372,7 @@ int batch_shape(polar_batch *b, int warps, uint32_t budget, uint32_t cta_threads
         if (cudaMalloc(&b->d_scratch, b->scratch_bytes) != cudaSuccess) return POLAR_ENOMEM;
     }
     b->warps = warps;
+    b->seg = seg;
     b->budget = budget;
     b->threads = (int)cta_threads;
     b->groups_per_cta = gpc;
@@ -1382,7 +1404,7 @@ int batch_launch(polar_batch *b, const void *llr, uint8_t *bits, float *pm, uint
     p.group_bytes = b->group_bytes;
     p.view_bytes = b->view_bytes;
     p.groups_per_cta = b->groups_per_cta;
-    const cudaError_t e = launch_batch_locked(b->dtype, b->warps, p, b->grid, b->cta_smem, b->threads, st);
+    const cudaError_t e = launch_batch_locked(b->dtype, b->warps, b->seg, p, b->grid, b->cta_smem, b->threads, st);
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
@@ -1504,6 +1526,22 @@ int polar_batch_autotune(polar_batch_t *b, const void *llr_dev, uint8_t *bits_de
         }
       }
     }
+    // the other packing choice on the best shape
+    if (bw == 1) {
+        const int keep = b->pack;
+        b->pack = keep ^ 1;
+        float ms = 0.f;
+        int rc = batch_shape(b, bw, bb, bt);
+        if (rc == POLAR_OK) rc = batch_launch(b, llr_dev, bits_dev, pm_dev, nullptr, nullptr, st);
+        if (rc == POLAR_OK) {
+            cudaEventRecord(e0, st);
+            rc = batch_launch(b, llr_dev, bits_dev, pm_dev, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = POLAR_ECUDA;
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (rc != POLAR_OK || ms >= best) b->pack = keep;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (bw == 0) return POLAR_ECUDA;
@@ -1588,7 +1626,6 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
             info->smem_per_frame[d] = s1.warp_bytes / 32u;
             info->scratch_per_frame[d] = s1.warp_gbytes / 32u;
             info->spill_mask[d] = ((1u << c->n) - 1u) & ~((1u << s1.split) - 1u);
-            info->smem_per_frame[d] = s1.warp_bytes / 32u;
             continue;
         }
         info->warps_per_frame[d] = (uint32_t)c->shape[d].warps;
@@ -1597,6 +1634,7 @@ int polar_code_get_info(const polar_code_t *c, polar_code_info_t *info) {
         info->scratch_per_frame[d] = c->shape[d].lay.gbytes;
         info->spill_mask[d] = c->shape[d].lay.spill_mask;
         info->recomputed_stages[d] = c->shape[d].lay.virt_mask;
+        info->packed[d] = c->shape[d].pack ? 1u : 0u;
     }
     info->max_recompute_depth = c->vmax;
     return POLAR_OK;
@@ -1662,6 +1700,7 @@ int polar_code_set_packing(polar_code_t *c, int llr_dtype, int on) {
     const bool fixed = c->explicit_shape[llr_dtype];
     const int st = install_shape(c, llr_dtype, sh);
     c->explicit_shape[llr_dtype] = fixed;
+    if (st == POLAR_OK) c->pack_pref[llr_dtype] = on != 0;
     return st;
 }
 
@@ -1769,6 +1808,7 @@ struct polar_server {
     std::vector<const polar_code *> codes;
     std::unordered_map<const polar_code *, uint32_t> code_idx;
     std::vector<uint32_t *> class_ops;
+    std::vector<uint8_t> class_pack[2];       // per class and LLR type: its view packs
     CodeView *d_classes[2] = {nullptr, nullptr};
     uint32_t frame_bytes[2] = {0, 0};         // largest per-frame shared layout
     uint64_t gbytes[2] = {0, 0};              // largest per-frame global scratch
@@ -1817,6 +1857,7 @@ int srv_register(polar_server *s, const polar_code *c, uint32_t &idx) {
         std::memset(&sh, 0, sizeof(sh));
         sh.lay = lay;
         sh.d_ops = ops;
+        sh.pack = packs(c, d, (uint32_t)s->warps) ? 1 : 0;
         CodeView v = make_view(c, sh);
         if (cudaMemcpy(s->d_classes[d] + idx, &v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaFree(ops);
@@ -1827,6 +1868,7 @@ int srv_register(polar_server *s, const polar_code *c, uint32_t &idx) {
     }
     s->codes.push_back(c);
     s->class_ops.push_back(ops);
+    for (int d = 0; d < 2; ++d) s->class_pack[d].push_back(packs(c, d, (uint32_t)s->warps) ? 1 : 0);
     s->code_idx[c] = idx;
     return POLAR_OK;
 }
@@ -1922,7 +1964,9 @@ int srv_launch(polar_server *s, int i) {
     uint32_t group_bytes, cta_smem;
     int gpc;
     srv_shape(s, d, group_bytes, cta_smem, gpc);
-    const int occ = occupancy_batch_locked(d, s->warps, cta_smem, kSrvCtaThreads);
+    bool seg = false;              // some request of the batch packs
+    for (SrvReq *r : take) seg |= s->class_pack[d][s->code_idx[r->code]] != 0;
+    const int occ = occupancy_batch_locked(d, s->warps, seg, cta_smem, kSrvCtaThreads);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t grid = (uint64_t)occ * s->sm_count;
     const uint64_t need = (n_items + gpc - 1) / gpc;
@@ -1951,7 +1995,7 @@ int srv_launch(polar_server *s, int i) {
     p.group_bytes = group_bytes;
     p.view_bytes = srv_view_bytes();
     p.groups_per_cta = gpc;
-    okc &= launch_batch_locked(d, s->warps, p, (int)grid, cta_smem, kSrvCtaThreads, st) == cudaSuccess;
+    okc &= launch_batch_locked(d, s->warps, seg, p, (int)grid, cta_smem, kSrvCtaThreads, st) == cudaSuccess;
     for (SrvReq *r : take) {
         const uint64_t bits_base = r->arena_off + ((r->llr_sz + 255) & ~uint64_t(255));
         okc &= cudaMemcpyAsync(s->h_arena + bits_base, s->d_arena + bits_base, r->bits_sz, cudaMemcpyDeviceToHost,

@@ -100,7 +100,9 @@ struct CodeView {
     int n_ops;
     int N, n, L, K, k, kb, crc_len;
     int systematic;                // payload read from x, not from u = x G_N
-    int pack;                      // L <= 16: run register subtrees 32 / L frames to a warp in lockstep rounds
+    int pack;                      // 1 only where it applies (L <= 16, one warp per frame): run register
+                                   // subtrees 32 / L frames to a warp in lockstep rounds, selection in
+                                   // L-lane segments
     Layout lay;
 };
 
@@ -153,7 +155,7 @@ struct LaunchShape {
     int groups_per_cta;
     int threads;                   // per CTA
     uint32_t smem;                 // dynamic shared memory per CTA
-    int pack;                      // CodeView::pack
+    int pack;                      // CodeView::pack; also picks the kernels that hold the packed code
     Layout lay;
 };
 
@@ -167,9 +169,9 @@ cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n_frames, uint32_t *
                                 cudaStream_t stream);
 // Batched form: CTAs of `threads` threads (groups of `warps` warps) with
 // `smem` bytes of shared memory.
-cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
+cudaError_t launch_batch(int dtype, int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
                          cudaStream_t stream);
-int occupancy_batch(int dtype, int warps, uint32_t smem, int threads);
+int occupancy_batch(int dtype, int warps, bool seg, uint32_t smem, int threads);
 // Wide lists (L = 64, 128): one CTA of L threads per frame over the fully
 // unrolled schedule; every stage in the CTA's global scratch region.
 struct WideView {

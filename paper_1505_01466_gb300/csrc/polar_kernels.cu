@@ -1124,7 +1124,7 @@ __device__ __forceinline__ uint32_t hd_word(const T *p) {
     return w;
 }
 
-template <typename T>
+template <typename T, bool SEG>
 __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t *Gs, uint32_t kind, int j, int dest,
                                          int La, int cur, int lane) {
     typedef typename Arith<T>::P PT;
@@ -1212,11 +1212,11 @@ __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t
 #pragma unroll
         for (int c = 0; c < 8; ++c) k[c] = KINF;
     }
-    // selection (Algorithm 1); with L <= 16 inside an L-lane segment (shorter
-    // sorting networks; the lanes past L hold no keys)
+    // selection (Algorithm 1); for codes that pack (L <= 16) inside an L-lane
+    // segment (shorter sorting networks; the lanes past L hold no keys)
     const int nc = La * C;
     KT *tab = reinterpret_cast<KT *>(S + lay.surv);
-    const bool seg = L <= 16;
+    const bool seg = SEG && cv.pack;
     const int ls = lane & (L - 1);
     const KT tau = (nc > L) ? (seg ? warp_kth_seg(k, C, L, La, lane & ~(L - 1), ls, tab) : warp_kth(k, C, L, La, lane, tab))
                             : KINF;
@@ -1274,7 +1274,7 @@ __device__ __forceinline__ void big_leaf(const CodeView &cv, uint8_t *S, uint8_t
 // ---------------------------------------------------------------------------
 // Decode one frame: channel row -> payload bits, penalty, CRC flag, slot.
 // Called by all W*32 threads of one frame group.
-template <typename T, int W>
+template <typename T, int W, bool SEG>
 __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uint8_t *Gs, const uint8_t *src,
                                              uint8_t *bits_row, float *pm_out, uint8_t *ok_out, int32_t *slot_out,
                                              int gidx, int gtid, bool lockstep, uint32_t sstride, uint64_t gstride,
@@ -1285,9 +1285,11 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
     const int lane = gtid & 31;
     const int wig = gtid >> 5;
     const int n = cv.n, N = cv.N, L = cv.L;
-    // register subtrees of several frames in one warp (lockstep rounds, one warp
-    // per frame, L <= 16, and 32 / L frame groups to a CTA)
-    const bool pack = cv.pack && W == 1 && lockstep && L <= 16 && 32 / L <= gpc;
+    // register subtrees of several frames in one warp (codes that pack: L <= 16,
+    // one warp per frame; in lockstep rounds with 32 / L frame groups to a CTA).
+    // Only the SEG instantiations hold that code.
+    static_assert(!SEG || W == 1, "packing needs one warp per frame");
+    const bool pack = SEG && cv.pack && lockstep && 32 / L <= gpc;
     const int bwn = beta_words(n);
     T *chan = chan_ptr<T>(lay, S, Gs);
     uint32_t *br = br_ptr(lay, S, Gs);
@@ -1476,7 +1478,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                     else run_sub<T, 3, true>(cv, S, Gs, op, La, cur, lane, P, sstride, gstride);
                 }
                 asm volatile("bar.sync 15, %0;" ::"r"(blockDim.x) : "memory");
-            } else if (wig == 0 && L <= 16) {
+            } else if (SEG && cv.pack && wig == 0) {
                 // one frame, its selection in an L-lane segment (shorter sorting
                 // networks); the other lanes idle
                 if (j == kSubLog) run_sub<T, 4, true>(cv, S, Gs, op, La, cur, lane);
@@ -1492,7 +1494,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
             if (op_sub_fork(op)) cur ^= 1;
         } else {
             // ---------------- a leaf of more than 16 bits (warp 0) ----------------
-            if (wig == 0) big_leaf<T>(cv, S, Gs, kind, j, dest, La, cur, lane);
+            if (wig == 0) big_leaf<T, SEG>(cv, S, Gs, kind, j, dest, La, cur, lane);
             if (kind != OP_R0) {
                 const int C = kind == OP_R1 ? 4 : (kind == OP_REP ? 2 : (L == 2 ? 2 : 8));
                 La = La * C < L ? La * C : L;
@@ -1600,7 +1602,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
 }
 
 // Plain form: one code, frames f = group, group + n_groups, ...
-template <typename T, int W>
+template <typename T, int W, bool SEG>
 __global__ void __launch_bounds__(kMaxCtaThreads) decode_kernel(const Params P) {
     constexpr int GT = W * 32;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -1617,7 +1619,7 @@ __global__ void __launch_bounds__(kMaxCtaThreads) decode_kernel(const Params P) 
         // lockstep only in rounds where every group of the CTA has a frame, so
         // that all warps reach each per-op barrier the same number of times
         const bool full = P.groups_per_cta > 1 && (i - (uint32_t)gidx) + (uint32_t)P.groups_per_cta <= nf;
-        decode_frame<T, W>(P.cv, S, Gs, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
+        decode_frame<T, W, SEG>(P.cv, S, Gs, reinterpret_cast<const uint8_t *>(P.llr) + (size_t)f * nbytes,
                            P.bits + (size_t)f * P.cv.kb, P.pm + f, P.ok ? P.ok + f : nullptr,
                            P.slot ? P.slot + f : nullptr, gidx, gtid, full, P.cv.lay.bytes, P.cv.lay.gbytes,
                            P.groups_per_cta);
@@ -1646,7 +1648,7 @@ __global__ void crc_failures_kernel(const uint8_t *ok, uint32_t n, uint32_t *idx
 // items contiguous) from a device counter; the code of an item is copied into
 // the group's shared memory when it changes. When all groups of the CTA got a
 // frame of the same code they run it in lockstep, as in the plain form.
-template <typename T, int W>
+template <typename T, int W, bool SEG>
 __global__ void __launch_bounds__(kMaxCtaThreads) batch_kernel(const BatchParams B) {
     constexpr int GT = W * 32;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -1682,51 +1684,145 @@ __global__ void __launch_bounds__(kMaxCtaThreads) batch_kernel(const BatchParams
             loaded = item.cls;
             gsync<W>(gidx);
         }
-        decode_frame<T, W>(*cvs, S, Gs, B.llr + item.llr_off, B.bits + item.bits_off, B.pm + item.frame,
+        decode_frame<T, W, SEG>(*cvs, S, Gs, B.llr + item.llr_off, B.bits + item.bits_off, B.pm + item.frame,
                            B.ok ? B.ok + item.frame : nullptr, B.slot ? B.slot + item.frame : nullptr, gidx, gtid,
                            lock, B.group_bytes, B.gbytes, B.groups_per_cta);
     }
 }
 
-template <typename T, int W>
+template <typename T, int W, bool SEG = false>
 cudaError_t launch_one(const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(decode_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(decode_kernel<T, W, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sh.smem);
     if (e != cudaSuccess) return e;
-    decode_kernel<T, W><<<grid, sh.threads, sh.smem, st>>>(p);
+    decode_kernel<T, W, SEG><<<grid, sh.threads, sh.smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <typename T, int W>
+template <typename T, int W, bool SEG = false>
 int occ_one(const LaunchShape &sh) {
-    if (cudaFuncSetAttribute(decode_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) !=
+    if (cudaFuncSetAttribute(decode_kernel<T, W, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) !=
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decode_kernel<T, W>, sh.threads, sh.smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decode_kernel<T, W, SEG>, sh.threads, sh.smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
 
-template <typename T, int W>
+template <typename T, int W, bool SEG = false>
 cudaError_t launch_batch_one(const BatchParams &b, int grid, uint32_t smem, int threads, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(batch_kernel<T, W, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    batch_kernel<T, W><<<grid, threads, smem, st>>>(b);
+    batch_kernel<T, W, SEG><<<grid, threads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
-template <typename T, int W>
+template <typename T, int W, bool SEG = false>
 int occ_batch_one(uint32_t smem, int threads) {
-    if (cudaFuncSetAttribute(batch_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(batch_kernel<T, W, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T, W>, threads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<T, W, SEG>, threads, smem) != cudaSuccess)
+        return 0;
     return nb;
+}
+
+// One type's kernels behind one entry each (shape -> instantiation).
+template <typename T>
+cudaError_t launch_decode_typed(const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
+    if (sh.pack && sh.warps == 1) return launch_one<T, 1, true>(sh, p, grid, st);
+    if (sh.warps == 1) return launch_one<T, 1>(sh, p, grid, st);
+    if (sh.warps == 2) return launch_one<T, 2>(sh, p, grid, st);
+    if (sh.warps == 4) return launch_one<T, 4>(sh, p, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int occupancy_typed(const LaunchShape &sh) {
+    if (sh.pack && sh.warps == 1) return occ_one<T, 1, true>(sh);
+    if (sh.warps == 1) return occ_one<T, 1>(sh);
+    if (sh.warps == 2) return occ_one<T, 2>(sh);
+    if (sh.warps == 4) return occ_one<T, 4>(sh);
+    return 0;
+}
+
+template <typename T>
+cudaError_t launch_batch_typed(int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
+                               cudaStream_t st) {
+    if (seg && warps == 1) return launch_batch_one<T, 1, true>(b, grid, smem, threads, st);
+    if (warps == 1) return launch_batch_one<T, 1>(b, grid, smem, threads, st);
+    if (warps == 2) return launch_batch_one<T, 2>(b, grid, smem, threads, st);
+    if (warps == 4) return launch_batch_one<T, 4>(b, grid, smem, threads, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+int occupancy_batch_typed(int warps, bool seg, uint32_t smem, int threads) {
+    if (seg && warps == 1) return occ_batch_one<T, 1, true>(smem, threads);
+    if (warps == 1) return occ_batch_one<T, 1>(smem, threads);
+    if (warps == 2) return occ_batch_one<T, 2>(smem, threads);
+    if (warps == 4) return occ_batch_one<T, 4>(smem, threads);
+    return 0;
 }
 
 }  // namespace
 
+// The kernels compile in four parts, one translation unit each, so that they
+// build in parallel: 0 float and 1 int8 in the plain form, 2 float and 3 int8
+// in the batched form. POLAR_KPART picks one part (all four when it is not
+// defined); the dispatchers sit in part 0.
+#ifndef POLAR_KPART
+#define POLAR_KPART -1
+#endif
+#define POLAR_HAS_PART(p) (POLAR_KPART < 0 || POLAR_KPART == (p))
+
+cudaError_t launch_decode_f32(const LaunchShape &sh, const Params &p, int grid, cudaStream_t st);
+cudaError_t launch_decode_i8(const LaunchShape &sh, const Params &p, int grid, cudaStream_t st);
+int occupancy_f32(const LaunchShape &sh);
+int occupancy_i8(const LaunchShape &sh);
+cudaError_t launch_batch_f32(int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
+                             cudaStream_t st);
+cudaError_t launch_batch_i8(int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
+                            cudaStream_t st);
+int occupancy_batch_f32(int warps, bool seg, uint32_t smem, int threads);
+int occupancy_batch_i8(int warps, bool seg, uint32_t smem, int threads);
+
+#if POLAR_HAS_PART(0)
+cudaError_t launch_decode_f32(const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
+    return launch_decode_typed<float>(sh, p, grid, st);
+}
+int occupancy_f32(const LaunchShape &sh) { return occupancy_typed<float>(sh); }
+#endif
+#if POLAR_HAS_PART(1)
+cudaError_t launch_decode_i8(const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
+    return launch_decode_typed<int8_t>(sh, p, grid, st);
+}
+int occupancy_i8(const LaunchShape &sh) { return occupancy_typed<int8_t>(sh); }
+#endif
+#if POLAR_HAS_PART(2)
+cudaError_t launch_batch_f32(int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
+                             cudaStream_t st) {
+    return launch_batch_typed<float>(warps, seg, b, grid, smem, threads, st);
+}
+int occupancy_batch_f32(int warps, bool seg, uint32_t smem, int threads) {
+    return occupancy_batch_typed<float>(warps, seg, smem, threads);
+}
+#endif
+#if POLAR_HAS_PART(3)
+cudaError_t launch_batch_i8(int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
+                            cudaStream_t st) {
+    return launch_batch_typed<int8_t>(warps, seg, b, grid, smem, threads, st);
+}
+int occupancy_batch_i8(int warps, bool seg, uint32_t smem, int threads) {
+    return occupancy_batch_typed<int8_t>(warps, seg, smem, threads);
+}
+#endif
+
+#if POLAR_HAS_PART(0)
 cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n, uint32_t *idx, uint32_t *cnt, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess || n == 0) return e;
@@ -1735,57 +1831,21 @@ cudaError_t launch_crc_failures(const uint8_t *ok, uint32_t n, uint32_t *idx, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(int dtype, int warps, const BatchParams &b, int grid, uint32_t smem, int threads,
+cudaError_t launch_batch(int dtype, int warps, bool seg, const BatchParams &b, int grid, uint32_t smem, int threads,
                          cudaStream_t st) {
-    if (dtype == 0) {
-        if (warps == 1) return launch_batch_one<float, 1>(b, grid, smem, threads, st);
-        if (warps == 2) return launch_batch_one<float, 2>(b, grid, smem, threads, st);
-        if (warps == 4) return launch_batch_one<float, 4>(b, grid, smem, threads, st);
-    } else {
-        if (warps == 1) return launch_batch_one<int8_t, 1>(b, grid, smem, threads, st);
-        if (warps == 2) return launch_batch_one<int8_t, 2>(b, grid, smem, threads, st);
-        if (warps == 4) return launch_batch_one<int8_t, 4>(b, grid, smem, threads, st);
-    }
-    return cudaErrorInvalidValue;
+    return dtype == 0 ? launch_batch_f32(warps, seg, b, grid, smem, threads, st)
+                      : launch_batch_i8(warps, seg, b, grid, smem, threads, st);
 }
 
-int occupancy_batch(int dtype, int warps, uint32_t smem, int threads) {
-    if (dtype == 0) {
-        if (warps == 1) return occ_batch_one<float, 1>(smem, threads);
-        if (warps == 2) return occ_batch_one<float, 2>(smem, threads);
-        if (warps == 4) return occ_batch_one<float, 4>(smem, threads);
-    } else {
-        if (warps == 1) return occ_batch_one<int8_t, 1>(smem, threads);
-        if (warps == 2) return occ_batch_one<int8_t, 2>(smem, threads);
-        if (warps == 4) return occ_batch_one<int8_t, 4>(smem, threads);
-    }
-    return 0;
+int occupancy_batch(int dtype, int warps, bool seg, uint32_t smem, int threads) {
+    return dtype == 0 ? occupancy_batch_f32(warps, seg, smem, threads) : occupancy_batch_i8(warps, seg, smem, threads);
 }
 
 cudaError_t launch_decode(int dtype, const LaunchShape &sh, const Params &p, int grid, cudaStream_t st) {
-    if (dtype == 0) {
-        if (sh.warps == 1) return launch_one<float, 1>(sh, p, grid, st);
-        if (sh.warps == 2) return launch_one<float, 2>(sh, p, grid, st);
-        if (sh.warps == 4) return launch_one<float, 4>(sh, p, grid, st);
-    } else {
-        if (sh.warps == 1) return launch_one<int8_t, 1>(sh, p, grid, st);
-        if (sh.warps == 2) return launch_one<int8_t, 2>(sh, p, grid, st);
-        if (sh.warps == 4) return launch_one<int8_t, 4>(sh, p, grid, st);
-    }
-    return cudaErrorInvalidValue;
+    return dtype == 0 ? launch_decode_f32(sh, p, grid, st) : launch_decode_i8(sh, p, grid, st);
 }
 
-int occupancy(int dtype, const LaunchShape &sh) {
-    if (dtype == 0) {
-        if (sh.warps == 1) return occ_one<float, 1>(sh);
-        if (sh.warps == 2) return occ_one<float, 2>(sh);
-        if (sh.warps == 4) return occ_one<float, 4>(sh);
-    } else {
-        if (sh.warps == 1) return occ_one<int8_t, 1>(sh);
-        if (sh.warps == 2) return occ_one<int8_t, 2>(sh);
-        if (sh.warps == 4) return occ_one<int8_t, 4>(sh);
-    }
-    return 0;
-}
+int occupancy(int dtype, const LaunchShape &sh) { return dtype == 0 ? occupancy_f32(sh) : occupancy_i8(sh); }
+#endif
 
 }  // namespace polar

@@ -50,6 +50,7 @@ class CodeInfo(ctypes.Structure):
         ("frames_per_cta", ctypes.c_uint32 * 2), ("smem_per_frame", ctypes.c_uint32 * 2),
         ("scratch_per_frame", ctypes.c_uint64 * 2), ("spill_mask", ctypes.c_uint32 * 2),
         ("recomputed_stages", ctypes.c_uint32 * 2), ("max_recompute_depth", ctypes.c_uint32),
+        ("packed", ctypes.c_uint32 * 2),
     ]
 
 

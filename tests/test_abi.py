@@ -297,3 +297,30 @@ def test_packing_needs_a_packable_shape(polar):
     c32 = polar.PolarCode(fr, 32, I.CRC32_POLY, 32, host_only=True)
     with pytest.raises(polar.PolarError):
         c32.set_packing(0, True)
+
+
+def test_packing_default_and_choice_follow_the_code(polar):
+    """Packing is on by default for L <= 4 and off for L = 8, 16; a choice made
+    with set_packing is kept by later one-warp shapes and dropped by shapes
+    with more warps per frame."""
+    fr = I.ga_frozen_mask(1024, 860, 4.0, 828 / 1024)
+    for L, default in ((2, 1), (4, 1), (8, 0), (16, 0), (32, 0)):
+        c = polar.PolarCode(fr, 32, I.CRC32_POLY, L, host_only=True)
+        c.set_launch(1, 1, 7000, 512)
+        assert c.info()["packed"][1] == default, L
+        c.set_launch(1, 2, 7000, 512)
+        assert c.info()["packed"][1] == 0, L
+    c8 = polar.PolarCode(fr, 32, I.CRC32_POLY, 8, host_only=True)
+    c8.set_launch(0, 1, 7000, 512)
+    c8.set_packing(0, True)
+    c8.set_launch(0, 1, 14000, 256)                # the choice outlives the shape
+    assert c8.info()["packed"] == [1, 0]
+    c8.set_launch(0, 4, 14000, 256)
+    assert c8.info()["packed"][0] == 0
+    c8.set_launch(0, 1, 7000, 512)                 # and comes back with one warp per frame
+    assert c8.info()["packed"][0] == 1
+    c2 = polar.PolarCode(fr, 32, I.CRC32_POLY, 2, host_only=True)
+    c2.set_launch(0, 1, 7000, 512)
+    c2.set_packing(0, False)
+    c2.set_launch(0, 1, 7000, 256)
+    assert c2.info()["packed"][0] == 0

@@ -1,12 +1,14 @@
 """Register subtrees of lists with L <= 16 paths.
 
-Such a frame's selection (Algorithm 1) sorts, scans and reduces inside an
-L-lane segment of its warp. With packing on, rounds where every frame group
-of a CTA holds a frame run the subtrees 32 / L frames to a warp (lane
-f * L + s is path s of frame f). The results must be the oracle's for every
-list size, node set, LLR type and CTA size, packed or not, including rounds
-that are not full (a frame count that is not a multiple of the CTA's
-frames), in the plain and in the batched form.
+With packing on, such a frame's selection (Algorithm 1) sorts, scans and
+reduces inside an L-lane segment of its warp, and rounds where every frame
+group of a CTA holds a frame run the subtrees 32 / L frames to a warp (lane
+f * L + s is path s of frame f). With it off a frame has its own warp and
+selects over all 32 lanes. The results must be the oracle's for every list
+size, node set, LLR type and CTA size, packed or not, including rounds that
+are not full (a frame count that is not a multiple of the CTA's frames), in
+the plain and in the batched form (classes that pack beside classes that do
+not, in one launch).
 """
 import os
 
@@ -64,15 +66,20 @@ def test_packed_subtrees_equal_the_oracle(env, dtype, L):
             code = polar.PolarCode(fr, crc, I.CRC8_POLY, L, mode=mode)
             for cta in (128, 256, 512):
                 code.set_launch(dt, 1, 0, cta)
-                g = code.decode(x)                             # each frame in its own warp, L-lane segments
-                torch.cuda.synchronize()
-                _check(g, o, dtype, f"L={L} N={N} mode={mode} cta={cta}")
                 if 32 // L <= cta // 32:
-                    code.set_packing(dt, True)                 # 32 / L frames to a warp in lockstep rounds
+                    for on in (False, True):                   # own warp each / 32 / L frames to a warp
+                        code.set_packing(dt, on)
+                        assert code.info()["packed"][dt] == int(on)
+                        g = code.decode(x)
+                        torch.cuda.synchronize()
+                        _check(g, o, dtype, f"packed={on} L={L} N={N} mode={mode} cta={cta}")
+                else:
+                    # too few groups per CTA to pack: with the choice on (from the
+                    # last CTA size, or the L <= 4 default) selection still runs in
+                    # L-lane segments, one frame to a warp
                     g = code.decode(x)
                     torch.cuda.synchronize()
-                    _check(g, o, dtype, f"packed L={L} N={N} mode={mode} cta={cta}")
-                else:
+                    _check(g, o, dtype, f"segments={code.info()['packed'][dt]} L={L} N={N} mode={mode} cta={cta}")
                     with pytest.raises(polar.PolarError):
                         code.set_packing(dt, True)
             code.close()
@@ -80,7 +87,8 @@ def test_packed_subtrees_equal_the_oracle(env, dtype, L):
 
 def test_packed_subtrees_in_the_batched_form(env):
     """A mix of L = 2..16 classes (and one L = 32) in one persistent launch
-    with 512-thread CTAs."""
+    with 512-thread CTAs: L = 2, 4 pack by default, one L = 8 class and the
+    L = 16 class are told to, the other L = 8 class is not."""
     torch, polar, oracle = env
     rng = np.random.default_rng(7)
     classes = [(256, 128, 2), (256, 160, 4), (512, 300, 8), (1024, 700, 16), (256, 200, 32), (128, 64, 8)]
@@ -88,7 +96,11 @@ def test_packed_subtrees_in_the_batched_form(env):
     for N, K, L in classes:
         fr = I.ga_frozen_mask(N, K, 2.0, (K - 32) / N)
         frozen.append(fr)
-        codes.append(polar.PolarCode(fr, 32, I.CRC32_POLY, L))
+        code = polar.PolarCode(fr, 32, I.CRC32_POLY, L)
+        if (N, L) in ((512, 8), (1024, 16)):
+            code.set_launch(polar.LLR_I8, 1, 7000, 512)
+            code.set_packing(polar.LLR_I8, True)
+        codes.append(code)
         llrs.append(I.make_frames(fr, 32, I.CRC32_POLY, 2.0, 700, seed=N + L).llr_i8)
     fc = np.repeat(np.arange(len(classes), dtype=np.uint32), 700)
     rng.shuffle(fc)
