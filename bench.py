@@ -733,13 +733,19 @@ def measure_serving(args):
         srv.result(tk, timeout_ms=600000)
     wall = time.perf_counter() - t0
     st = srv.stats()
+    # the tail by request size: small requests wait behind large ones, large
+    # ones take as long as their own frames
+    by_size = {}
+    for lo, hi in ((1, 16), (17, 256), (257, 4096)):
+        q = srv.latency(lo, hi)
+        by_size[f"{lo}-{hi}"] = {"requests": q["count"], "p50_ms": q["p50_us"] / 1e3, "p99_ms": q["p99_us"] / 1e3}
     srv.close()
     return {
         "workload": "Poisson requests, 1..4096 frames (log-uniform), (N,K,L) from the 125-class Zipf mix, "
                     "f32/int8 50/50, Eb/N0 3.5..4.5 dB",
         "offered_frames_per_s": args.serve_rate, "requests": len(reqs), "frames": frames,
         "duration_s": wall, "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
-        "max_ms": st["max_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
+        "max_ms": st["max_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3, "by_frames": by_size,
         "info_gbps": st["info_bits"] / (st["span_us"] * 1e-6) / 1e9 if st["span_us"] > 0 else None,
         "batches": st["batches"], "max_batches_in_flight": st["max_batches_in_flight"],
         "server_launch": {"warps_per_frame": args.serve_warps or 1, "smem_budget": args.serve_budget or 7000},
@@ -828,13 +834,24 @@ def run_ours(args):
     e2e_steps = max(1, min(args.steps, 3))
     code.decode_host(host_llr, hbits, hpm, hok, stream=stream)
     barrier()
+    call_ms = []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        t1 = time.perf_counter()
         code.decode_host(host_llr, hbits, hpm, hok, stream=stream)
+        call_ms.append((time.perf_counter() - t1) * 1e3)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     barrier()
+    # the copy engine's rate on this host (one pinned copy of the whole input)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    llr.copy_(host_llr, non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = llr.numel() * llr.element_size() / (time.perf_counter() - t1) / 1e9
     e2e_ms = reduce_max(torch, e2e_ms, dev)
     e2e_val = job_gbps(k, args.frames, world, e2e_ms)
+    e2e_calls = [round(x, 1) for x in call_ms]
+    e2e_h2d_gbs = round(h2d_gbs, 1)
     if not torch.equal(hbits[:UNIQUE].to(dev), bits[:UNIQUE]):
         raise RuntimeError("host-buffer decode differs from the device decode")
     h2d = llr.numel() * llr.element_size()
@@ -941,7 +958,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": config_dict(args, "ours"),
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "calls_ms": e2e_calls, "h2d_gbs": e2e_h2d_gbs},
             "gpu_launches": args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -956,8 +974,10 @@ def run_ours(args):
                             "ms_per_step": other.get("ms_per_step")} if other else None,
             "adaptive": compact_adaptive(fer_sweep),
             "fer": compact_fer(fer_sweep),
-            "serving": {x: serving.get(x) for x in ("offered_frames_per_s", "requests", "frames", "p50_ms", "p99_ms",
-                                                    "info_gbps")} if serving else None,
+            "serving": dict({x: serving.get(x) for x in ("offered_frames_per_s", "requests", "frames", "p50_ms",
+                                                         "p99_ms", "info_gbps")},
+                            p99_ms_by_frames={k: v["p99_ms"] for k, v in serving["by_frames"].items()})
+            if serving else None,
             "batched": {x: batched.get(x) for x in ("value", "plain_value", "ms_per_step", "plain_ms_per_step",
                                                     "plain_launches_per_step", "results_equal_plain")}
             if batched else None,

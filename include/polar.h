@@ -228,8 +228,9 @@ POLAR_API int polar_code_set_smem_budget(polar_code_t *code, int llr_dtype, uint
  * each way). The choice is kept per LLR type: later shapes from
  * polar_code_set_launch use it where they allow it (one warp per frame), and
  * the batched and serving forms follow the code's choice for its frames.
- * Turning it on needs a shape with one warp per frame and at least 32 / L
- * frames per CTA; the rest of the current shape is kept. polar_code_autotune
+ * Turning it on needs a shape with one warp per frame; frames are packed
+ * only in CTAs of at least 32 / L frame groups, elsewhere the segments alone
+ * apply. The rest of the current shape is kept. polar_code_autotune
  * and polar_batch_autotune (all classes on or off) try both settings. Results
  * do not depend on it. Errors: POLAR_EINVAL (bad arguments or shape),
  * POLAR_EUNSUPPORTED (a wide code), POLAR_ENOMEM / POLAR_ECUDA (uploading the
@@ -423,6 +424,12 @@ POLAR_API int polar_server_wait(polar_server_t *server, uint64_t ticket, uint32_
 POLAR_API int polar_server_pause(polar_server_t *server, int paused);
 /* Counters and latency percentiles; reset != 0 clears them afterwards. */
 POLAR_API int polar_server_stats(polar_server_t *server, polar_server_stats_t *stats, int reset);
+/* Latency percentiles (submit -> results on host, microseconds) over the
+ * requests completed since the last reset whose size is min_frames ..
+ * max_frames frames; 0 when there are none. Any output may be NULL. Errors:
+ * POLAR_EINVAL (NULL server, min_frames > max_frames). */
+POLAR_API int polar_server_latency(polar_server_t *server, uint32_t min_frames, uint32_t max_frames,
+                                   double *p50_us, double *p99_us, uint64_t *count);
 
 /* Allocation-free variant of polar_list_decode. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

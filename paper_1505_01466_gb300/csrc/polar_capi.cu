@@ -827,6 +827,9 @@ int polar_code_create(polar_code_t **out, uint32_t N, uint32_t K, const uint8_t 
         *out = c;
         return POLAR_OK;
     }
+    // the latency shape: four warps and every stage that fits in a CTA's
+    // shared memory (one warp with the selection in L-lane segments was
+    // measured slower for one frame at every L <= 16)
     for (int d = 0; d < 2; ++d) {
         LaunchShape lat;
         if (!c->host_only && make_shape(c, d, 4, 0xffffffffu, lat, 128, 0) &&
@@ -879,9 +882,13 @@ int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int l
     const uint64_t row = (uint64_t)code->N * (llr_dtype == POLAR_LLR_I8 ? 1u : 4u);
     const uint64_t kb = (code->k + 7) / 8;
     // chunks of frames in a two-buffer ring: the copy in of chunk c + 1 and the
-    // copy out of chunk c - 1 overlap the decode of chunk c
+    // copy out of chunk c - 1 overlap the decode of chunk c. The first chunks
+    // are smaller (doubling up to `chunk`) so that the copy in that nothing
+    // overlaps is short.
     const uint32_t chunk = std::min<uint32_t>(n_frames, std::max<uint32_t>(4096u, std::min<uint32_t>(131072u, n_frames / 8)));
-    const uint32_t n_chunks = (n_frames + chunk - 1) / chunk;
+    const uint32_t first = std::max<uint32_t>(std::min<uint32_t>(chunk, 2048u), chunk / 16u);
+    uint32_t n_chunks = 0;
+    for (uint64_t f = 0, sz = first; f < n_frames; f += sz, sz = std::min<uint64_t>(2 * sz, chunk)) ++n_chunks;
     const uint64_t out_row = kb + 4 + 1 + 4;
     const uint64_t buf_bytes = (uint64_t)chunk * (row + out_row) + 64;
     cudaStream_t dec = reinterpret_cast<cudaStream_t>(stream);
@@ -901,10 +908,10 @@ int polar_list_decode_host(const polar_code_t *code, const void *llr_host, int l
     // the caller's stream may have pending work on the host buffers' producers
     if (rc == POLAR_OK && cudaEventRecord(ev_dec[0], dec) != cudaSuccess) rc = POLAR_ECUDA;
     if (rc == POLAR_OK && cudaStreamWaitEvent(cin, ev_dec[0], 0) != cudaSuccess) rc = POLAR_ECUDA;
-    for (uint32_t c = 0; rc == POLAR_OK && c < n_chunks; ++c) {
+    uint64_t f0 = 0, sz = first;
+    for (uint32_t c = 0; rc == POLAR_OK && c < n_chunks; ++c, f0 += sz, sz = std::min<uint64_t>(2 * sz, chunk)) {
         const int b = (int)(c & 1u);
-        const uint64_t f0 = (uint64_t)c * chunk;
-        const uint32_t nf = (uint32_t)std::min<uint64_t>(chunk, n_frames - f0);
+        const uint32_t nf = (uint32_t)std::min<uint64_t>(sz, n_frames - f0);
         uint8_t *d_llr = buf[b];
         uint8_t *d_bits = d_llr + (uint64_t)chunk * row;
         float *d_pm = reinterpret_cast<float *>(((uintptr_t)(d_bits + (uint64_t)chunk * kb) + 15) & ~(uintptr_t)15);
@@ -1164,7 +1171,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
     }
     // several frames' register subtrees to a warp (L <= 16, one warp per frame,
     // 32 / L frame groups to a CTA) on the best shape
-    if (status == POLAR_OK && best_w == 1 && code->L <= 16 && (uint32_t)(32 / code->L) <= best_t / 32) {
+    if (status == POLAR_OK && best_w == 1 && code->L <= 16) {
         LaunchShape sh = best;
         sh.pack = best.pack ^ 1;
         std::vector<uint32_t> fl = flag_ops(code->ops, 1);
@@ -1694,7 +1701,7 @@ int polar_code_set_packing(polar_code_t *c, int llr_dtype, int on) {
     if (!c || (llr_dtype != POLAR_LLR_F32 && llr_dtype != POLAR_LLR_I8)) return POLAR_EINVAL;
     if (c->wide) return POLAR_EUNSUPPORTED;
     LaunchShape sh = c->shape[llr_dtype];
-    if (on && (sh.warps != 1 || c->L > 16 || 32 / (int)c->L > sh.groups_per_cta)) return POLAR_EINVAL;
+    if (on && (sh.warps != 1 || c->L > 16)) return POLAR_EINVAL;
     sh.pack = on ? 1 : 0;
     sh.d_ops = nullptr;
     const bool fixed = c->explicit_shape[llr_dtype];
@@ -1833,6 +1840,7 @@ struct polar_server {
     std::thread worker;
     // statistics since the last reset
     std::vector<double> lat_us;
+    std::vector<uint32_t> lat_frames;         // frames of the request of each lat_us entry
     uint64_t frames_done = 0, bits_done = 0, batches = 0, max_inflight = 0;
     double t_first = 0.0, t_last = 0.0;
 };
@@ -2029,6 +2037,7 @@ void srv_finish(polar_server *s, int i) {
         r->done = true;
         r->t_done = t;
         s->lat_us.push_back(t - r->t_submit);
+        s->lat_frames.push_back(r->n);
         s->frames_done += r->n;
         s->bits_done += (uint64_t)r->n * r->code->k;
         if (s->t_first == 0.0 || r->t_submit < s->t_first) s->t_first = r->t_submit;
@@ -2273,10 +2282,26 @@ int polar_server_stats(polar_server_t *s, polar_server_stats_t *out, int reset) 
     }
     if (reset) {
         s->lat_us.clear();
+        s->lat_frames.clear();
         s->frames_done = s->bits_done = s->batches = s->max_inflight = 0;
         s->t_first = s->t_last = 0.0;
     }
     return s->error;
+}
+
+int polar_server_latency(polar_server_t *s, uint32_t min_frames, uint32_t max_frames, double *p50_us,
+                         double *p99_us, uint64_t *count) {
+    if (!s || min_frames > max_frames) return POLAR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::vector<double> v;
+    for (size_t i = 0; i < s->lat_us.size(); ++i)
+        if (s->lat_frames[i] >= min_frames && s->lat_frames[i] <= max_frames) v.push_back(s->lat_us[i]);
+    std::sort(v.begin(), v.end());
+    auto q = [&](double p) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    if (p50_us) *p50_us = q(0.50);
+    if (p99_us) *p99_us = q(0.99);
+    if (count) *count = v.size();
+    return POLAR_OK;
 }
 
 }  // extern "C"

@@ -30,7 +30,7 @@ EXPORTED = [
     "polar_batch_plan", "polar_batch_destroy", "polar_batch_layout", "polar_batch_run", "polar_batch_set_launch",
     "polar_batch_autotune", "polar_batch_capture", "polar_batch_replay", "polar_batch_get_info",
     "polar_server_create", "polar_server_destroy", "polar_server_submit", "polar_server_poll", "polar_server_wait",
-    "polar_server_pause", "polar_server_stats", "polar_adaptive_decode", "polar_list_decode_host",
+    "polar_server_pause", "polar_server_stats", "polar_server_latency", "polar_adaptive_decode", "polar_list_decode_host",
     "polar_debug_inject",
 ]
 
@@ -136,6 +136,8 @@ def _lib():
         lib.polar_server_wait.argtypes = [vp, u64, u32]
         lib.polar_server_pause.argtypes = [vp, i32]
         lib.polar_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats), i32]
+        lib.polar_server_latency.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
         lib.polar_adaptive_decode.argtypes = [vp, vp, vp, i32, u32, vp, vp, vp, vp, vp, vp]
         lib.polar_list_decode_host.argtypes = [vp, vp, i32, u32, vp, vp, vp, vp, vp]
         lib.polar_debug_inject.argtypes = [i32, ctypes.c_int64]
@@ -452,3 +454,10 @@ class PolarServer:
         st = ServerStats()
         _check(_lib().polar_server_stats(self._h, ctypes.byref(st), 1 if reset else 0), "polar_server_stats")
         return {name: (getattr(st, name)) for name, _ in ServerStats._fields_}
+
+    def latency(self, min_frames: int, max_frames: int) -> dict:
+        """p50 / p99 latency (us) of completed requests of min..max frames."""
+        p50, p99, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        _check(_lib().polar_server_latency(self._h, min_frames, max_frames, ctypes.byref(p50), ctypes.byref(p99),
+                                           ctypes.byref(cnt)), "polar_server_latency")
+        return {"p50_us": p50.value, "p99_us": p99.value, "count": cnt.value}

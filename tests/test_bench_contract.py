@@ -93,7 +93,8 @@ def test_metric_comparisons_fit_the_line_tail():
             "graph_replay": True, "results_equal_plain": True, "roofline": {"frac": 0.0412345, "plain_frac": 0.04}}
     tail = {"fer": fer,
             "serving": {"offered_frames_per_s": 200000.0, "requests": 1234, "frames": 1612345,
-                        "p50_ms": 0.423456789, "p99_ms": 4.123456789, "info_gbps": 0.19123456789},
+                        "p50_ms": 0.423456789, "p99_ms": 4.123456789, "info_gbps": 0.19123456789,
+                        "p99_ms_by_frames": {"1-16": 1.123456789, "17-256": 2.123456789, "257-4096": 5.123456789}},
             "batched": {"value": 5.3123456789, "plain_value": 4.6312345678, "ms_per_step": 123.456789,
                         "plain_ms_per_step": 140.123456789, "plain_launches_per_step": 125,
                         "results_equal_plain": True},

@@ -195,12 +195,14 @@ def test_autotune_keeps_results(torch_cuda, oracle_mod):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "i8"])
-def test_host_buffer_decode_matches_device_decode(torch_cuda, oracle_mod, dtype):
-    # polar_list_decode_host: chunked copy in / decode / copy out, ragged last chunk
+@pytest.mark.parametrize("n_frames", [10001, 70001])
+def test_host_buffer_decode_matches_device_decode(torch_cuda, oracle_mod, dtype, n_frames):
+    # polar_list_decode_host: chunked copy in / decode / copy out, chunks growing
+    # from the first (2048 frames) to the largest, ragged last chunk
     from paper_1505_01466_gb300.polar import PolarCode
     torch = torch_cuda
     fr = I.ga_frozen_mask(512, 300, 3.0, 268 / 512)
-    f = I.make_frames(fr, 32, I.CRC32_POLY, 2.5, 10001, seed=12)
+    f = I.make_frames(fr, 32, I.CRC32_POLY, 2.5, n_frames, seed=12)
     x = f.llr_i8 if dtype == "i8" else f.llr_f32
     code = PolarCode(fr, 32, I.CRC32_POLY, 8)
     ref = [t.cpu() for t in code.decode(torch.from_numpy(x).cuda())]

@@ -52,6 +52,15 @@ def test_results_same_alone_and_in_the_mix(env):
     st = srv.stats()
     assert st["completed"] == 2 * len(reqs)
     assert st["batches"] < 2 * len(reqs)            # requests were batched together in the mix
+    # latency percentiles by request size cover the same requests
+    sizes = [llr.shape[0] for _, llr in reqs]
+    small, rest, every = srv.latency(1, 16), srv.latency(17, 1 << 30), srv.latency(1, 1 << 30)
+    assert small["count"] == 2 * sum(1 for n in sizes if n <= 16)
+    assert small["count"] + rest["count"] == every["count"] == 2 * len(reqs)
+    assert every["p50_us"] == st["p50_us"] and every["p99_us"] == st["p99_us"]
+    assert 0 < small["p50_us"] <= small["p99_us"] <= st["max_us"]
+    with pytest.raises(polar.PolarError):
+        srv.latency(5, 4)
     for (code, llr), a, m in zip(reqs, alone, mixed):
         for x, y in zip(a, m):
             assert np.array_equal(x, y)
