@@ -93,8 +93,9 @@ enum polar_flags {
  *   crc_len      0 (no CRC: the best path wins) or 1..32.
  *   crc_poly     generator polynomial without the x^crc_len term.
  *   L            list size, a power of two, 1 <= L <= 128 (L = 1 is Fast-SSC
- *                decoding, Sec. V, with a kernel of its own: one lane per
- *                frame). 2 <= L <= 32 runs the warp-per-frame kernels;
+ *                decoding, Sec. V, with kernels of its own: one lane per
+ *                frame, or one warp per frame for batches no larger than
+ *                the SM count). 2 <= L <= 32 runs the warp-per-frame kernels;
  *                L = 64 and 128 (the paper's Fig. 3 uses L = 128) run one CTA
  *                of L threads per frame over the fully unrolled schedule, with
  *                its stages in global scratch (polar_code_set_smem_budget can
@@ -132,9 +133,9 @@ POLAR_API int polar_code_destroy(polar_code_t *code);
  * Re-entrant: concurrent calls on distinct streams are safe (each call takes
  * its own scratch from the stream-ordered allocator when the code needs any).
  * A call with no more frames than the device has SMs runs them with a
- * latency shape (four warps and a CTA's shared memory per frame) unless
- * polar_code_set_launch fixed the shape, L = 1 codes included; results do not
- * depend on the shape.
+ * latency shape (four warps and a CTA's shared memory per frame; at L = 1 one
+ * warp over the node elements) unless polar_code_set_launch fixed the shape;
+ * results do not depend on the shape.
  * The call is asynchronous: it reports launch errors; an error raised while
  * its kernels run shows up in polar_sync (or the next CUDA call).
  * Errors: POLAR_EINVAL (NULL code/required pointer, bad dtype, host-only

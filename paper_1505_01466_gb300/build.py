@@ -1,8 +1,9 @@
 """Build ``libpolar_gb300.so`` in-tree with nvcc for sm_103a.
 
-Seven objects compile in parallel: the host runtime, the list kernels in four
+Eight objects compile in parallel: the host runtime, the list kernels in four
 parts (float / int8 x plain / batched form, one source compiled with
--DPOLAR_KPART=0..3), the wide-list kernel and the L = 1 kernel. They are linked
+-DPOLAR_KPART=0..3), the wide-list kernel and the two L = 1 kernels (many
+frames: a lane each; small batches: a warp each). They are linked
 into one shared library next to this file. No CMake, no torch extension
 machinery: the library has a plain C ABI (include/polar.h).
 """
@@ -15,13 +16,14 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpolar_gb300.so")
-SOURCES = ["polar_capi.cu", "polar_kernels.cu", "polar_wide.cu", "polar_sc1.cu"]
+SOURCES = ["polar_capi.cu", "polar_kernels.cu", "polar_wide.cu", "polar_sc1.cu", "polar_sc1w.cu"]
 # (source, object, extra flags): the list kernels compile once per part
 UNITS = [("polar_capi.cu", "polar_capi.o", []),
          *[("polar_kernels.cu", f"polar_kernels_p{p}.o", [f"-DPOLAR_KPART={p}", "-diag-suppress", "177"])
            for p in range(4)],   # a part leaves the other parts' helpers unused
          ("polar_wide.cu", "polar_wide.o", []),
-         ("polar_sc1.cu", "polar_sc1.o", [])]
+         ("polar_sc1.cu", "polar_sc1.o", []),
+         ("polar_sc1w.cu", "polar_sc1w.o", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -150,6 +150,14 @@ cudaError_t launch_sc1_locked(int dtype, const Sc1Params &p, int grid, int warps
     std::lock_guard<std::mutex> lk(g_launch_mu);
     return launch_sc1(dtype, p, grid, warps, st);
 }
+int occupancy_sc1w_locked(int dtype, int n, bool root_leaf, int warps) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return occupancy_sc1w(dtype, n, root_leaf, warps);
+}
+cudaError_t launch_sc1w_locked(int dtype, const Sc1wParams &p, int grid, int warps, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return launch_sc1w(dtype, p, grid, warps, st);
+}
 
 // NVTX range for the duration of a host call (visible in Nsight timelines).
 struct NvtxRange {
@@ -674,6 +682,37 @@ int decode_sc1(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
     return e == cudaSuccess ? POLAR_OK : POLAR_ECUDA;
 }
 
+// L = 1, small batches: one warp per frame, one warp per CTA (so that the
+// frames spread over the SMs); nothing in global scratch.
+int decode_sc1w(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
+                uint8_t *ok, int32_t *slot, cudaStream_t st) {
+    Sc1wParams p;
+    std::memset(&p, 0, sizeof(p));
+    const bool root_leaf = code->sops.size() == 1;
+    p.ops = code->d_sops;
+    p.n_ops = (int)code->sops.size();
+    p.syn = code->d_syn;
+    p.info = code->d_info;
+    p.n = (int)code->n;
+    p.k = (int)code->k;
+    p.kb = (int)((code->k + 7) / 8);
+    p.crc_len = (int)code->crc_len;
+    p.systematic = (code->flags & POLAR_SYSTEMATIC) ? 1 : 0;
+    p.root_leaf = root_leaf ? 1 : 0;
+    p.warp_bytes = sc1w_warp_bytes((int)code->n, dtype == POLAR_LLR_I8 ? 1 : 4, root_leaf, &p.beta_off);
+    p.llr = llr;
+    p.bits = bits;
+    p.pm = pm;
+    p.ok = ok;
+    p.slot = slot;
+    p.n_frames = n_frames;
+    const int occ = occupancy_sc1w_locked(dtype, (int)code->n, root_leaf, 1);
+    if (occ <= 0) return POLAR_ECUDA;
+    const uint64_t grid = std::min<uint64_t>((uint64_t)occ * (uint64_t)code->sm_count, n_frames);
+    return launch_sc1w_locked(dtype, p, (int)std::max<uint64_t>(grid, 1), 1, st) == cudaSuccess ? POLAR_OK
+                                                                                                 : POLAR_ECUDA;
+}
+
 // The installed shape of the narrow kernels, the L = 1 kernel or the wide kernel.
 int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_frames, uint8_t *bits, float *pm,
                uint8_t *ok, int32_t *slot, cudaStream_t st, const uint32_t *frame_idx = nullptr,
@@ -681,11 +720,12 @@ int decode_any(const polar_code *code, int dtype, const void *llr, uint32_t n_fr
     if (code->wide) return decode_wide(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
     // a batch no larger than the SM count is latency-bound: give each frame a
     // CTA of its own with everything on chip (unless the shape was fixed).
-    // That holds at L = 1 too, where one lane would otherwise walk a whole
-    // frame alone.
+    // At L = 1 that is one warp over the node elements, where one lane would
+    // otherwise walk a whole frame alone.
     const bool small = n_frames <= (uint32_t)code->sm_count && !frame_idx;
-    if (use_sc1(code, dtype) && !(small && code->lat[dtype].d_ops))
-        return decode_sc1(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
+    if (use_sc1(code, dtype))
+        return small ? decode_sc1w(code, dtype, llr, n_frames, bits, pm, ok, slot, st)
+                     : decode_sc1(code, dtype, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);
     const LaunchShape &sh = (small && !code->explicit_shape[dtype] && code->lat[dtype].d_ops) ? code->lat[dtype]
                                                                                                 : code->shape[dtype];
     return decode_shape(code, dtype, sh, llr, n_frames, bits, pm, ok, slot, st, frame_idx, frame_cnt);

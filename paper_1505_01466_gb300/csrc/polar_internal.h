@@ -246,4 +246,28 @@ void sc1_layout(int n, int es, uint32_t budget, Sc1Layout *lay);
 int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps);
 cudaError_t launch_sc1(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t stream);
 
+// The L = 1 kernel for small batches (polar_sc1w.cu): one warp per frame, the
+// lanes over a node's elements, every stored stage in the warp's shared memory.
+constexpr int kSc1wThreads = 256;  // most threads per CTA
+struct Sc1wParams {
+    const uint32_t *ops;           // sc1_op entries, fully unrolled (F/G/Combine/leaves)
+    int n_ops;
+    const uint32_t *syn;           // [N/8][256] CRC syndrome of each codeword byte
+    const uint16_t *info;          // [K] information positions, ascending
+    int n, k, kb, crc_len, systematic;
+    int root_leaf;                 // the root is a leaf: its input (the channel) is copied to stage n
+    int warp_bytes, beta_off;      // shared memory of one warp; offset of its beta row
+    const void *llr;               // [n_frames][N]
+    uint8_t *bits;                 // [n_frames][kb]
+    float *pm;
+    uint8_t *ok;
+    int32_t *slot;
+    uint32_t n_frames;
+    const uint32_t *frame_idx;     // optional indirection, as in Params
+    const uint32_t *frame_cnt;
+};
+int sc1w_warp_bytes(int n, int es, bool root_leaf, int *beta_off);
+int occupancy_sc1w(int dtype, int n, bool root_leaf, int warps);
+cudaError_t launch_sc1w(int dtype, const Sc1wParams &p, int grid, int warps, cudaStream_t stream);
+
 }  // namespace polar

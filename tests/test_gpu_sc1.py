@@ -1,9 +1,10 @@
-"""GPU parity of the L = 1 (Fast-SSC) kernel against the oracle.
+"""GPU parity of the L = 1 (Fast-SSC) kernels against the oracle.
 
-A code with L = 1 runs its own kernel (one lane per frame, 32 frames per
-warp) unless set_launch fixes a shape of the list kernels. Both
-must give the oracle's results bit for bit (payload, CRC flag, slot 0) with the
-penalty exact for int8 and within 1e-5 relative for float32.
+A code with L = 1 runs its own kernels unless set_launch fixes a shape of the
+list kernels: one lane per frame (32 frames per warp) for batches larger than
+the SM count, one warp per frame for smaller ones. All three must give the
+oracle's results bit for bit (payload, CRC flag, slot 0) with the penalty
+exact for int8 and within 1e-5 relative for float32.
 """
 import os
 
@@ -51,14 +52,23 @@ def _check(g, o, dtype, what):
 
 
 def _both_kernels(torch, oracle_mod, fr, crc, poly, llr, mode=0, systematic=False, offset=0):
+    """The three decoders of an L = 1 code: a batch larger than the SM count
+    takes the lane-per-frame kernel, a batch no larger the warp-per-frame
+    kernel, and an explicit launch shape the list kernel at L = 1."""
     from paper_1505_01466_gb300.polar import PolarCode
     dtype = "i8" if llr.dtype == np.int8 else "f32"
     o = oracle_mod.decode(fr, 1, llr, crc, poly, mode | (oracle_mod.SYSTEMATIC if systematic else 0), n_threads=NT)
     code = PolarCode(fr, crc, poly, 1, mode=mode, systematic=systematic)
     info = code.info()
     assert info["warps_per_frame"] == [1, 1] and info["frames_per_cta"][0] % 32 == 0
-    g = _decode(torch, code, llr, offset)
-    _check(g, o, dtype, f"L=1 kernel N={fr.size} mode={mode} sys={systematic} offset={offset}")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    reps = -(-(sms + 1) // llr.shape[0])
+    g = _decode(torch, code, np.concatenate([llr] * reps), offset)
+    _check(g, tuple(np.concatenate([x] * reps) for x in o), dtype,
+           f"lane per frame N={fr.size} mode={mode} sys={systematic} offset={offset}")
+    m = min(llr.shape[0], sms, 100)
+    g = _decode(torch, code, llr[:m], offset)
+    _check(g, tuple(x[:m] for x in o), dtype, f"warp per frame N={fr.size} mode={mode} sys={systematic} offset={offset}")
     code.set_launch(1 if dtype == "i8" else 0, 1, 0, 128)          # the list kernel at L = 1
     g2 = _decode(torch, code, llr, offset)
     _check(g2, o, dtype, f"list kernel N={fr.size} mode={mode}")
