@@ -1351,27 +1351,32 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                 else if (D == 2) fg_virtual<T, 2>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
                 else fg_virtual<T, 3>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
             }
-        } else if (kind == OP_F && op_kind(opn) == OP_F && op_stage(opn) == j - 1 && j - 2 >= 5 &&
+        } else if ((kind == OP_F || kind == OP_G) && op_kind(opn) == OP_F && op_stage(opn) == j - 1 && j - 2 >= 5 &&
                    ((lay.virt_mask >> (j - 2)) & 7u) == 0 && (sizeof(T) == 1 || L <= 8)) {
-            // ---------------- F twice: stage j -> j-1 -> j-2 ----------------
-            // The left child is an inner node too, so its F comes next. Each
-            // item reads the four quarter rows of stage j at one offset, writes
-            // both halves of stage j-1 there (the left child's G reads them
-            // later) and, from the same registers, stage j-2: one pass and one
-            // dependent round trip fewer than two F operations. Measured faster
-            // for int8 at every L and for float at L <= 8; float at L = 16 / 32
-            // keeps two F operations (eight items in flight per thread instead
-            // of four there).
+            // ------------ F or G, then the child's F: stage j -> j-1 -> j-2 ------------
+            // The child that stage j-1 feeds (the left one after F, the right
+            // one after G) is an inner node too, so its F comes next. Each item
+            // reads the four quarter rows of stage j at one offset (and, for G,
+            // the left child's beta bits there), writes both halves of stage
+            // j-1 (the child's G reads them later) and, from the same
+            // registers, stage j-2: one pass and one dependent round trip fewer
+            // than two operations. Measured faster for int8 at every L and for
+            // float at L <= 8; float at L = 16 / 32 keeps two operations (eight
+            // items in flight per thread instead of four there).
             if (!solo || wig == 0) {
                 const int q = 1 << (j - 2);
+                const bool isG = kind == OP_G;
                 const T *inb = (j == n) ? chan : alpha_ptr<T>(lay, S, Gs, j);
                 T *o1b = alpha_ptr<T>(lay, S, Gs, j - 1);
                 T *o2b = alpha_ptr<T>(lay, S, Gs, j - 2);
+                const uint32_t *blb = bl_ptr(lay, S, Gs, j - 1);
+                const int bwc = beta_words(j - 1);
                 if (sizeof(T) == 4) {
                     const int lv = j - 4;              // float4 items per quarter row (q >= 32)
                     const int total = La << lv;
                     for (int t0 = tid; t0 < total; t0 += 4 * nthr) {
                         float4 a[4][4];
+                        uint32_t nb0[4] = {0u, 0u, 0u, 0u}, nb1[4] = {0u, 0u, 0u, 0u};
                         int pp[4], vv[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
@@ -1382,15 +1387,32 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                                 reinterpret_cast<const float *>(inb) + (j == n ? 0 : ((int)idxc[pp[u] * 16 + j] << j)));
 #pragma unroll
                             for (int r = 0; r < 4; ++r) a[u][r] = in[vv[u] + r * (q >> 2)];
+                            if (isG) {
+                                const uint32_t *bl = blb + (int)bidxc[pp[u] * 16 + j - 1] * bwc;
+                                const int i0 = vv[u] << 2, i1 = i0 + q;
+                                nb0[u] = bl[i0 >> 5] >> (i0 & 31);
+                                nb1[u] = bl[i1 >> 5] >> (i1 & 31);
+                            }
                         }
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             if (t0 + u * nthr >= total) break;
                             float4 e0, e1, r;
-                            e0.x = f_op(a[u][0].x, a[u][2].x); e0.y = f_op(a[u][0].y, a[u][2].y);
-                            e0.z = f_op(a[u][0].z, a[u][2].z); e0.w = f_op(a[u][0].w, a[u][2].w);
-                            e1.x = f_op(a[u][1].x, a[u][3].x); e1.y = f_op(a[u][1].y, a[u][3].y);
-                            e1.z = f_op(a[u][1].z, a[u][3].z); e1.w = f_op(a[u][1].w, a[u][3].w);
+                            if (isG) {
+                                e0.x = g_op(a[u][0].x, a[u][2].x, nb0[u] & 1u);
+                                e0.y = g_op(a[u][0].y, a[u][2].y, (nb0[u] >> 1) & 1u);
+                                e0.z = g_op(a[u][0].z, a[u][2].z, (nb0[u] >> 2) & 1u);
+                                e0.w = g_op(a[u][0].w, a[u][2].w, (nb0[u] >> 3) & 1u);
+                                e1.x = g_op(a[u][1].x, a[u][3].x, nb1[u] & 1u);
+                                e1.y = g_op(a[u][1].y, a[u][3].y, (nb1[u] >> 1) & 1u);
+                                e1.z = g_op(a[u][1].z, a[u][3].z, (nb1[u] >> 2) & 1u);
+                                e1.w = g_op(a[u][1].w, a[u][3].w, (nb1[u] >> 3) & 1u);
+                            } else {
+                                e0.x = f_op(a[u][0].x, a[u][2].x); e0.y = f_op(a[u][0].y, a[u][2].y);
+                                e0.z = f_op(a[u][0].z, a[u][2].z); e0.w = f_op(a[u][0].w, a[u][2].w);
+                                e1.x = f_op(a[u][1].x, a[u][3].x); e1.y = f_op(a[u][1].y, a[u][3].y);
+                                e1.z = f_op(a[u][1].z, a[u][3].z); e1.w = f_op(a[u][1].w, a[u][3].w);
+                            }
                             r.x = f_op(e0.x, e1.x); r.y = f_op(e0.y, e1.y); r.z = f_op(e0.z, e1.z); r.w = f_op(e0.w, e1.w);
                             float4 *o1 = reinterpret_cast<float4 *>(reinterpret_cast<float *>(o1b) + (pp[u] << (j - 1)));
                             o1[vv[u]] = e0;
@@ -1403,6 +1425,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                     const int total = La << lv;
                     for (int t0 = tid; t0 < total; t0 += 2 * nthr) {
                         uint4 a[2][4];
+                        uint32_t nb0[2] = {0u, 0u}, nb1[2] = {0u, 0u};
                         int pp[2], vv[2];
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
@@ -1413,15 +1436,32 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                                 reinterpret_cast<const int8_t *>(inb) + (j == n ? 0 : ((int)idxc[pp[u] * 16 + j] << j)));
 #pragma unroll
                             for (int r = 0; r < 4; ++r) a[u][r] = in[vv[u] + r * (q >> 4)];
+                            if (isG) {
+                                const uint32_t *bl = blb + (int)bidxc[pp[u] * 16 + j - 1] * bwc;
+                                const int i0 = vv[u] << 4, i1 = i0 + q;
+                                nb0[u] = bl[i0 >> 5] >> (i0 & 31);
+                                nb1[u] = bl[i1 >> 5] >> (i1 & 31);
+                            }
                         }
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             if (t0 + u * nthr >= total) break;
                             uint4 e0, e1, r;
-                            e0.x = f4(a[u][0].x, a[u][2].x); e0.y = f4(a[u][0].y, a[u][2].y);
-                            e0.z = f4(a[u][0].z, a[u][2].z); e0.w = f4(a[u][0].w, a[u][2].w);
-                            e1.x = f4(a[u][1].x, a[u][3].x); e1.y = f4(a[u][1].y, a[u][3].y);
-                            e1.z = f4(a[u][1].z, a[u][3].z); e1.w = f4(a[u][1].w, a[u][3].w);
+                            if (isG) {
+                                e0.x = g4(a[u][0].x, a[u][2].x, nb0[u] & 15u);
+                                e0.y = g4(a[u][0].y, a[u][2].y, (nb0[u] >> 4) & 15u);
+                                e0.z = g4(a[u][0].z, a[u][2].z, (nb0[u] >> 8) & 15u);
+                                e0.w = g4(a[u][0].w, a[u][2].w, (nb0[u] >> 12) & 15u);
+                                e1.x = g4(a[u][1].x, a[u][3].x, nb1[u] & 15u);
+                                e1.y = g4(a[u][1].y, a[u][3].y, (nb1[u] >> 4) & 15u);
+                                e1.z = g4(a[u][1].z, a[u][3].z, (nb1[u] >> 8) & 15u);
+                                e1.w = g4(a[u][1].w, a[u][3].w, (nb1[u] >> 12) & 15u);
+                            } else {
+                                e0.x = f4(a[u][0].x, a[u][2].x); e0.y = f4(a[u][0].y, a[u][2].y);
+                                e0.z = f4(a[u][0].z, a[u][2].z); e0.w = f4(a[u][0].w, a[u][2].w);
+                                e1.x = f4(a[u][1].x, a[u][3].x); e1.y = f4(a[u][1].y, a[u][3].y);
+                                e1.z = f4(a[u][1].z, a[u][3].z); e1.w = f4(a[u][1].w, a[u][3].w);
+                            }
                             r.x = f4(e0.x, e1.x); r.y = f4(e0.y, e1.y); r.z = f4(e0.z, e1.z); r.w = f4(e0.w, e1.w);
                             uint4 *o1 = reinterpret_cast<uint4 *>(reinterpret_cast<int8_t *>(o1b) + (pp[u] << (j - 1)));
                             o1[vv[u]] = e0;
@@ -1435,7 +1475,7 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                     idxc[t * 16 + j - 2] = (uint8_t)t;
                 }
             }
-            // the left child's F is done: its flags (sync) close this operation
+            // the child's F is done: its flags (sync) close this operation
             ++o;
             op = opn;
             opn = (o + 1 < cv.n_ops) ? __ldg(cv.ops + o + 1) : 0u;
