@@ -64,6 +64,19 @@ template <> struct WA<int8_t> {
 
 __device__ __forceinline__ uint32_t spc_mask(int c) { return (0xFCA69530u >> (4 * c)) & 0xFu; }
 
+// Four int8 LLRs in one word (lanes of the SIMD intrinsics): F of Eq. (1) as
+// max(min(a, b), -max(a, b)), which is sign(a) sign(b) min(|a|, |b|) for
+// values in [-127, 127]; G of Eq. (2) with the four beta bits in nib (bit e ->
+// byte e), saturated to [-127, 127].
+__device__ __forceinline__ uint32_t f4w(uint32_t a, uint32_t b) {
+    return __vmaxs4(__vmins4(a, b), __vneg4(__vmaxs4(a, b)));
+}
+__device__ __forceinline__ uint32_t g4w(uint32_t a, uint32_t b, uint32_t nib) {
+    const uint32_t m = ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;   // byte e = 0xFF when bit e of nib
+    const uint32_t sa = (a & ~m) | (__vneg4(a) & m);
+    return __vmaxs4(__vaddss4(b, sa), 0x81818181u);
+}
+
 // Shared memory of one CTA (one frame at a time).
 struct WideSmem {
     uint8_t *idx[2], *bidx[2];     // [L][16] stage -> physical row
@@ -136,6 +149,52 @@ __device__ __forceinline__ int cta_excl_scan(int x, int *scan, int *total) {
     return base + v - x;
 }
 
+// Compare-exchange across lanes at distance j (< 32): the lower lane of each
+// pair keeps the smaller key when the run ascends, the larger one otherwise.
+__device__ __forceinline__ unsigned long long ce_lanes(unsigned long long x, int lane, int j, bool up) {
+    const unsigned long long y = __shfl_xor_sync(FULLW, x, j);
+    const unsigned long long mn = x < y ? x : y, mx = x < y ? y : x;
+    return (((lane & j) == 0) == up) ? mn : mx;
+}
+
+// Ascending bitonic sort of buf[0 .. P) by the CTA, P a power of two of at
+// least 32: the network of the plain shared-memory sort, with every distance
+// below 32 done by warp shuffles inside a 32-key chunk (warp w takes chunks w,
+// w + warps, ... one at a time, one key per lane), so that only distances of
+// 32 and more pass through shared memory with a CTA barrier after each.
+__device__ void cta_sort(unsigned long long *buf, int P) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nch = P >> 5;
+    for (int c = w; c < nch; c += nw) {
+        unsigned long long x = buf[c * 32 + lane];
+        for (int k = 2; k <= 32; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) x = ce_lanes(x, lane, j, ((c * 32 + lane) & k) == 0);
+        buf[c * 32 + lane] = x;
+    }
+    __syncthreads();
+    for (int k = 64; k <= P; k <<= 1) {
+        for (int j = k >> 1; j >= 32; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int o = i ^ j;
+                if (o > i) {
+                    const unsigned long long a = buf[i], b = buf[o];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { buf[i] = b; buf[o] = a; }
+                }
+            }
+            __syncthreads();
+        }
+        for (int c = w; c < nch; c += nw) {
+            unsigned long long x = buf[c * 32 + lane];
+            const bool up = ((c * 32) & k) == 0;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) x = ce_lanes(x, lane, j, up);
+            buf[c * 32 + lane] = x;
+        }
+        __syncthreads();
+    }
+}
+
 // Exact L-th smallest of the M = La * C > L candidate keys, source t owning
 // keys[c * L + t] for c < C. With a full list (La = L) the answer is at most t0, the
 // largest of the sources' best keys, so only keys <= t0 are sorted: the L
@@ -169,23 +228,11 @@ __device__ __forceinline__ unsigned long long cta_kth(const WideSmem &s, int M, 
     if (t < La)
         for (int c = 0; c < C; ++c)
             if (s.keys[c * L + t] <= t0) s.sortb[off++] = s.keys[c * L + t];
-    int P = 1;
+    int P = 32;
     while (P < S) P <<= 1;
     for (int i = S + t; i < P; i += blockDim.x) s.sortb[i] = KINF64;
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int o = i ^ j;
-                if (o > i) {
-                    const unsigned long long a = s.sortb[i], b = s.sortb[o];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) { s.sortb[i] = b; s.sortb[o] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
+    cta_sort(s.sortb, P);
     return s.sortb[L - 1];
 }
 
@@ -259,7 +306,77 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
             const int bwc = beta_words(jo);
             const uint32_t *blb = reinterpret_cast<const uint32_t *>(wbuf(v.gbl[jo], SX, G));
             T *outb = reinterpret_cast<T *>(wbuf(v.galpha[jo], SX, G));
-            if (h >= 4) {
+            // L = 128: several 16-byte items in flight per thread; L = 64 (64
+            // threads) measured faster with one 4-element item per pass
+            if (L >= 128 && sizeof(T) == 4 && h >= 4) {
+                // float4 items, four in flight per thread
+                const int lq = jo - 2;
+                const int total = La << lq;
+                for (int e0 = t; e0 < total; e0 += 4 * nt) {
+                    float4 a[4], b[4];
+                    uint32_t nb[4] = {0u, 0u, 0u, 0u};
+                    int pp[4], ii[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u * nt;
+                        pp[u] = e < total ? e >> lq : 0;
+                        ii[u] = e < total ? (e & ((h >> 2) - 1)) << 2 : 0;
+                        const float *in = reinterpret_cast<const float *>(wrow<T>(v, SX, G, s, cur, pp[u], j));
+                        a[u] = *reinterpret_cast<const float4 *>(in + ii[u]);
+                        b[u] = *reinterpret_cast<const float4 *>(in + ii[u] + h);
+                        if (kind == OP_G)
+                            nb[u] = (blb[(int)s.bidx[cur][pp[u] * 16 + jo] * bwc + (ii[u] >> 5)] >> (ii[u] & 31)) & 15u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (e0 + u * nt >= total) break;
+                        float4 r;
+                        if (kind == OP_F) {
+                            r.x = WA<float>::f(a[u].x, b[u].x); r.y = WA<float>::f(a[u].y, b[u].y);
+                            r.z = WA<float>::f(a[u].z, b[u].z); r.w = WA<float>::f(a[u].w, b[u].w);
+                        } else {
+                            r.x = WA<float>::g(a[u].x, b[u].x, nb[u] & 1u);
+                            r.y = WA<float>::g(a[u].y, b[u].y, (nb[u] >> 1) & 1u);
+                            r.z = WA<float>::g(a[u].z, b[u].z, (nb[u] >> 2) & 1u);
+                            r.w = WA<float>::g(a[u].w, b[u].w, (nb[u] >> 3) & 1u);
+                        }
+                        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(outb) + ((size_t)pp[u] << jo) + ii[u]) = r;
+                    }
+                }
+            } else if (L >= 128 && sizeof(T) == 1 && h >= 16) {
+                // 16-byte items of int8 LLRs (four-lane SIMD words), two in flight per thread
+                const int lq = jo - 4;
+                const int total = La << lq;
+                for (int e0 = t; e0 < total; e0 += 2 * nt) {
+                    uint4 a[2], b[2];
+                    uint32_t nb[2] = {0u, 0u};
+                    int pp[2], ii[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int e = e0 + u * nt;
+                        pp[u] = e < total ? e >> lq : 0;
+                        ii[u] = e < total ? (e & ((h >> 4) - 1)) << 4 : 0;
+                        const int8_t *in = reinterpret_cast<const int8_t *>(wrow<T>(v, SX, G, s, cur, pp[u], j));
+                        a[u] = *reinterpret_cast<const uint4 *>(in + ii[u]);
+                        b[u] = *reinterpret_cast<const uint4 *>(in + ii[u] + h);
+                        if (kind == OP_G)
+                            nb[u] = (blb[(int)s.bidx[cur][pp[u] * 16 + jo] * bwc + (ii[u] >> 5)] >> (ii[u] & 31)) & 0xFFFFu;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (e0 + u * nt >= total) break;
+                        uint4 r;
+                        if (kind == OP_F) {
+                            r.x = f4w(a[u].x, b[u].x); r.y = f4w(a[u].y, b[u].y);
+                            r.z = f4w(a[u].z, b[u].z); r.w = f4w(a[u].w, b[u].w);
+                        } else {
+                            r.x = g4w(a[u].x, b[u].x, nb[u] & 15u); r.y = g4w(a[u].y, b[u].y, (nb[u] >> 4) & 15u);
+                            r.z = g4w(a[u].z, b[u].z, (nb[u] >> 8) & 15u); r.w = g4w(a[u].w, b[u].w, (nb[u] >> 12) & 15u);
+                        }
+                        *reinterpret_cast<uint4 *>(reinterpret_cast<int8_t *>(outb) + ((size_t)pp[u] << jo) + ii[u]) = r;
+                    }
+                }
+            } else if (h >= 4) {
                 // four consecutive elements per item (16-byte float / 4-byte int8 vectors)
                 const int lq = jo - 2;
                 for (int e = t; e < (La << lq); e += nt) {
@@ -447,10 +564,8 @@ __device__ void wide_frame(const WideView &v, uint8_t *SX, uint8_t *G, const Wid
                 const int sp = ki / C, c = ki - sp * C;
                 const unsigned long long key = s.keys[(ki & (C - 1)) * L + ki / C];
                 s.pen[nxt][t] = (uint32_t)(key >> 32);
-                for (int b = 0; b < 16; ++b) {
-                    s.idx[nxt][t * 16 + b] = s.idx[cur][sp * 16 + b];
-                    s.bidx[nxt][t * 16 + b] = s.bidx[cur][sp * 16 + b];
-                }
+                reinterpret_cast<uint4 *>(s.idx[nxt])[t] = reinterpret_cast<const uint4 *>(s.idx[cur])[sp];
+                reinterpret_cast<uint4 *>(s.bidx[nxt])[t] = reinterpret_cast<const uint4 *>(s.bidx[cur])[sp];
                 if (!dest) s.bidx[nxt][t * 16 + j] = (uint8_t)t;
                 uint32_t *ob = bout + t * ostride;
                 if (kind == OP_REP) {
