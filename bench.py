@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--fer-points", default="3.5,3.75,4.0,4.25,4.5", help="Eb/N0 points (dB) of the FER sweep")
     ap.add_argument("--fer-codes", default="c2,c3", help="FER sweep codes: c2 = (1024,860), c3 = (2048,1723)")
     ap.add_argument("--details", default="", help="also write every measured block in full to this JSON file")
-    ap.add_argument("--case", default="", choices=["", "sc1", "list", "wide", "batch"],
+    ap.add_argument("--case", default="", choices=["", "sc1", "sc1w", "list", "wide", "batch"],
                     help="run one small decode case for a profiler and exit: each dtype (or plan) once as warm-up, "
                          "then once more")
     return ap.parse_args()
@@ -991,6 +991,8 @@ def run_ours(args):
 def run_case(name):
     """Small cases for ncu captures (inputs above L2, a few GB at most):
     sc1   (2048,1723) L = 1, 2^16 frames, f32 then int8 (launches 1 and 3 of sc1_kernel);
+    sc1w  (2048,1723) L = 1, 152 frames (a small batch: one warp per frame), f32 then int8
+          (launches 1 and 3 of sc1w_kernel);
     list  (2048,1723) L = 32, 2^15 frames, 1 warp per frame, 7000-byte budget, 512-thread CTAs,
           f32 then int8 (launches 1 and 3 of decode_kernel);
     wide  (1024,860) L = 128, 2^13 frames, f32 (launch 1 of wide_kernel);
@@ -1003,15 +1005,15 @@ def run_case(name):
     from paper_1505_01466_gb300 import inputs as I, workloads as WL
     from paper_1505_01466_gb300.polar import PolarCode, PolarBatch, LLR_I8
     torch.cuda.set_device(0)
-    if name in ("sc1", "list"):
-        Lc, F = (1, 1 << 16) if name == "sc1" else (L, 1 << 15)
+    if name in ("sc1", "sc1w", "list"):
+        Lc, F = {"sc1": (1, 1 << 16), "sc1w": (1, 152), "list": (L, 1 << 15)}[name]
         frozen = I.ga_frozen_mask(N, K, DESIGN_DB, (K - CRC_LEN) / N)
         _, f32, i8 = I.make_frames_torch(frozen, CRC_LEN, I.CRC32_POLY, EBN0_DB, F, seed=5, device="cuda")
         code = PolarCode(frozen, CRC_LEN, I.CRC32_POLY, Lc)
         for dt, llr in ((0, f32), (1, i8)):
             if name == "list":
                 code.set_launch(dt, 1, 7000, 512)
-            code.decode(llr[:4096])
+            code.decode(llr[:min(4096, F)])
             code.decode(llr)
     elif name == "wide":
         frozen = I.ga_frozen_mask(1024, 860, DESIGN_DB, 828 / 1024)
