@@ -1351,8 +1351,8 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
                 else if (D == 2) fg_virtual<T, 2>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
                 else fg_virtual<T, 3>(lay, S, Gs, chan, idxc, bidxc, isG, j, s0, La, tid, nthr);
             }
-        } else if ((kind == OP_F || kind == OP_G) && op_kind(opn) == OP_F && op_stage(opn) == j - 1 && j - 2 >= 5 &&
-                   ((lay.virt_mask >> (j - 2)) & 7u) == 0 && (sizeof(T) == 1 || L <= 8)) {
+        } else if ((sizeof(T) == 1 || (SEG && L <= 8)) && (kind == OP_F || kind == OP_G) && op_kind(opn) == OP_F &&
+                   op_stage(opn) == j - 1 && j - 2 >= 5 && ((lay.virt_mask >> (j - 2)) & 7u) == 0) {
             // ------------ F or G, then the child's F: stage j -> j-1 -> j-2 ------------
             // The child that stage j-1 feeds (the left one after F, the right
             // one after G) is an inner node too, so its F comes next. Each item
@@ -1361,8 +1361,10 @@ __device__ __forceinline__ void decode_frame(const CodeView &cv, uint8_t *S, uin
             // j-1 (the child's G reads them later) and, from the same
             // registers, stage j-2: one pass and one dependent round trip fewer
             // than two operations. Measured faster for int8 at every L and for
-            // float at L <= 8; float at L = 16 / 32 keeps two operations (eight
-            // items in flight per thread instead of four there).
+            // float at L <= 8, slower for float at L = 16 / 32 (four items in
+            // flight per thread instead of eight). Float takes it only in the
+            // packed instantiations (L <= 4 by default): compiled into the
+            // kernel that L = 32 runs, the unused code alone cost it about 1 %.
             if (!solo || wig == 0) {
                 const int q = 1 << (j - 2);
                 const bool isG = kind == OP_G;
