@@ -379,6 +379,20 @@ __global__ void __launch_bounds__(kSc1Threads) sc1_kernel(const Sc1Params p) {
             } else {
                 leaf<T, PT>(ln, ch, kind, j, s, pen);
             }
+            // float: after the last reader of stage j (G, or a leaf) its lines
+            // are dead until an F or G rewrites them; drop them from L2 so that
+            // they are never written back (this kernel is bound by DRAM
+            // bandwidth, much of it the write-back of spilled stages). Measured:
+            // +2 to +5 % (f32); also dropping the stage below a leaf gained less.
+            if (es == 4 && gwarp && j < p.n && j >= p.split && kind != OP_F && kind != OP_COMB) {
+                uint8_t *dead = gwarp + (size_t)(words_below(j, es) - words_below(p.split, es)) * 128;
+                if ((reinterpret_cast<uintptr_t>(dead) & 127u) == 0) {
+                    __syncwarp();
+                    for (int q = lane; q < (1 << j); q += 32)
+                        asm volatile("discard.global.L2 [%0], 128;" ::"l"(dead + (size_t)q * 128) : "memory");
+                    __syncwarp();
+                }
+            }
         }
 
         // ---------------- final pick (Sec. II-B) ----------------
