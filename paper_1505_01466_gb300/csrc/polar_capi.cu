@@ -142,9 +142,9 @@ cudaError_t launch_batch_locked(int dtype, int warps, bool seg, const BatchParam
     std::lock_guard<std::mutex> lk(g_launch_mu);
     return launch_batch(dtype, warps, seg, b, grid, smem, threads, st);
 }
-int occupancy_sc1_locked(int dtype, uint32_t warp_bytes, int warps) {
+int occupancy_sc1_locked(int dtype, uint32_t warp_bytes, int warps, bool drop) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
-    return occupancy_sc1(dtype, warp_bytes, warps);
+    return occupancy_sc1(dtype, warp_bytes, warps, drop);
 }
 cudaError_t launch_sc1_locked(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_launch_mu);
@@ -611,6 +611,11 @@ bool use_sc1(const polar_code *c, int dtype) { return c->L == 1 && c->d_sops && 
 // as the shared memory takes (at most kSc1Threads / 32).
 struct Sc1Shape : Sc1Layout {
     int warps;
+    // float codes with special nodes (Fast-SSC) run the instantiation that drops
+    // dead spilled stages from L2: measured 2 to 5 % faster; plain SC decoding
+    // (one-bit leaves, many more small operations) lost 15 % to it, mostly to
+    // the registers it adds, and keeps the plain one
+    bool drop;
 };
 
 Sc1Shape sc1_shape(const polar_code *code, int dtype, uint32_t budget) {
@@ -619,6 +624,7 @@ Sc1Shape sc1_shape(const polar_code *code, int dtype, uint32_t budget) {
     sc1_layout((int)code->n, es, std::min(budget, kMaxSmemPerCta), &sh);
     sh.warps = sh.warp_bytes == 0 ? kSc1Threads / 32
                                   : std::max(1, std::min<int>(kSc1Threads / 32, (int)(kMaxSmemPerCta / sh.warp_bytes)));
+    sh.drop = dtype == POLAR_LLR_F32 && (code->flags & 0xFFu) != POLAR_NO_SPECIAL_NODES;
     return sh;
 }
 
@@ -640,6 +646,7 @@ Sc1Params sc1_params(const polar_code *code, const Sc1Shape &sh, const void *llr
     p.warp_bytes = sh.warp_bytes;
     p.beta_off = sh.beta_off;
     p.warp_gbytes = sh.warp_gbytes;
+    p.drop = sh.drop ? 1 : 0;
     p.llr = llr;
     p.bits = bits;
     p.pm = pm;
@@ -653,7 +660,7 @@ Sc1Params sc1_params(const polar_code *code, const Sc1Shape &sh, const void *llr
 
 // Grid of the L = 1 kernel: resident CTAs, no more than the frames need.
 int sc1_grid(const polar_code *code, int dtype, const Sc1Shape &sh, uint32_t n_frames, uint64_t *grid) {
-    const int occ = occupancy_sc1_locked(dtype, sh.warp_bytes, sh.warps);
+    const int occ = occupancy_sc1_locked(dtype, sh.warp_bytes, sh.warps, sh.drop);
     if (occ <= 0) return POLAR_ECUDA;
     uint64_t g = (uint64_t)occ * (uint64_t)code->sm_count;
     const uint64_t need = ((uint64_t)n_frames + 32u * sh.warps - 1) / (32u * sh.warps);
@@ -1096,7 +1103,7 @@ int polar_code_autotune(polar_code_t *code, int llr_dtype, const void *llr_dev, 
         // favour layouts with fewer resident warps; keep the default then.
         {
             const Sc1Shape d0 = sc1_shape(code, llr_dtype, 0);
-            const int occ0 = occupancy_sc1_locked(llr_dtype, d0.warp_bytes, d0.warps);
+            const int occ0 = occupancy_sc1_locked(llr_dtype, d0.warp_bytes, d0.warps, d0.drop);
             if (occ0 <= 0) return POLAR_ECUDA;
             if ((uint64_t)n_frames < (uint64_t)occ0 * code->sm_count * 32u * (uint64_t)d0.warps) {
                 code->sc1_budget[llr_dtype] = 0;

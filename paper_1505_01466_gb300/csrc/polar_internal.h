@@ -226,6 +226,7 @@ struct Sc1Params {
     uint32_t warp_bytes, beta_off; // shared memory of one warp (32 frames); offset of its beta rows
     uint64_t warp_gbytes;          // global scratch of one warp
     uint8_t *scratch;              // warp_gbytes per warp of the grid (when split < n)
+    int drop;                      // float: drop dead spilled stages from L2 (the DROP instantiation)
     const void *llr;               // [n_frames][N]
     uint8_t *bits;                 // [n_frames][kb]
     float *pm;
@@ -243,7 +244,7 @@ struct Sc1Layout {
     uint64_t warp_gbytes;
 };
 void sc1_layout(int n, int es, uint32_t budget, Sc1Layout *lay);
-int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps);
+int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps, bool drop);
 cudaError_t launch_sc1(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t stream);
 
 // The L = 1 kernel for small batches (polar_sc1w.cu): one warp per frame, the

@@ -335,8 +335,9 @@ __device__ __forceinline__ void leaf(const Lane &ln, const Chan &ch, int kind, i
     }
 }
 
-template <typename T>
+template <typename T, bool DROP>
 __global__ void __launch_bounds__(kSc1Threads) sc1_kernel(const Sc1Params p) {
+    static_assert(!DROP || sizeof(T) == 4, "stages are dropped for float only");
     typedef typename std::conditional<sizeof(T) == 4, float, int>::type PT;   // penalty: exact int for int8
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -379,12 +380,12 @@ __global__ void __launch_bounds__(kSc1Threads) sc1_kernel(const Sc1Params p) {
             } else {
                 leaf<T, PT>(ln, ch, kind, j, s, pen);
             }
-            // float: after the last reader of stage j (G, or a leaf) its lines
-            // are dead until an F or G rewrites them; drop them from L2 so that
-            // they are never written back (this kernel is bound by DRAM
-            // bandwidth, much of it the write-back of spilled stages). Measured:
-            // +2 to +5 % (f32); also dropping the stage below a leaf gained less.
-            if (es == 4 && gwarp && j < p.n && j >= p.split && kind != OP_F && kind != OP_COMB) {
+            // DROP (float, node sets with special nodes): after the last reader
+            // of stage j (G, or a leaf) its lines are dead until an F or G
+            // rewrites them; drop them from L2 so that they are never written
+            // back (this kernel is bound by DRAM bandwidth, much of it the
+            // write-back of spilled stages)
+            if (DROP && gwarp && j < p.n && j >= p.split && kind != OP_F && kind != OP_COMB) {
                 uint8_t *dead = gwarp + (size_t)(words_below(j, es) - words_below(p.split, es)) * 128;
                 if ((reinterpret_cast<uintptr_t>(dead) & 127u) == 0) {
                     __syncwarp();
@@ -463,9 +464,10 @@ void sc1_layout(int n, int es, uint32_t budget, Sc1Layout *lay) {
     lay->warp_gbytes = gb + (lay->beta_smem ? 0u : beta_bytes);
 }
 
-int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps) {
+int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps, bool drop) {
     const int smem = warps * (int)warp_bytes;
-    const void *fn = dtype == POLAR_LLR_I8 ? (const void *)sc1_kernel<int8_t> : (const void *)sc1_kernel<float>;
+    const void *fn = dtype == POLAR_LLR_I8 ? (const void *)sc1_kernel<int8_t, false>
+                                           : (drop ? (const void *)sc1_kernel<float, true> : (const void *)sc1_kernel<float, false>);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, 32 * warps, smem) != cudaSuccess) return 0;
@@ -475,11 +477,14 @@ int occupancy_sc1(int dtype, uint32_t warp_bytes, int warps) {
 cudaError_t launch_sc1(int dtype, const Sc1Params &p, int grid, int warps, cudaStream_t st) {
     const int smem = warps * (int)p.warp_bytes;
     if (dtype == POLAR_LLR_I8) {
-        cudaFuncSetAttribute(sc1_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        sc1_kernel<int8_t><<<grid, 32 * warps, smem, st>>>(p);
+        cudaFuncSetAttribute(sc1_kernel<int8_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        sc1_kernel<int8_t, false><<<grid, 32 * warps, smem, st>>>(p);
+    } else if (p.drop) {
+        cudaFuncSetAttribute(sc1_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        sc1_kernel<float, true><<<grid, 32 * warps, smem, st>>>(p);
     } else {
-        cudaFuncSetAttribute(sc1_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        sc1_kernel<float><<<grid, 32 * warps, smem, st>>>(p);
+        cudaFuncSetAttribute(sc1_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        sc1_kernel<float, false><<<grid, 32 * warps, smem, st>>>(p);
     }
     return cudaGetLastError();
 }
