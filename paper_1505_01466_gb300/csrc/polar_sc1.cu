@@ -31,7 +31,12 @@
 //    w * 32 + l), in shared memory if the budget holds it: a leaf writes its bits at its position and
 //    Combine (Eq. (3)) xors the right half into the left in place, so at the
 //    end the row holds the codeword x;
-//  * the channel row (stage n) is read from the caller's buffer.
+//  * the channel row (stage n) is read from the caller's buffer;
+//  * float codes with special nodes run the DROP instantiation: once the last
+//    reader of a spilled stage (a G, or a leaf) is done, its lines are
+//    discarded from L2, so that dead stages are not written back to DRAM
+//    (the float kernel is bound by DRAM bandwidth). Plain SC decoding keeps
+//    the other instantiation, which needs fewer registers.
 //
 // Float sums follow the pairwise tree s[i] = x[i] + x[i + n/2] (computed in
 // the dead stage below the leaf); int8 LLRs use saturated G and exact
